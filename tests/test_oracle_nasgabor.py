@@ -1,0 +1,369 @@
+"""Pins of the FP64 NASGabor oracle against what the paper and the mathematics fix.
+
+Each test is chosen so that a plausible mistake in the oracle (a dropped term,
+a wrong sign or index, a transposed operand) fails at least one of them:
+  * special cases that reduce to textbook / library functions (SG, von Mises-Fisher),
+  * the Sec. 4.1 closed-form integral where it is exact, by quadrature,
+  * the unit mass of the approximately normalised kernel at k = 0,
+  * the special values at d = +-z,
+  * invariance under a joint rotation and under x -> -x (evenness in d.x),
+  * the Supp. C cosine frame against a library rotation,
+  * every analytic derivative against central finite differences in FP64.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+from scipy.stats import vonmises_fisher
+
+from oracle import nasgabor as ng
+from paper_2606_09794_gb300 import inputs
+from tests._quadrature import integrate_lobe
+
+RNG = np.random.default_rng(20260)
+
+
+def _unit(v):
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+def _random_frames(n, rng):
+    q = _unit(rng.standard_normal((n, 4)))
+    return (q,) + ng.frame_from_quat(q)
+
+
+# ---------------------------------------------------------------------------
+# Special cases
+# ---------------------------------------------------------------------------
+
+def test_isotropic_no_carrier_is_spherical_gaussian():
+    """a = 0, k = 0: G reduces to the normalised SG of the distributions table,
+    lam/(2 pi (1 - e^{-2 lam})) exp(lam (z.d - 1))."""
+    n = 2000
+    d = _unit(RNG.standard_normal((n, 3)))
+    _, x, z = _random_frames(n, RNG)
+    lam = np.exp(RNG.uniform(-2, 5, n))
+    G = ng.lobe(d, x, z, lam, np.zeros(n), np.zeros(n), ng.NORM_APPROX)
+    u = np.sum(d * z, -1)
+    sg = lam / (2 * np.pi * (1 - np.exp(-2 * lam))) * np.exp(lam * (u - 1))
+    np.testing.assert_allclose(G, sg, rtol=1e-12, atol=0)
+
+
+def test_isotropic_no_carrier_is_von_mises_fisher_density():
+    """a = 0, k = 0, normalised: the von Mises-Fisher density with concentration lam (scipy)."""
+    for lam in (0.5, 3.0, 40.0):
+        z = _unit(RNG.standard_normal(3))
+        q = Rotation.align_vectors([z], [[0, 0, 1]])[0].as_quat()  # x, y, z, w
+        qw = np.array([q[3], q[0], q[1], q[2]])
+        x_ax, z_ax = ng.frame_from_quat(qw[None, :])
+        np.testing.assert_allclose(z_ax[0], z, atol=1e-12)
+        d = _unit(RNG.standard_normal((500, 3)))
+        n = d.shape[0]
+        G = ng.lobe(d, np.broadcast_to(x_ax, d.shape), np.broadcast_to(z_ax, d.shape),
+                    np.full(n, lam), np.zeros(n), np.zeros(n), ng.NORM_APPROX)
+        ref = vonmises_fisher(z, lam).pdf(d)
+        np.testing.assert_allclose(G, ref, rtol=1e-10)
+
+
+def test_isotropic_with_carrier_is_sg_times_carrier():
+    """a = 0: tau = 0, E = 1 and G = SG(d) (1 + cos(k d.x))/2; checks the carrier's argument is d.x."""
+    n = 1000
+    d = _unit(RNG.standard_normal((n, 3)))
+    _, x, z = _random_frames(n, RNG)
+    lam = np.exp(RNG.uniform(0, 4, n))
+    k = RNG.uniform(0, 40, n)
+    G = ng.lobe(d, x, z, lam, np.zeros(n), k, ng.NORM_NONE)
+    u, v = np.sum(d * z, -1), np.sum(d * x, -1)
+    np.testing.assert_allclose(G, np.exp(lam * (u - 1)) * np.cos(k * v / 2) ** 2, rtol=1e-12, atol=1e-300)
+
+
+def test_special_values_at_poles():
+    """Sec. 4.1: G(z) = 1 and G(-z) = 0 for the unnormalised kernel; C^-1 at z when normalised."""
+    n = 50
+    _, x, z = _random_frames(n, RNG)
+    lam = np.exp(RNG.uniform(0, 6, n))
+    a = RNG.uniform(0, 2, n)
+    k = RNG.uniform(0, 40, n)
+    # random frames: z.z is 1 only up to rounding, so the values are the limits
+    np.testing.assert_allclose(ng.lobe(z, x, z, lam, a, k, ng.NORM_NONE), 1.0, rtol=1e-12)
+    # (at -z the limit depends on the path: along d.x = 0 it is e^{-2 lam}, not the
+    # convention G(-z) = 0, so only the exact antipode is checked below)
+    np.testing.assert_allclose(ng.lobe(z, x, z, lam, a, k, ng.NORM_APPROX), ng.norm_approx(lam, a), rtol=1e-12)
+    # exact world-axis frame: the Sec. 4.1 special values hold exactly
+    e = np.array([[0.0, 0.0, 1.0]])
+    xe = np.array([[1.0, 0.0, 0.0]])
+    one = np.ones(1)
+    assert ng.lobe(e, xe, e, 7 * one, 0.4 * one, 3 * one, ng.NORM_NONE)[0] == 1.0
+    assert ng.lobe(-e, xe, e, 7 * one, 0.4 * one, 3 * one, ng.NORM_NONE)[0] == 0.0
+    # exact poles along the world axis: q = identity, d = +-e_z, all finite
+    G, par = ng.lobe(e, xe, e, np.array([5.0]), np.array([0.3]), np.array([2.0]), ng.NORM_APPROX, True)
+    assert np.isfinite(G).all() and all(np.isfinite(v).all() for v in par.values())
+    G, par = ng.lobe(-e, xe, e, np.array([5.0]), np.array([0.3]), np.array([2.0]), ng.NORM_APPROX, True)
+    assert G[0] == 0.0 and all((v == 0).all() for v in par.values())
+
+
+def test_near_pole_is_continuous():
+    """Directions 1e-3 .. 1e-7 rad from +z approach the pole value C^-1 h(0) = C^-1."""
+    lam, a, k = 20.0, 0.7, 3.0
+    vals = []
+    for eps in (1e-3, 1e-5, 1e-7):
+        d = np.array([[math.sin(eps), 0.0, math.cos(eps)]])
+        vals.append(ng.lobe(d, np.array([[1.0, 0, 0]]), np.array([[0, 0, 1.0]]), np.array([lam]),
+                            np.array([a]), np.array([k]), ng.NORM_APPROX)[0])
+    lim = ng.norm_approx(lam, a)
+    errs = [abs(v - lim) / lim for v in vals]
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Integrals (Sec. 4.1 closed form; NASG normalisation of the distributions table)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lam,a", [(0.3, 0.0), (1.0, 0.5), (4.0, 1.5), (60.0, 0.9), (900.0, 0.3)])
+def test_approx_normalised_kernel_has_unit_mass_without_carrier(lam, a):
+    """k = 0: int C^-1 p E d omega = 1 (the NASG constant is exact)."""
+    val = integrate_lobe(ng.lobe, lam, a, 0.0, ng.NORM_APPROX)
+    assert abs(val - 1.0) < 1e-9
+
+
+@pytest.mark.parametrize("lam,a,k", [
+    (0.3, 0.0, 3.0), (1.0, 0.0, 2.0), (2.5, 0.0, 40.0), (7.0, 0.0, 7.0), (30.0, 0.0, 12.0),
+    (1.0, 0.5, 0.0), (3.0, 1.2, 0.0), (200.0, 0.7, 0.0),
+])
+def test_closed_form_integral_where_exact(lam, a, k):
+    """Sec. 4.1 closed form vs quadrature of the unnormalised kernel, for a = 0 or k = 0.
+
+    Covers Lambda > k, Lambda < k (sinhc continued to sin x / x) and Lambda = k."""
+    quad = integrate_lobe(ng.lobe, lam, a, k, ng.NORM_NONE)
+    closed = float(ng.integral_closed_form(lam, a, k))
+    assert abs(quad - closed) <= 1e-9 * abs(closed)
+
+
+def test_closed_form_integral_is_approximate_for_anisotropic_carrier():
+    """For a > 0 and k > 0 the printed closed form departs from the quadrature
+    (reading recorded in the design notes); the deviation is small but real."""
+    quad = integrate_lobe(ng.lobe, 1.0, 0.5, 2.0, ng.NORM_NONE)
+    closed = float(ng.integral_closed_form(1.0, 0.5, 2.0))
+    rel = abs(quad - closed) / quad
+    assert 1e-3 < rel < 0.1
+
+
+def test_exact_normalisation_has_unit_mass_where_closed_form_exact():
+    val = integrate_lobe(ng.lobe, 3.0, 0.0, 9.0, ng.NORM_EXACT)
+    assert abs(val - 1.0) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Invariances
+# ---------------------------------------------------------------------------
+
+def _quat_mul(p, q):
+    w1, x1, y1, z1 = (p[..., i] for i in range(4))
+    w2, x2, y2, z2 = (q[..., i] for i in range(4))
+    return np.stack([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2,
+                     w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2,
+                     w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2], axis=-1)
+
+
+def test_joint_rotation_invariance():
+    n = 3000
+    q, x, z = _random_frames(n, RNG)
+    d = _unit(RNG.standard_normal((n, 3)))
+    lam, a, k = np.exp(RNG.uniform(0, 5, n)), RNG.uniform(0, 1, n), RNG.uniform(0, 8, n)
+    G0 = ng.lobe(d, x, z, lam, a, k)
+    r = _unit(RNG.standard_normal(4))
+    R = Rotation.from_quat([r[1], r[2], r[3], r[0]]).as_matrix()
+    x2, z2 = ng.frame_from_quat(_quat_mul(np.broadcast_to(r, q.shape), q))
+    np.testing.assert_allclose(x2, x @ R.T, atol=1e-14)
+    G1 = ng.lobe(d @ R.T, x2, z2, lam, a, k)
+    np.testing.assert_allclose(G1, G0, rtol=1e-11, atol=1e-300)
+
+
+def test_even_in_d_dot_x():
+    """Rotating the frame by pi about z (x -> -x, y -> -y) leaves G unchanged."""
+    n = 2000
+    q, x, z = _random_frames(n, RNG)
+    d = _unit(RNG.standard_normal((n, 3)))
+    lam, a, k = np.exp(RNG.uniform(0, 5, n)), RNG.uniform(0, 1, n), RNG.uniform(0, 8, n)
+    q2 = _quat_mul(q, np.broadcast_to(np.array([0.0, 0, 0, 1]), q.shape))
+    x2, z2 = ng.frame_from_quat(q2)
+    np.testing.assert_allclose(x2, -x, atol=1e-14)
+    np.testing.assert_allclose(z2, z, atol=1e-14)
+    np.testing.assert_allclose(ng.lobe(d, x2, z2, lam, a, k), ng.lobe(d, x, z, lam, a, k), rtol=1e-9)
+
+
+def test_anisotropy_orientation():
+    """With a > 0 the lobe is narrower along x than along y: G(tilt toward x) < G(tilt toward y)."""
+    x = np.array([[1.0, 0, 0]])
+    z = np.array([[0, 0, 1.0]])
+    t = 0.2
+    dx = np.array([[math.sin(t), 0, math.cos(t)]])
+    dy = np.array([[0, math.sin(t), math.cos(t)]])
+    args = (np.array([10.0]), np.array([1.0]), np.array([0.0]))
+    assert ng.lobe(dx, x, z, *args) < ng.lobe(dy, x, z, *args)
+
+
+def test_quat_frame_matches_library_rotation():
+    q = _unit(RNG.standard_normal((200, 4)))
+    x, z = ng.frame_from_quat(q)
+    R = Rotation.from_quat(np.stack([q[:, 1], q[:, 2], q[:, 3], q[:, 0]], -1)).as_matrix()
+    np.testing.assert_allclose(x, R[:, :, 0], atol=1e-14)
+    np.testing.assert_allclose(z, R[:, :, 2], atol=1e-14)
+
+
+def test_cos_frame_is_a_rotation_and_agrees_with_quat_mode():
+    """Supp. C frame: orthonormal with y = z x x, and the same G as the QUAT frame of that rotation."""
+    n = 500
+    ang = RNG.uniform(0.05, np.pi - 0.05, (n, 3))
+    c = np.cos(ang)
+    x, z = ng.frame_from_cos(c)
+    y = np.cross(z, x)
+    R = np.stack([x, y, z], axis=-1)
+    np.testing.assert_allclose(R @ np.swapaxes(R, -1, -2), np.broadcast_to(np.eye(3), R.shape), atol=1e-14)
+    np.testing.assert_allclose(np.linalg.det(R), 1.0, atol=1e-13)
+    qs = Rotation.from_matrix(R).as_quat()
+    q = np.stack([qs[:, 3], qs[:, 0], qs[:, 1], qs[:, 2]], -1)
+    xq, zq = ng.frame_from_quat(q)
+    np.testing.assert_allclose(xq, x, atol=1e-13)
+    np.testing.assert_allclose(zq, z, atol=1e-13)
+
+
+def test_parameter_count_matches_paper_table():
+    """Efficiency table: NASGabor with 1/2/4 lobes has 12/21/39 appearance parameters
+    (3 diffuse + 9 per lobe in the Supp. C parameterisation); SH degree 3 has 48.
+    The storage column is consistent with those counts at one primitive count."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "efficiency_table.json")) as f:
+        tab = json.load(f)
+    for row in tab["nasgabor"]:
+        assert 3 + ng.lobe_planes(ng.FRAME_COS) * row["lobes"] == row["params"]
+    assert (3 + 1) ** 2 * 3 == tab["sh3"]["params"]
+    # storage deltas per extra FP32 parameter give one primitive count
+    rows = {r["lobes"]: r for r in tab["nasgabor"]}
+    per_param = []
+    for a, b in ((1, 2), (2, 4)):
+        dp = rows[b]["params"] - rows[a]["params"]
+        per_param.append((rows[b]["storage_mb"] - rows[a]["storage_mb"]) / dp)
+    dp = tab["sh3"]["params"] - rows[1]["params"]
+    per_param.append((tab["sh3"]["storage_mb"] - rows[1]["storage_mb"]) / dp)
+    assert max(per_param) / min(per_param) < 1.001
+
+
+# ---------------------------------------------------------------------------
+# Derivatives (Supp. E/F, readings R3-R8) against central finite differences
+# ---------------------------------------------------------------------------
+
+def _fd_case(frame_mode, act_mode, n, n_lobes, seed, lam_hi=50.0):
+    rng = np.random.default_rng(seed)
+    P = ng.lobe_planes(frame_mode)
+    if act_mode == ng.ACT_RAW:
+        w = inputs.point_cloud_workload(n, n_lobes, seed, frame_mode)
+        params = w.params.astype(np.float64)
+        base = 4 if frame_mode == ng.FRAME_QUAT else 3
+        params[base] = np.log(np.exp(rng.uniform(0, math.log(lam_hi), n * n_lobes)))
+        # spread k over the paper's full [0, 40] range, and w over [-1, 1]
+        params[base + 2] = np.arctanh(rng.uniform(0.01, 39.9, n * n_lobes) / 20 - 1)
+        params[base + 3:base + 6] = np.arctanh(rng.uniform(-0.95, 0.95, (3, n * n_lobes)))
+        c0, means, cam = w.c0, w.means, w.cam
+    else:
+        params = np.zeros((P, n * n_lobes))
+        if frame_mode == ng.FRAME_QUAT:
+            params[0:4] = rng.standard_normal((4, n * n_lobes))
+        else:
+            params[0:3] = np.cos(rng.uniform(0.1, np.pi - 0.1, (3, n * n_lobes)))
+        base = 4 if frame_mode == ng.FRAME_QUAT else 3
+        params[base] = rng.uniform(0.5, lam_hi, n * n_lobes)
+        params[base + 1] = rng.uniform(0.0, 2.0, n * n_lobes)
+        params[base + 2] = rng.uniform(0.0, 40.0, n * n_lobes)
+        params[base + 3:base + 6] = rng.uniform(-1, 1, (3, n * n_lobes))
+        c0 = rng.uniform(0, 1, (3, n))
+        means = rng.uniform(0, 1, (n, 3))
+        cam = np.array([0.0, 0.0, 3.0])
+    g_rgb = rng.standard_normal((n, 3))
+    return params, c0, means, cam, g_rgb
+
+
+def _assert_fd(an, fd, where, rtol=2e-6, atol_frac=1e-8):
+    """|analytic - FD| <= rtol |FD| + atol_frac max|FD| (the FD noise floor is ~1e-10 absolute)."""
+    tol = rtol * np.abs(fd) + atol_frac * np.max(np.abs(fd)) + 1e-14
+    bad = np.abs(an - fd) > tol
+    assert not bad.any(), (where, an[bad][:4], fd[bad][:4])
+
+
+def _per_prim_loss(params, c0, means, cam, g_rgb, n_lobes, fm, nm, am):
+    return np.sum(g_rgb * ng.forward(params, c0, means, cam, n_lobes, fm, nm, am), axis=-1)
+
+
+@pytest.mark.parametrize("frame_mode", [ng.FRAME_QUAT, ng.FRAME_COS])
+@pytest.mark.parametrize("norm_mode", [ng.NORM_APPROX, ng.NORM_NONE, ng.NORM_EXACT])
+@pytest.mark.parametrize("act_mode", [ng.ACT_RAW, ng.ACT_IDENTITY])
+def test_backward_matches_central_differences(frame_mode, norm_mode, act_mode):
+    n, L = 64, 3
+    params, c0, means, cam, g_rgb = _fd_case(frame_mode, act_mode, n, L, seed=11)
+    g_p, g_c0, g_mu = ng.backward(params, c0, means, cam, g_rgb, L, frame_mode, norm_mode, act_mode)
+    args = (L, frame_mode, norm_mode, act_mode)
+    P = params.shape[0]
+    for p in range(P):
+        for l in range(L):
+            idx = np.arange(n) * L + l
+            h = 1e-6 * np.maximum(1.0, np.abs(params[p, idx]))
+            pp, pm = params.copy(), params.copy()
+            pp[p, idx] += h
+            pm[p, idx] -= h
+            fd = (_per_prim_loss(pp, c0, means, cam, g_rgb, *args)
+                  - _per_prim_loss(pm, c0, means, cam, g_rgb, *args)) / (2 * h)
+            an = g_p[p, idx]
+            _assert_fd(an, fd, (p, l))
+    for c in range(3):
+        h = 1e-6
+        mp, mm = means.astype(np.float64).copy(), means.astype(np.float64).copy()
+        mp[:, c] += h
+        mm[:, c] -= h
+        fd = (_per_prim_loss(params, c0, mp, cam, g_rgb, *args)
+              - _per_prim_loss(params, c0, mm, cam, g_rgb, *args)) / (2 * h)
+        _assert_fd(g_mu[:, c], fd, c)
+    np.testing.assert_array_equal(g_c0, g_rgb.T)
+
+
+def test_normalisation_lambda_derivative_sign():
+    """Reading R4: dC^-1/dlam at lam = 0.7, a = 0.4 is 0.13542 (finite differences);
+    the printed '+' numerator would give 0.36449."""
+    lam, a, h = 0.7, 0.4, 1e-6
+    fd = (ng.norm_approx(lam + h, a) - ng.norm_approx(lam - h, a)) / (2 * h)
+    d = np.array([[0.0, 0.0, 1.0]])
+    _, par = ng.lobe(d, np.array([[1.0, 0, 0]]), d, np.array([lam]), np.array([a]), np.array([0.0]),
+                     ng.NORM_APPROX, True)
+    # at d = z (pole, tau := 0, h = 1) dG/dlam = dC^-1/dlam
+    assert abs(par["lam"][0] - fd) < 1e-8
+    assert abs(fd - 0.13542) < 1e-5
+    em = math.exp(-2 * lam)
+    printed = (math.sqrt(1 + a) * (1 - em) + 2 * lam * math.sqrt(1 + a) * em) / (2 * math.pi * (1 - em) ** 2)
+    assert abs(printed - 0.36449) < 1e-5
+
+
+def test_sharp_lobe_derivatives():
+    """Derivatives stay consistent with finite differences at sharpness up to 1e3."""
+    n, L = 32, 2
+    params, c0, means, cam, g_rgb = _fd_case(ng.FRAME_QUAT, ng.ACT_IDENTITY, n, L, seed=5, lam_hi=1000.0)
+    args = (L, ng.FRAME_QUAT, ng.NORM_APPROX, ng.ACT_IDENTITY)
+    # aim lobe 0 of every primitive close to its view direction so that G is not negligible
+    d, _ = ng.view_directions(means, cam)
+    for i in range(n):
+        zt = d[i] + 0.01 * np.random.default_rng(i).standard_normal(3)
+        zt /= np.linalg.norm(zt)
+        q = Rotation.align_vectors([zt], [[0, 0, 1]])[0].as_quat()
+        params[0:4, i * L] = [q[3], q[0], q[1], q[2]]
+    g_p = ng.backward(params, c0, means, cam, g_rgb, *args)[0]
+    assert np.isfinite(g_p).all()
+    for p in range(10):
+        idx = np.arange(n) * L
+        # the naive FP64 lobe carries ~2 lam 1e-16 relative noise, so the step is not tiny
+        h = 1e-5 * np.maximum(np.abs(params[p, idx]), 1e-2)
+        pp, pm = params.copy(), params.copy()
+        pp[p, idx] += h
+        pm[p, idx] -= h
+        fd = (_per_prim_loss(pp, c0, means, cam, g_rgb, *args) - _per_prim_loss(pm, c0, means, cam, g_rgb, *args)) / (2 * h)
+        _assert_fd(g_p[p, idx], fd, p, rtol=1e-5, atol_frac=1e-7)
