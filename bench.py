@@ -1,0 +1,490 @@
+#!/usr/bin/env python3
+"""Throughput of the NASGabor appearance path on GB300: primitives*lobes/s.
+
+Headline step: one fused forward+backward pass (given upstream dLoss/dRGB) of
+the NASGabor appearance model over N = 1,000,000 primitives with L = 8 lobes,
+parameters stored in BF16 (FP32 math), QUAT frames, approximate normalisation,
+on synthetic primitives (seeded; unit-cube positions, one camera at (0,0,3)).
+One step = one launch of the fused kernel. value = N*L*steps / time.
+
+Side measurements in the same JSON line ("paths"): the plain FP32 path
+(separate forward and backward kernels), the FP32 fused kernel and the SH
+degree-3 comparison kernels at the same N and view directions, each with its
+kernels' HBM roofline fraction.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank times its own shard of the same size (weak scaling,
+no collective on the data path); the timing is max-reduced over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_PRIMS = 1_000_000
+N_LOBES = 8
+SEED = 1002
+METRIC = "primitives*lobes/s fwd+bwd (fused BF16-parameter NASGabor)"
+UNIT = "primitive-lobes/s"
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic bytes per primitive (QUAT, P = 10 raw scalars per lobe):
+#   fused BF16 fwd+bwd: per lobe 20 B params read + 40 B f32 gradients written;
+#     per primitive mu 12 + c0 6 + g_rgb 12 read, rgb 12 + g_c0 12 + g_mu 12 written.
+#   fused FP32 fwd+bwd: per lobe 40 + 40; per primitive 12 + 12 + 12 + 12 + 12 + 12.
+#   plain FP32 fwd: per lobe 40; per primitive mu 12 + c0 12 + rgb 12.
+#   plain FP32 bwd: per lobe 40 + 40; per primitive mu 12 + g_rgb 12 + g_c0 12 + g_mu 12.
+#   SH-3 fwd: 48 coefficients * 4 B + mu 12 + rgb 12; SH-3 bwd: coefficients read
+#     (for dLoss/dmu) 192 + g_coeffs 192 + mu 12 + g_rgb 12 + g_mu 12.
+
+
+def bytes_fused_bf16(L):
+    return 60 * L + 66
+
+
+def bytes_fused_f32(L):
+    return 80 * L + 72
+
+
+def bytes_fwd_f32(L):
+    return 40 * L + 36
+
+
+def bytes_bwd_f32(L):
+    return 80 * L + 48
+
+
+BYTES_SH3_FWD = 216
+BYTES_SH3_BWD = 420
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("nasg_eval.cu", "nasg_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_09794_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the headline kernel from the committed ncu summary,
+    or None when the kernel source has changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "nasgabor_fused_bf16_fwd_bwd_1m_l8.md")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if line.startswith("- ") and ":" in line:
+                    k, v = line[2:].split(":", 1)
+                    kv[k.strip()] = v.strip().strip("`")
+        if kv.get("source_sha256_16") != kernel_source_hash():
+            return None
+        return int(float(kv["dram_bytes_per_launch"]))
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (host logic; tested with gloo on CPU)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def shard_seed(base_seed, rank):
+    """Every rank gets its own shard of the same size and distribution."""
+    return base_seed + 7919 * rank
+
+
+def reduce_max(value, world, device=None):
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.samples = []
+        self.proc = None
+        self.thread = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                self.samples.append((time.time(), float(parts[0]), float(parts[1]), parts[3:8]))
+            except ValueError:
+                continue
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        inside = [s for s in self.samples if t0 <= s[0] <= t1]
+        window = "timed"
+        if len(inside) < 3:
+            inside = [s for s in self.samples if s[0] <= t1]
+            window = "warmup+timed"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = set()
+        for s in inside:
+            for nm, v in zip(names, s[3][1:]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(s[1] for s in inside), "sm_max_mhz": max(s[2] for s in inside),
+                "reasons": sorted(reasons), "samples": len(inside), "window": window}
+
+
+def gpu_id_for_smi(local_rank):
+    """nvidia-smi -i argument for the device this rank runs on (its UUID when torch knows it)."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(local_rank).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[local_rank] if vis else str(local_rank)
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on a bounded sample
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_rate(target_s=12.0, max_n=100_000):
+    """Oracle forward+backward (BF16-dequantised parameters) on a seeded sample of
+    the headline workload, sized for about target_s of single-thread CPU work."""
+    try:
+        from threadpoolctl import threadpool_limits
+    except Exception:  # pragma: no cover - not in every image
+        threadpool_limits = None
+    import contextlib
+
+    import numpy as np
+
+    from oracle import nasgabor as ong
+    from paper_2606_09794_gb300 import inputs
+
+    ctx = threadpool_limits(limits=1) if threadpool_limits else contextlib.nullcontext()
+    L = N_LOBES
+
+    def run(n):
+        w = inputs.point_cloud_workload(n, L, SEED)
+        p = inputs.quantize_bf16(w.params)
+        c = inputs.quantize_bf16(w.c0)
+        t0 = time.perf_counter()
+        ong.forward(p, c, w.means, w.cam, L)
+        ong.backward(p, c, w.means, w.cam, w.g_rgb, L)
+        return time.perf_counter() - t0
+
+    with ctx:
+        probe_n = 2000
+        dt = run(probe_n)
+        n = int(min(max_n, max(probe_n, probe_n * target_s / max(dt, 1e-6))))
+        reps, total = 0, 0.0
+        while total < target_s or reps == 0:
+            total += run(n)
+            reps += 1
+    return {"value": n * L * reps / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} primitives x {L} lobes of the N=1e6 workload (seed {SEED}) x {reps} passes, "
+                      f"forward+backward in float64 numpy, one thread, {total:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    vals = []
+    per_step = float(os.environ.get("BENCH_ORACLE_TARGET_S", max(2.0, 20.0 / max(args.steps, 1))))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(target_s=min(2.0, per_step))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_rate(target_s=per_step))
+    wall = time.perf_counter() - t0
+    value = statistics.median(v["value"] for v in vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"NASGabor fwd+bwd, N={N_PRIMS}, L={N_LOBES}, QUAT, BF16-stored params "
+                               "(sampled per step)", "global_batch": N_PRIMS, "lobes": N_LOBES},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": vals[-1]["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU measurement
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-paths", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import numpy as np
+    import torch
+
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2606_09794_gb300 import binding as nb
+    from paper_2606_09794_gb300 import inputs
+
+    N, L = N_PRIMS, N_LOBES
+    w = inputs.point_cloud_workload(N, L, shard_seed(SEED, rank))
+    params = torch.from_numpy(w.params).to(dev).to(torch.bfloat16)
+    c0 = torch.from_numpy(w.c0).to(dev).to(torch.bfloat16)
+    means = torch.from_numpy(w.means).to(dev)
+    g_rgb = torch.from_numpy(w.g_rgb).to(dev)
+    cam = tuple(float(x) for x in w.cam)
+    out = (torch.empty((N, 3), device=dev), torch.empty(params.shape, device=dev, dtype=torch.float32),
+           torch.empty((3, N), device=dev), torch.empty((N, 3), device=dev))
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        nb.nasgabor_fused_fwd_bwd(params, c0, means, cam, g_rgb, L, out=out, stream=stream)
+
+    peak, peak_kind = load_peaks()
+    sampler = ClockSampler(gpu_id_for_smi(local_rank)) if rank == 0 else None
+    time.sleep(0.3)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.time()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize(dev)
+    t_wall1 = time.time()
+    barrier(world, dev)
+    ms_local = ev0.elapsed_time(ev1)
+    ms = reduce_max(ms_local, world, dev)
+    clocks = sampler.summary(t_wall0, t_wall1) if sampler else None
+    if sampler:
+        sampler.stop()
+
+    units = N * L * args.steps * world
+    value = units / (ms * 1e-3)
+    ms_per_step = ms / args.steps
+    alg_bytes = N * bytes_fused_bf16(L)
+    achieved = alg_bytes / (ms_local / args.steps * 1e-3) / 1e9
+    traffic = profiled_traffic()
+
+    # ---- end to end through the public API with host buffers -------------------
+    pin = dict(params=params.cpu().pin_memory(), c0=c0.cpu().pin_memory(), means=means.cpu().pin_memory(),
+               g_rgb=g_rgb.cpu().pin_memory())
+    host_out = tuple(torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in out)
+    dev_in = dict(params=torch.empty_like(params), c0=torch.empty_like(c0), means=torch.empty_like(means),
+                  g_rgb=torch.empty_like(g_rgb))
+    h2d = sum(t.numel() * t.element_size() for t in pin.values())
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+
+    def e2e_step():
+        for k in dev_in:
+            dev_in[k].copy_(pin[k], non_blocking=True)
+        nb.nasgabor_fused_fwd_bwd(dev_in["params"], dev_in["c0"], dev_in["means"], cam, dev_in["g_rgb"], L,
+                                  out=out, stream=stream)
+        for h, d in zip(host_out, out):
+            h.copy_(d, non_blocking=True)
+
+    e2e_steps = max(5, min(50, args.steps))
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = reduce_max(e0.elapsed_time(e1), world, dev)
+    e2e_value = N * L * e2e_steps * world / (e2e_ms * 1e-3)
+
+    paths = None
+    if rank == 0 and world == 1 and not args.no_paths:
+        paths = measure_paths(nb, inputs, w, params, dev, stream, peak)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"NASGabor fused fwd+bwd, N={N} primitives per GPU, L={L} lobes, QUAT "
+                                   "frames, BF16-stored params, FP32 math, approx. normalisation, "
+                                   "upstream dL/dRGB ~ N(0,1)",
+                       "global_batch": N * world, "lobes": L, "param_storage": "bf16",
+                       "parallelism": f"replicas x{world} (independent shards)",
+                       "l2": "no flush: inputs 190 MB + outputs 356 MB per step exceed the 129 MB L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "eval_kernel<QUAT, bf16, V=4, fwd+bwd>",
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": args.steps,
+            "cpu_baseline": cpu,
+            "paths": paths,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_paths(nb, inputs, w, params_bf16, dev, stream, peak, reps=200):
+    """Per-kernel CUDA-event timings of the comparison paths at the same N."""
+    import torch
+    N, L = w.n, w.n_lobes
+    cam = tuple(float(x) for x in w.cam)
+    p32 = torch.from_numpy(w.params).to(dev)
+    c32 = torch.from_numpy(w.c0).to(dev)
+    c16 = c32.to(torch.bfloat16)
+    means = torch.from_numpy(w.means).to(dev)
+    g = torch.from_numpy(w.g_rgb).to(dev)
+    rgb = torch.empty((N, 3), device=dev)
+    gp = torch.empty(p32.shape, device=dev)
+    gc = torch.empty((3, N), device=dev)
+    gm = torch.empty((N, 3), device=dev)
+    coeffs = torch.from_numpy(inputs.sh_coefficients(N, 3, SEED)).to(dev)
+    gco = torch.empty_like(coeffs)
+
+    kernels = {
+        "nasgabor_fwd_f32": (lambda: nb.nasgabor_eval_fwd(p32, c32, means, cam, L, rgb=rgb, stream=stream),
+                             N * bytes_fwd_f32(L)),
+        "nasgabor_bwd_f32": (lambda: nb.nasgabor_eval_bwd(p32, means, cam, g, L, g_params=gp, g_c0=gc,
+                                                          g_means=gm, stream=stream), N * bytes_bwd_f32(L)),
+        "nasgabor_fused_f32": (lambda: nb.nasgabor_fused_fwd_bwd(p32, c32, means, cam, g, L,
+                                                                 out=(rgb, gp, gc, gm), stream=stream),
+                               N * bytes_fused_f32(L)),
+        "nasgabor_fused_bf16": (lambda: nb.nasgabor_fused_fwd_bwd(params_bf16, c16, means, cam, g, L,
+                                                                  out=(rgb, gp, gc, gm), stream=stream),
+                                N * bytes_fused_bf16(L)),
+        "sh3_fwd_f32": (lambda: nb.sh_eval_fwd(coeffs, means, cam, 3, rgb=rgb, stream=stream), N * BYTES_SH3_FWD),
+        "sh3_bwd_f32": (lambda: nb.sh_eval_bwd(coeffs, means, cam, g, 3, g_coeffs=gco, g_means=gm,
+                                               stream=stream), N * BYTES_SH3_BWD),
+    }
+    res = {}
+    for name, (fn, nbytes) in kernels.items():
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / reps
+        gbs = nbytes / (us * 1e-6) / 1e9
+        res[name] = {"us": us, "alg_bytes": nbytes, "gbs": gbs, "frac": gbs / peak}
+    t_plain = res["nasgabor_fwd_f32"]["us"] + res["nasgabor_bwd_f32"]["us"]
+    t_sh = res["sh3_fwd_f32"]["us"] + res["sh3_bwd_f32"]["us"]
+    return {
+        "kernels": res,
+        "plain_f32_fwd_then_bwd": {"value": N * L / (t_plain * 1e-6), "unit": UNIT, "us": t_plain},
+        "fused_f32": {"value": N * L / (res["nasgabor_fused_f32"]["us"] * 1e-6), "unit": UNIT},
+        "fused_bf16": {"value": N * L / (res["nasgabor_fused_bf16"]["us"] * 1e-6), "unit": UNIT},
+        "sh3_fwd_then_bwd": {"value": N / (t_sh * 1e-6), "unit": "primitives/s",
+                             "value_basis_lobes": 16 * N / (t_sh * 1e-6), "us": t_sh},
+    }
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * nasgabor.h -- C ABI of libnasgabor.so: NASGabor appearance evaluation on GB300 (sm_103a).
+ *
+ * The library evaluates, for every primitive i, the view-dependent colour of
+ * the appearance model of "Beyond Spherical Harmonics" (arXiv 2606.09794,
+ * Sec. 3.2, eq:app_model)
+ *
+ *     f_C(d_i) = c0_i + sum_{l=1..L} w_il G(d_i; [x_il, y_il, z_il], lam_il, a_il, k_il)
+ *
+ * with G the Normalized Anisotropic Spherical Gabor lobe (Sec. 4.1 definition,
+ * normalised by the approximate constant of Supp. E/F), at the central-ray
+ * direction d_i = (mu_i - cam)/|mu_i - cam| (Sec. 4.2: one evaluation per
+ * primitive per frame), plus the matching backward pass (Supp. F derivatives,
+ * chained through the Supp. C activations) and the comparison real-SH model
+ * (Sec. 3.2, Spherical Harmonics).
+ *
+ * Conventions for every entry point:
+ *   - Device pointers live on the CUDA device current on the calling thread;
+ *     "host" pointers are read during the call only.
+ *   - The caller owns and allocates every buffer; no entry point allocates
+ *     device memory unless its comment says otherwise.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream). Arguments are validated on the host before any launch; a
+ *     rejected call launches nothing and returns a negative status.
+ *   - n == 0 (or n_idx == 0) is valid and launches nothing.
+ *   - No C++ exception crosses this boundary.
+ *
+ * Parameter layout ("planes"): a lobe has P raw scalars, P = 10 in QUAT frame
+ * mode (q_w q_x q_y q_z lam_r a_r k_r w_r w_g w_b) and P = 9 in COS frame mode
+ * (ct_r cp_r cpsi_r lam_r a_r k_r w_r w_g w_b; Supp. C). Parameters are stored
+ * plane-major, lobe-minor: element (plane p, primitive i, lobe l) sits at
+ * p*N*L + i*L + l. Diffuse colours c0 are planar [3][N]; means, colours and
+ * colour gradients are interleaved [N][3].
+ *
+ * Activations (Supp. C table; act_mode RAW): lam = exp(lam_r), a = exp(a_r),
+ * k = 20 (tanh(k_r) + 1), w = tanh(w_r), COS cosines c = tanh(r). In act_mode
+ * IDENTITY the stored values are the activated quantities themselves.
+ */
+#ifndef NASGABOR_H_
+#define NASGABOR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t nasg_status;
+#define NASG_OK               0
+#define NASG_ERR_NULL        -1  /* a required pointer is NULL                         */
+#define NASG_ERR_RANGE       -2  /* a size, count or mode is out of range              */
+#define NASG_ERR_ALIGN       -3  /* a pointer is not aligned to its element type       */
+#define NASG_ERR_UNSUPPORTED -4  /* valid but not built (e.g. an unsupported mode mix) */
+#define NASG_ERR_CUDA        -5  /* a CUDA runtime call or launch failed               */
+#define NASG_ERR_DEVICE      -6  /* no usable CUDA device                              */
+
+#define NASG_FRAME_QUAT 0   /* frame from a quaternion (4 raw scalars)              */
+#define NASG_FRAME_COS  1   /* frame from three cosines (Supp. C parameterisation)  */
+
+#define NASG_DTYPE_F32  0   /* parameters stored as float32                         */
+#define NASG_DTYPE_BF16 1   /* parameters stored as bfloat16 (math stays float32)   */
+
+#define NASG_NORM_APPROX 0  /* C^-1 = lam sqrt(1+a) / (2 pi (1 - e^{-2 lam})) (Sec. 4.1, used for all results) */
+#define NASG_NORM_NONE   1  /* the unnormalised Sec. 4.1 kernel (G(z) = 1)          */
+
+#define NASG_ACT_RAW      0 /* stored values are raw; Supp. C activations applied   */
+#define NASG_ACT_IDENTITY 1 /* stored values are the activated quantities           */
+
+#define NASG_MAX_LOBES 32
+
+/* Shape and mode of one parameter set. */
+typedef struct nasg_desc {
+  int64_t n;            /* number of primitives N (>= 0)                              */
+  int32_t n_lobes;      /* lobes per primitive L, 1..NASG_MAX_LOBES                   */
+  int32_t frame_mode;   /* NASG_FRAME_*                                                */
+  int32_t param_dtype;  /* NASG_DTYPE_* of `params` and `c0`                           */
+  int32_t norm_mode;    /* NASG_NORM_*                                                 */
+  int32_t act_mode;     /* NASG_ACT_*                                                  */
+  int32_t accumulate;   /* backward outputs: 0 overwrite, 1 add into (g += ...)        */
+} nasg_desc;
+
+/* Raw scalars per lobe for a frame mode: 10 (QUAT) or 9 (COS); -1 if invalid. */
+int32_t nasg_lobe_planes(int32_t frame_mode);
+
+/* Static description of a status code (never NULL). */
+const char* nasg_status_string(nasg_status status);
+
+/* The cudaError_t of the most recent failed CUDA call made by this library on
+ * the calling thread (0 if none); reading it does not clear it. */
+int32_t nasg_last_cuda_error(void);
+
+/* ABI version of this header (bumped on any incompatible change). */
+#define NASG_ABI_VERSION 1
+int32_t nasg_abi_version(void);
+
+/*
+ * Forward pass (eq:app_model with the Sec. 4.1 / Supp. F lobe):
+ *   rgb[i][c] = c0[c][i] + sum_l w_il[c] G_il(d_i),  d_i = normalize(means[i] - cam).
+ *
+ * params  device, [P][N*L] of desc->param_dtype (f32 or bf16)
+ * c0      device, [3][N] of desc->param_dtype
+ * means   device, [N][3] f32
+ * cam     HOST, 3 f32 (camera centre)
+ * idx     device, nullable: evaluate only primitives idx[0..n_idx) (each in
+ *         [0, N)); rgb rows of other primitives are left untouched. NULL
+ *         evaluates every primitive (n_idx ignored).
+ * rgb     device, [N][3] f32 output
+ * Errors: NASG_ERR_NULL (params/c0/means/cam/rgb NULL), NASG_ERR_RANGE (bad
+ * desc fields, n_idx < 0), NASG_ERR_ALIGN (misaligned element pointers),
+ * NASG_ERR_CUDA (launch failure).
+ */
+nasg_status nasgabor_eval_fwd(const nasg_desc* desc, const void* params, const void* c0,
+                              const float* means, const float* cam, const int32_t* idx,
+                              int64_t n_idx, float* rgb, void* stream);
+
+/*
+ * Backward pass (Supp. F derivatives, recomputed from the inputs; nothing is
+ * saved by the forward): for the upstream gradient g_rgb = dLoss/drgb,
+ *   g_params = dLoss/d(raw params) [P][N*L] f32, g_c0 = dLoss/dc0 [3][N] f32,
+ *   g_means  = dLoss/dmeans [N][3] f32 (through d = normalize(mu - cam)).
+ * g_means may be NULL (not computed). With desc->accumulate = 1 the results are
+ * added into the outputs. With idx, only the listed primitives' entries are
+ * written. Same errors as the forward; g_rgb, g_params, g_c0 must be non-NULL.
+ */
+nasg_status nasgabor_eval_bwd(const nasg_desc* desc, const void* params, const float* means,
+                              const float* cam, const int32_t* idx, int64_t n_idx,
+                              const float* g_rgb, float* g_params, float* g_c0, float* g_means,
+                              void* stream);
+
+/*
+ * Forward and backward in one pass over the parameters, for a given upstream
+ * gradient: writes rgb as nasgabor_eval_fwd and the gradients as
+ * nasgabor_eval_bwd, reading params, c0, means and g_rgb once. Every primitive
+ * is processed (no index list). g_means may be NULL.
+ */
+nasg_status nasgabor_fused_fwd_bwd(const nasg_desc* desc, const void* params, const void* c0,
+                                   const float* means, const float* cam, const float* g_rgb,
+                                   float* rgb, float* g_params, float* g_c0, float* g_means,
+                                   void* stream);
+
+/*
+ * Real spherical harmonics of degree 0..3 (Sec. 3.2): orthonormal real basis
+ * with the Condon-Shortley phase, coefficient j = l^2 + l + m (m = -l..l).
+ *   rgb[i][c] = sum_j coeffs[j][c][i] Y_j(d_i),  d_i = normalize(means[i] - cam).
+ * coeffs device [(degree+1)^2][3][N] f32, means device [N][3] f32, cam HOST 3 f32,
+ * rgb device [N][3] f32. No offset and no clamp are applied.
+ */
+nasg_status sh_eval_fwd(int32_t degree, int64_t n, const float* coeffs, const float* means,
+                        const float* cam, float* rgb, void* stream);
+
+/* Backward of sh_eval_fwd: g_coeffs [(degree+1)^2][3][N] f32 (overwritten) and
+ * g_means [N][3] f32 (nullable, overwritten). */
+nasg_status sh_eval_bwd(int32_t degree, int64_t n, const float* coeffs, const float* means,
+                        const float* cam, const float* g_rgb, float* g_coeffs, float* g_means,
+                        void* stream);
+
+#ifdef __cplusplus
+}  /* extern "C" */
+#endif
+
+#endif  /* NASGABOR_H_ */

@@ -6,15 +6,12 @@ wrapper (ctypes marshalling of torch CUDA tensors) and ``inputs`` holds the
 seeded synthetic workloads. Importing the package does not load the library;
 ``binding`` loads it on import and raises if it is missing.
 """
+import importlib
 
 __all__ = ["binding", "inputs"]
 
 
 def __getattr__(name):
-    if name == "binding":
-        from . import binding
-        return binding
-    if name == "inputs":
-        from . import inputs
-        return inputs
+    if name in __all__:
+        return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)

@@ -1,0 +1,259 @@
+"""Thin Python binding of libnasgabor.so (C ABI in include/nasgabor.h).
+
+Argument marshalling only: every step of the computation runs in the
+library's CUDA kernels. torch supplies device memory and the current CUDA
+stream; tensors are passed to the C ABI as raw pointers. Importing this module
+loads the library and raises ImportError if it has not been built (there is no
+fallback path).
+
+Function names mirror the C entry points. Outputs are allocated here with
+torch when the caller does not pass them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnasgabor.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python -m paper_2606_09794_gb300.build` "
+                      "(or __graft_entry__.build()) first")
+lib = ctypes.CDLL(LIB_PATH)
+
+FRAME = {"quat": 0, "cos": 1}
+NORM = {"approx": 0, "none": 1}
+ACT = {"raw": 0, "identity": 1}
+PLANES = {"quat": 10, "cos": 9}
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+
+class NasgDesc(ctypes.Structure):
+    _fields_ = [("n", _i64), ("n_lobes", _i32), ("frame_mode", _i32), ("param_dtype", _i32),
+                ("norm_mode", _i32), ("act_mode", _i32), ("accumulate", _i32)]
+
+
+def _decl(name, argtypes, restype=_i32):
+    fn = getattr(lib, name)
+    fn.argtypes = argtypes
+    fn.restype = restype
+    return fn
+
+
+_P = ctypes.POINTER
+_decl("nasg_lobe_planes", [_i32])
+_decl("nasg_status_string", [_i32], ctypes.c_char_p)
+_decl("nasg_last_cuda_error", [])
+_decl("nasg_abi_version", [])
+_decl("nasgabor_eval_fwd", [_P(NasgDesc), _vp, _vp, _vp, _P(ctypes.c_float), _vp, _i64, _vp, _vp])
+_decl("nasgabor_eval_bwd", [_P(NasgDesc), _vp, _vp, _P(ctypes.c_float), _vp, _i64, _vp, _vp, _vp, _vp, _vp])
+_decl("nasgabor_fused_fwd_bwd", [_P(NasgDesc), _vp, _vp, _vp, _P(ctypes.c_float), _vp, _vp, _vp, _vp, _vp, _vp])
+_decl("sh_eval_fwd", [_i32, _i64, _vp, _vp, _P(ctypes.c_float), _vp, _vp])
+_decl("sh_eval_bwd", [_i32, _i64, _vp, _vp, _P(ctypes.c_float), _vp, _vp, _vp, _vp])
+
+
+class NasgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib.nasg_status_string(status).decode()
+        extra = ""
+        if status == -5:
+            extra = f" (cudaError {lib.nasg_last_cuda_error()})"
+        super().__init__(f"{where}: status {status}: {msg}{extra}")
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise NasgError(status, where)
+
+
+def _ptr(t):
+    return None if t is None else _vp(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return _vp(s.cuda_stream)
+
+
+def _cam(cam):
+    if isinstance(cam, torch.Tensor):
+        cam = cam.detach().to("cpu", torch.float32).reshape(-1).tolist()
+    vals = [float(c) for c in cam]
+    if len(vals) != 3:
+        raise ValueError("cam must have 3 components")
+    return (ctypes.c_float * 3)(*vals)
+
+
+def _cuda(t, name, dtype=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _param_dtype(t):
+    if t.dtype == torch.float32:
+        return 0
+    if t.dtype == torch.bfloat16:
+        return 1
+    raise TypeError("params must be float32 or bfloat16")
+
+
+def make_desc(n, n_lobes, frame_mode="quat", param_dtype=torch.float32, norm_mode="approx", act_mode="raw",
+              accumulate=False) -> NasgDesc:
+    return NasgDesc(int(n), int(n_lobes), FRAME[frame_mode], 1 if param_dtype == torch.bfloat16 else 0,
+                    NORM[norm_mode], ACT[act_mode], 1 if accumulate else 0)
+
+
+def lobe_planes(frame_mode="quat") -> int:
+    return int(lib.nasg_lobe_planes(FRAME[frame_mode]))
+
+
+def nasgabor_eval_fwd(params, c0, means, cam, n_lobes, frame_mode="quat", norm_mode="approx",
+                      act_mode="raw", idx=None, rgb=None, stream=None):
+    """rgb [N, 3] = c0 + sum_l w_l G_l(d) at d = normalize(means - cam); see include/nasgabor.h."""
+    _cuda(params, "params")
+    _cuda(c0, "c0", params.dtype)
+    _cuda(means, "means", torch.float32)
+    n = means.shape[0]
+    if rgb is None:
+        rgb = torch.empty((n, 3), device=means.device, dtype=torch.float32)
+    _cuda(rgb, "rgb", torch.float32)
+    if idx is not None:
+        _cuda(idx, "idx", torch.int32)
+    desc = make_desc(n, n_lobes, frame_mode, params.dtype, norm_mode, act_mode)
+    _param_dtype(params)
+    _check(lib.nasgabor_eval_fwd(ctypes.byref(desc), _ptr(params), _ptr(c0), _ptr(means), _cam(cam),
+                                 _ptr(idx), 0 if idx is None else idx.numel(), _ptr(rgb), _stream(stream)),
+           "nasgabor_eval_fwd")
+    return rgb
+
+
+def nasgabor_eval_bwd(params, means, cam, g_rgb, n_lobes, frame_mode="quat", norm_mode="approx",
+                      act_mode="raw", idx=None, g_params=None, g_c0=None, g_means=None, want_means=True,
+                      accumulate=False, stream=None):
+    """(g_params [P, N*L] f32, g_c0 [3, N] f32, g_means [N, 3] f32 or None); see include/nasgabor.h."""
+    _cuda(params, "params")
+    _cuda(means, "means", torch.float32)
+    _cuda(g_rgb, "g_rgb", torch.float32)
+    n = means.shape[0]
+    dev = means.device
+    if g_params is None:
+        g_params = torch.empty(params.shape, device=dev, dtype=torch.float32)
+    if g_c0 is None:
+        g_c0 = torch.empty((3, n), device=dev, dtype=torch.float32)
+    if g_means is None and want_means:
+        g_means = torch.empty((n, 3), device=dev, dtype=torch.float32)
+    for t, nm in ((g_params, "g_params"), (g_c0, "g_c0")):
+        _cuda(t, nm, torch.float32)
+    if g_means is not None:
+        _cuda(g_means, "g_means", torch.float32)
+    if idx is not None:
+        _cuda(idx, "idx", torch.int32)
+    desc = make_desc(n, n_lobes, frame_mode, params.dtype, norm_mode, act_mode, accumulate)
+    _param_dtype(params)
+    _check(lib.nasgabor_eval_bwd(ctypes.byref(desc), _ptr(params), _ptr(means), _cam(cam), _ptr(idx),
+                                 0 if idx is None else idx.numel(), _ptr(g_rgb), _ptr(g_params), _ptr(g_c0),
+                                 _ptr(g_means), _stream(stream)), "nasgabor_eval_bwd")
+    return g_params, g_c0, g_means
+
+
+def nasgabor_fused_fwd_bwd(params, c0, means, cam, g_rgb, n_lobes, frame_mode="quat", norm_mode="approx",
+                           act_mode="raw", out=None, want_means=True, stream=None):
+    """One pass: (rgb, g_params, g_c0, g_means) for a given upstream gradient g_rgb."""
+    _cuda(params, "params")
+    _cuda(c0, "c0", params.dtype)
+    _cuda(means, "means", torch.float32)
+    _cuda(g_rgb, "g_rgb", torch.float32)
+    n = means.shape[0]
+    dev = means.device
+    if out is None:
+        out = (torch.empty((n, 3), device=dev, dtype=torch.float32),
+               torch.empty(params.shape, device=dev, dtype=torch.float32),
+               torch.empty((3, n), device=dev, dtype=torch.float32),
+               torch.empty((n, 3), device=dev, dtype=torch.float32) if want_means else None)
+    rgb, g_params, g_c0, g_means = out
+    desc = make_desc(n, n_lobes, frame_mode, params.dtype, norm_mode, act_mode)
+    _param_dtype(params)
+    _check(lib.nasgabor_fused_fwd_bwd(ctypes.byref(desc), _ptr(params), _ptr(c0), _ptr(means), _cam(cam),
+                                      _ptr(g_rgb), _ptr(rgb), _ptr(g_params), _ptr(g_c0), _ptr(g_means),
+                                      _stream(stream)), "nasgabor_fused_fwd_bwd")
+    return rgb, g_params, g_c0, g_means
+
+
+def sh_eval_fwd(coeffs, means, cam, degree=3, rgb=None, stream=None):
+    _cuda(coeffs, "coeffs", torch.float32)
+    _cuda(means, "means", torch.float32)
+    n = means.shape[0]
+    if rgb is None:
+        rgb = torch.empty((n, 3), device=means.device, dtype=torch.float32)
+    _check(lib.sh_eval_fwd(degree, n, _ptr(coeffs), _ptr(means), _cam(cam), _ptr(rgb), _stream(stream)),
+           "sh_eval_fwd")
+    return rgb
+
+
+def sh_eval_bwd(coeffs, means, cam, g_rgb, degree=3, g_coeffs=None, g_means=None, want_means=True,
+                stream=None):
+    _cuda(coeffs, "coeffs", torch.float32)
+    _cuda(means, "means", torch.float32)
+    _cuda(g_rgb, "g_rgb", torch.float32)
+    n = means.shape[0]
+    if g_coeffs is None:
+        g_coeffs = torch.empty_like(coeffs)
+    if g_means is None and want_means:
+        g_means = torch.empty((n, 3), device=means.device, dtype=torch.float32)
+    _check(lib.sh_eval_bwd(degree, n, _ptr(coeffs), _ptr(means), _cam(cam), _ptr(g_rgb), _ptr(g_coeffs),
+                           _ptr(g_means), _stream(stream)), "sh_eval_bwd")
+    return g_coeffs, g_means
+
+
+# ---------------------------------------------------------------------------
+# autograd: the backward recomputes from the saved inputs (nothing else saved)
+# ---------------------------------------------------------------------------
+
+class NasgEval(torch.autograd.Function):
+    """rgb = NasgEval.apply(params, c0, means, cam, n_lobes, frame_mode, norm_mode, act_mode)."""
+
+    @staticmethod
+    def forward(ctx, params, c0, means, cam, n_lobes, frame_mode="quat", norm_mode="approx", act_mode="raw"):
+        cam_t = tuple(float(c) for c in (cam.tolist() if isinstance(cam, torch.Tensor) else cam))
+        ctx.save_for_backward(params, means)
+        ctx.cfg = (cam_t, n_lobes, frame_mode, norm_mode, act_mode)
+        return nasgabor_eval_fwd(params, c0, means, cam_t, n_lobes, frame_mode, norm_mode, act_mode)
+
+    @staticmethod
+    def backward(ctx, g_rgb):
+        params, means = ctx.saved_tensors
+        cam_t, n_lobes, frame_mode, norm_mode, act_mode = ctx.cfg
+        g_params, g_c0, g_means = nasgabor_eval_bwd(params, means, cam_t, g_rgb.contiguous(), n_lobes,
+                                                    frame_mode, norm_mode, act_mode,
+                                                    want_means=ctx.needs_input_grad[2])
+        return (g_params.to(params.dtype), g_c0.to(params.dtype), g_means, None, None, None, None, None)
+
+
+class ShEval(torch.autograd.Function):
+    """rgb = ShEval.apply(coeffs, means, cam, degree)."""
+
+    @staticmethod
+    def forward(ctx, coeffs, means, cam, degree=3):
+        cam_t = tuple(float(c) for c in (cam.tolist() if isinstance(cam, torch.Tensor) else cam))
+        ctx.save_for_backward(coeffs, means)
+        ctx.cfg = (cam_t, degree)
+        return sh_eval_fwd(coeffs, means, cam_t, degree)
+
+    @staticmethod
+    def backward(ctx, g_rgb):
+        coeffs, means = ctx.saved_tensors
+        cam_t, degree = ctx.cfg
+        g_coeffs, g_means = sh_eval_bwd(coeffs, means, cam_t, g_rgb.contiguous(), degree,
+                                        want_means=ctx.needs_input_grad[1])
+        return g_coeffs, g_means, None, None

@@ -1,0 +1,48 @@
+// Library-wide C ABI helpers: status strings, ABI version, CUDA error record,
+// device properties cache.
+#include <cuda_runtime.h>
+
+#include "nasg_host.h"
+
+namespace nasg {
+
+static thread_local int32_t g_last_cuda_error = 0;
+
+void record_cuda_error(cudaError_t e) { g_last_cuda_error = static_cast<int32_t>(e); }
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+}  // namespace nasg
+
+extern "C" int32_t nasg_lobe_planes(int32_t frame_mode) {
+  if (frame_mode == NASG_FRAME_QUAT) return 10;
+  if (frame_mode == NASG_FRAME_COS) return 9;
+  return -1;
+}
+
+extern "C" const char* nasg_status_string(nasg_status status) {
+  switch (status) {
+    case NASG_OK: return "ok";
+    case NASG_ERR_NULL: return "a required pointer is NULL";
+    case NASG_ERR_RANGE: return "a size, count or mode is out of range";
+    case NASG_ERR_ALIGN: return "a pointer is misaligned for its element type";
+    case NASG_ERR_UNSUPPORTED: return "unsupported combination of modes";
+    case NASG_ERR_CUDA: return "a CUDA call or kernel launch failed";
+    case NASG_ERR_DEVICE: return "no usable CUDA device";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int32_t nasg_last_cuda_error(void) { return nasg::g_last_cuda_error; }
+
+extern "C" int32_t nasg_abi_version(void) { return NASG_ABI_VERSION; }

@@ -76,8 +76,11 @@ class Workload:
         return lobe_planes(self.frame_mode)
 
 
-def _draw_lobes(st, count: int, frame_mode: str, k_max: float = 8.0):
-    """Raw lobe parameters for `count` lobes, drawn by inverse transform."""
+def _draw_lobes(st, count: int, frame_mode: str, k_max: float = 8.0, activated: bool = False):
+    """Raw lobe parameters for `count` lobes, drawn by inverse transform.
+
+    With activated=True the stored values are the activated quantities
+    themselves (lam, a, k, w, and the frame cosines in COS mode)."""
     if frame_mode == FRAME_QUAT:
         q = st["quat"].standard_normal((count, 4))
         q /= np.linalg.norm(q, axis=1, keepdims=True)
@@ -88,7 +91,10 @@ def _draw_lobes(st, count: int, frame_mode: str, k_max: float = 8.0):
         # tanh(raw) reproduces the cosine. Angles are kept off the ends so
         # the raw values stay finite.
         ang = st["quat"].uniform(0.02, math.pi - 0.02, size=(count, 3))
-        frame = [np.arctanh(np.cos(ang[:, j])) for j in range(3)]
+        if activated:
+            frame = [np.cos(ang[:, j]) for j in range(3)]
+        else:
+            frame = [np.arctanh(np.cos(ang[:, j])) for j in range(3)]
     lam = np.exp(st["lam"].uniform(0.0, math.log(1e3), size=count))
     lam_r = np.log(lam)
     a = np.maximum(st["a"].uniform(0.0, 1.0, size=count), _A_MIN)
@@ -98,12 +104,15 @@ def _draw_lobes(st, count: int, frame_mode: str, k_max: float = 8.0):
     phase = st["phase"].uniform(0.0, 2.0 * math.pi, size=count)
     w = np.minimum(st["w"].uniform(0.0, 1.0, size=(count, 3)), _W_MAX)
     w_r = np.arctanh(w)
-    planes = frame + [lam_r, a_r, k_r, w_r[:, 0], w_r[:, 1], w_r[:, 2]]
+    if activated:
+        planes = frame + [lam, a, k, w[:, 0], w[:, 1], w[:, 2]]
+    else:
+        planes = frame + [lam_r, a_r, k_r, w_r[:, 0], w_r[:, 1], w_r[:, 2]]
     return np.stack(planes).astype(np.float32), phase.astype(np.float32)
 
 
 def point_cloud_workload(n: int, n_lobes: int, seed: int, frame_mode: str = FRAME_QUAT,
-                         with_upstream: bool = True) -> Workload:
+                         with_upstream: bool = True, activated: bool = False) -> Workload:
     """Primitives uniform in the unit cube seen from one camera at (0, 0, 3).
 
     This is the small parity workload (N=4096, L=4) and the single-scene
@@ -112,7 +121,7 @@ def point_cloud_workload(n: int, n_lobes: int, seed: int, frame_mode: str = FRAM
     """
     st = _streams(seed)
     means = st["positions"].uniform(0.0, 1.0, size=(n, 3)).astype(np.float32)
-    params, phase = _draw_lobes(st, n * n_lobes, frame_mode)
+    params, phase = _draw_lobes(st, n * n_lobes, frame_mode, activated=activated)
     c0 = st["c0"].uniform(0.0, 1.0, size=(3, n)).astype(np.float32)
     g_rgb = st["upstream"].standard_normal((n, 3)).astype(np.float32) if with_upstream else None
     cam = np.array([0.0, 0.0, 3.0], dtype=np.float32)

@@ -1,0 +1,228 @@
+"""GPU parity of the NASGabor kernels (through the C ABI) against the FP64 oracle.
+
+Colours: |c_gpu - c_oracle| <= base + 4 nu per output (nu = oracle sensitivity
+floor, tests/_parity.py), base 1e-5 for FP32 parameters and 4e-3 for BF16
+parameters (oracle fed the dequantised values). Gradients: relative L2 error
+<= 1e-4 per parameter plane, for c0 and for the means.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import nasgabor as ong
+from paper_2606_09794_gb300 import inputs
+from tests._parity import colour_report, rel_l2, sensitivity_floor
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-4
+
+
+def _dev(x, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    return t if dtype is None else t.to(dtype)
+
+
+def _prepare(w, bf16):
+    """Device tensors and the float32 values the kernel reads (dequantised for BF16)."""
+    import torch
+    if bf16:
+        pq = inputs.quantize_bf16(w.params)
+        cq = inputs.quantize_bf16(w.c0)
+        return (_dev(w.params).to(torch.bfloat16), _dev(w.c0).to(torch.bfloat16), pq, cq)
+    return _dev(w.params), _dev(w.c0), w.params, w.c0
+
+
+def _check_forward(lib, w, bf16, norm="approx", act="raw", base=None):
+    import torch
+    params, c0, p_np, c0_np = _prepare(w, bf16)
+    means = _dev(w.means)
+    rgb = lib.nasgabor_eval_fwd(params, c0, means, w.cam, w.n_lobes, w.frame_mode, norm, act)
+    torch.cuda.synchronize()
+    gpu = rgb.cpu().numpy()
+    assert np.isfinite(gpu).all()
+
+    def fwd(p, c, m, cam):
+        return ong.forward(p, c, m, cam, w.n_lobes, w.frame_mode, norm, act)
+
+    ref, nu = sensitivity_floor(fwd, (p_np, c0_np, w.means, w.cam), (0, 1, 2, 3))
+    rep = colour_report(gpu, ref, nu, base if base is not None else (4e-3 if bf16 else 1e-5))
+    assert rep["violations"] == 0, rep
+    return rep
+
+
+def _check_backward(lib, w, bf16, norm="approx", act="raw"):
+    import torch
+    params, c0, p_np, c0_np = _prepare(w, bf16)
+    means = _dev(w.means)
+    g_rgb = _dev(w.g_rgb)
+    g_p, g_c0, g_mu = lib.nasgabor_eval_bwd(params, means, w.cam, g_rgb, w.n_lobes, w.frame_mode, norm, act)
+    torch.cuda.synchronize()
+    r_p, r_c0, r_mu = ong.backward(p_np, c0_np, w.means, w.cam, w.g_rgb, w.n_lobes, w.frame_mode, norm, act)
+    g_p = g_p.cpu().numpy()
+    assert np.isfinite(g_p).all()
+    errs = [rel_l2(g_p[p], r_p[p]) for p in range(g_p.shape[0])]
+    assert max(errs) <= GRAD_TOL, errs
+    np.testing.assert_array_equal(g_c0.cpu().numpy(), w.g_rgb.T)
+    assert rel_l2(g_mu.cpu().numpy(), r_mu) <= GRAD_TOL
+    return errs
+
+
+CASES = [
+    # frame, N, L, bf16, norm, act, seed
+    ("quat", 4096, 4, False, "approx", "raw", 1001),   # the small parity workload
+    ("quat", 1037, 8, False, "approx", "raw", 7),      # ragged tail, 4-lobe vector path
+    ("quat", 777, 3, False, "approx", "raw", 8),       # scalar path (L % 4 != 0)
+    ("quat", 301, 1, False, "approx", "raw", 9),
+    ("cos", 1029, 4, False, "approx", "raw", 10),
+    ("cos", 555, 5, False, "approx", "raw", 11),
+    ("quat", 600, 4, False, "none", "raw", 12),
+    ("quat", 513, 5, False, "approx", "identity", 13),
+    ("cos", 700, 4, False, "approx", "identity", 14),
+    ("quat", 4096, 8, True, "approx", "raw", 15),
+    ("cos", 999, 4, True, "approx", "raw", 16),
+    ("quat", 333, 3, True, "approx", "raw", 17),
+]
+
+
+@pytest.mark.parametrize("frame,n,L,bf16,norm,act,seed", CASES)
+def test_forward_parity(lib, frame, n, L, bf16, norm, act, seed):
+    w = inputs.point_cloud_workload(n, L, seed, frame, activated=(act == "identity"))
+    _check_forward(lib, w, bf16, norm, act)
+
+
+@pytest.mark.parametrize("frame,n,L,bf16,norm,act,seed", CASES)
+def test_backward_parity(lib, frame, n, L, bf16, norm, act, seed):
+    w = inputs.point_cloud_workload(n, L, seed, frame, activated=(act == "identity"))
+    _check_backward(lib, w, bf16, norm, act)
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_fused_equals_separate_passes(lib, bf16):
+    import torch
+    w = inputs.point_cloud_workload(2049, 8, 21)
+    params, c0, _, _ = _prepare(w, bf16)
+    means, g_rgb = _dev(w.means), _dev(w.g_rgb)
+    rgb = lib.nasgabor_eval_fwd(params, c0, means, w.cam, 8)
+    g = lib.nasgabor_eval_bwd(params, means, w.cam, g_rgb, 8)
+    f = lib.nasgabor_fused_fwd_bwd(params, c0, means, w.cam, g_rgb, 8)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(f[0], rgb, rtol=1e-6, atol=1e-6)
+    for a, b in zip(f[1:], g):
+        torch.testing.assert_close(a, b, rtol=1e-6, atol=1e-6)
+
+
+def test_index_list_and_accumulate(lib):
+    import torch
+    w = inputs.point_cloud_workload(1000, 4, 22)
+    params, c0 = _dev(w.params), _dev(w.c0)
+    means, g_rgb = _dev(w.means), _dev(w.g_rgb)
+    full = lib.nasgabor_eval_fwd(params, c0, means, w.cam, 4)
+    idx_np = np.sort(np.random.default_rng(3).choice(1000, 317, replace=False)).astype(np.int32)
+    idx = _dev(idx_np)
+    rgb = torch.full((1000, 3), -7.0, device="cuda")
+    lib.nasgabor_eval_fwd(params, c0, means, w.cam, 4, idx=idx, rgb=rgb)
+    gpu = rgb.cpu().numpy()
+    assert (gpu[np.setdiff1d(np.arange(1000), idx_np)] == -7.0).all()
+    np.testing.assert_array_equal(gpu[idx_np], full.cpu().numpy()[idx_np])
+    # backward with an index list touches only the listed primitives; accumulate adds
+    g1 = lib.nasgabor_eval_bwd(params, means, w.cam, g_rgb, 4)
+    gp = torch.zeros_like(g1[0])
+    gc = torch.zeros_like(g1[1])
+    gm = torch.zeros_like(g1[2])
+    lib.nasgabor_eval_bwd(params, means, w.cam, g_rgb, 4, idx=idx, g_params=gp, g_c0=gc, g_means=gm)
+    lib.nasgabor_eval_bwd(params, means, w.cam, g_rgb, 4, idx=idx, g_params=gp, g_c0=gc, g_means=gm,
+                          accumulate=True)
+    torch.cuda.synchronize()
+    lobes = (idx_np[:, None] * 4 + np.arange(4)).reshape(-1)
+    np.testing.assert_allclose(gp.cpu().numpy()[:, lobes], 2 * g1[0].cpu().numpy()[:, lobes], rtol=1e-6)
+    others = np.setdiff1d(np.arange(4000), lobes)
+    assert (gp.cpu().numpy()[:, others] == 0).all()
+    np.testing.assert_allclose(gm.cpu().numpy()[idx_np], 2 * g1[2].cpu().numpy()[idx_np], rtol=1e-6)
+
+
+def test_poles_and_near_poles(lib):
+    """Exact +-z view directions and directions 1e-3, 1e-5, 1e-7 rad from the axis."""
+    import torch
+    cam = np.array([0.0, 0.0, 3.0], dtype=np.float32)
+    angles = [0.0, 1e-3, 1e-5, 1e-7]
+    means = np.array([[2 * math.sin(e), 0.0, 3.0 - 2 * math.cos(e)] for e in angles], np.float32)
+    n = len(angles)
+    L = 2
+    # lobe 0: z = (0, 0, -1) (q = (0, 1, 0, 0)), looking along d: the u > 0 pole;
+    # lobe 1: z = (0, 0, 1) (identity quaternion): the u < 0 pole (G = 0)
+    p = np.zeros((10, n * L), np.float32)
+    p[1, 0::2] = 1.0
+    p[0, 1::2] = 1.0
+    p[4] = math.log(200.0)
+    p[5] = math.log(0.6)
+    p[6] = math.atanh(3.0 / 20 - 1)
+    p[7:10] = math.atanh(0.5)
+    c0 = np.full((3, n), 0.25, np.float32)
+    g_rgb = np.ones((n, 3), np.float32)
+    w = inputs.Workload(n, L, "quat", p, c0, means, cam, g_rgb, None)
+    rep = _check_forward(lib, w, False)
+    gpu = lib.nasgabor_eval_fwd(_dev(p), _dev(c0), _dev(means), cam, L).cpu().numpy()
+    cinv = 200 * math.sqrt(1.6) / (2 * math.pi * (1 - math.exp(-400)))
+    np.testing.assert_allclose(gpu[0], 0.25 + 0.5 * cinv, rtol=1e-6)
+    g_p, g_c0, g_mu = lib.nasgabor_eval_bwd(_dev(p), _dev(means), cam, _dev(g_rgb), L)
+    torch.cuda.synchronize()
+    assert np.isfinite(g_p.cpu().numpy()).all() and np.isfinite(g_mu.cpu().numpy()).all()
+    assert (g_p.cpu().numpy()[:, 1::2][:, 0] == 0).all()  # exact anti-pole: zero gradients
+    assert rep["violations"] == 0
+
+
+def test_large_workload_sampled(lib):
+    """N = 1e6, L = 8 (the single-scene throughput workload), FP32 and BF16, in the
+    launch configuration the benchmark times; the oracle checks a seeded sample."""
+    import torch
+    n, L = 1_000_000, 8
+    w = inputs.point_cloud_workload(n, L, 1002)
+    sample = inputs.subsample_indices(n, 20_000, 1)
+    for bf16 in (False, True):
+        params, c0, p_np, c0_np = _prepare(w, bf16)
+        means, g_rgb = _dev(w.means), _dev(w.g_rgb)
+        rgb, g_p, g_c0, g_mu = lib.nasgabor_fused_fwd_bwd(params, c0, means, w.cam, g_rgb, L)
+        torch.cuda.synchronize()
+        lobes = (sample[:, None] * L + np.arange(L)).reshape(-1)
+        ps, cs = p_np[:, lobes], c0_np[:, sample]
+        ms, gs = w.means[sample], w.g_rgb[sample]
+
+        def fwd(p, c, m, cam):
+            return ong.forward(p, c, m, cam, L)
+
+        ref, nu = sensitivity_floor(fwd, (ps, cs, ms, w.cam), (0, 1, 2, 3))
+        rep = colour_report(rgb.cpu().numpy()[sample], ref, nu, 4e-3 if bf16 else 1e-5)
+        assert rep["violations"] == 0, rep
+        r_p, _, r_mu = ong.backward(ps, cs, ms, w.cam, gs, L)
+        gp = g_p.cpu().numpy()[:, lobes]
+        errs = [rel_l2(gp[p], r_p[p]) for p in range(10)]
+        assert max(errs) <= GRAD_TOL, errs
+        assert rel_l2(g_mu.cpu().numpy()[sample], r_mu) <= GRAD_TOL
+        for t in (rgb, g_p, g_c0, g_mu):
+            assert torch.isfinite(t).all()
+
+
+def test_autograd_function(lib):
+    import torch
+    w = inputs.point_cloud_workload(1500, 4, 23)
+    params = _dev(w.params).requires_grad_(True)
+    c0 = _dev(w.c0).requires_grad_(True)
+    means = _dev(w.means).requires_grad_(True)
+    g = _dev(w.g_rgb)
+    rgb = lib.NasgEval.apply(params, c0, means, tuple(w.cam.tolist()), 4)
+    rgb.backward(g)
+    gp, gc, gm = lib.nasgabor_eval_bwd(params.detach(), means.detach(), w.cam, g, 4)
+    torch.testing.assert_close(params.grad, gp, rtol=0, atol=0)
+    torch.testing.assert_close(c0.grad, gc, rtol=0, atol=0)
+    torch.testing.assert_close(means.grad, gm, rtol=0, atol=0)
+
+
+def test_empty_problem(lib):
+    import torch
+    z = torch.zeros((10, 0), device="cuda")
+    out = lib.nasgabor_eval_fwd(z, torch.zeros((3, 0), device="cuda"), torch.zeros((0, 3), device="cuda"),
+                                (0, 0, 3), 4)
+    assert out.shape == (0, 3)
