@@ -155,6 +155,17 @@ nasg_status sh_eval_bwd(int32_t degree, int64_t n, const float* coeffs, const fl
                         const float* cam, const float* g_rgb, float* g_coeffs, float* g_means,
                         void* stream);
 
+/*
+ * Diagnostic: evaluates one of the library's FP32 elementary functions on the
+ * device so that tests can measure its error against a float64 reference. The
+ * paper has no counterpart; the functions are the kernels' building blocks.
+ *   fn 0: y = e^x - 1 for x <= 0            (y2 unused, may be NULL)
+ *   fn 1: y = tanh(x), y2 = 1 - tanh(x)^2
+ *   fn 2: y = sin(x),  y2 = cos(x)          (|x| <= 6400)
+ * x, y, y2 device [n] f32. Errors: NASG_ERR_RANGE (fn or n), NASG_ERR_NULL.
+ */
+nasg_status nasg_math_probe(int32_t fn, const float* x, float* y, float* y2, int64_t n, void* stream);
+
 #ifdef __cplusplus
 }  /* extern "C" */
 #endif

@@ -55,6 +55,7 @@ _decl("nasgabor_eval_bwd", [_P(NasgDesc), _vp, _vp, _P(ctypes.c_float), _vp, _i6
 _decl("nasgabor_fused_fwd_bwd", [_P(NasgDesc), _vp, _vp, _vp, _P(ctypes.c_float), _vp, _vp, _vp, _vp, _vp, _vp])
 _decl("sh_eval_fwd", [_i32, _i64, _vp, _vp, _P(ctypes.c_float), _vp, _vp])
 _decl("sh_eval_bwd", [_i32, _i64, _vp, _vp, _P(ctypes.c_float), _vp, _vp, _vp, _vp])
+_decl("nasg_math_probe", [_i32, _vp, _vp, _vp, _i64, _vp])
 
 
 class NasgError(RuntimeError):
@@ -214,6 +215,15 @@ def sh_eval_bwd(coeffs, means, cam, g_rgb, degree=3, g_coeffs=None, g_means=None
     _check(lib.sh_eval_bwd(degree, n, _ptr(coeffs), _ptr(means), _cam(cam), _ptr(g_rgb), _ptr(g_coeffs),
                            _ptr(g_means), _stream(stream)), "sh_eval_bwd")
     return g_coeffs, g_means
+
+
+def nasg_math_probe(fn, x, stream=None):
+    """Diagnostic: the library's FP32 elementary function `fn` (0 expm1, 1 tanh, 2 sincos) at x."""
+    _cuda(x, "x", torch.float32)
+    y = torch.empty_like(x)
+    y2 = torch.empty_like(x) if fn > 0 else None
+    _check(lib.nasg_math_probe(fn, _ptr(x), _ptr(y), _ptr(y2), x.numel(), _stream(stream)), "nasg_math_probe")
+    return y, y2
 
 
 # ---------------------------------------------------------------------------

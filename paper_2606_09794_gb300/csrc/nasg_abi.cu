@@ -46,3 +46,37 @@ extern "C" const char* nasg_status_string(nasg_status status) {
 extern "C" int32_t nasg_last_cuda_error(void) { return nasg::g_last_cuda_error; }
 
 extern "C" int32_t nasg_abi_version(void) { return NASG_ABI_VERSION; }
+
+// ---------------------------------------------------------------------------
+// Diagnostic probe of the elementary functions (nasg_fastmath.cuh)
+// ---------------------------------------------------------------------------
+#include "nasg_fastmath.cuh"
+
+namespace nasg {
+__global__ void math_probe_kernel(int fn, const float* __restrict__ x, float* __restrict__ y,
+                                  float* __restrict__ y2, int64_t n) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float v = x[i];
+    float a = 0.f, b = 0.f;
+    if (fn == 0) {
+      a = vexpm1n(v);
+    } else if (fn == 1) {
+      vtanh(v, a, b);
+    } else {
+      vsincos(v, a, b);
+    }
+    y[i] = a;
+    if (y2) y2[i] = b;
+  }
+}
+}  // namespace nasg
+
+extern "C" nasg_status nasg_math_probe(int32_t fn, const float* x, float* y, float* y2, int64_t n,
+                                       void* stream) {
+  if (fn < 0 || fn > 2 || n < 0) return NASG_ERR_RANGE;
+  if (n == 0) return NASG_OK;
+  if (!x || !y || (fn > 0 && !y2)) return NASG_ERR_NULL;
+  nasg::math_probe_kernel<<<nasg::grid_for(n, 256), 256, 0, nasg::as_stream(stream)>>>(fn, x, y, y2, n);
+  return nasg::check_launch();
+}

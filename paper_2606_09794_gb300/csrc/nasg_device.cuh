@@ -1,32 +1,37 @@
 // Device-side math of the NASGabor lobe (arXiv 2606.09794), shared by every
-// NASGabor kernel of the library. FP32 throughout.
+// NASGabor kernel of the library. FP32, generic over the value type V (one
+// lobe as float, or two lobes packed as P2, see nasg_vec.cuh).
 //
 // The lobe (Sec. 4.1 definition, Supp. F factorisation):
 //   u = d.z, v = d.x, kappa = (1+u)/2, tau = a v^2 / (1-u^2), E = kappa^tau,
 //   p = exp(2 lam (E kappa - 1)), h = (1 + cos(k v))/2, G = C^-1 p E h,
 //   C^-1 = lam sqrt(1+a) / (2 pi (1 - e^{-2 lam}))  (Supp. E/F; used for all Sec. 5 results).
 //
-// FP32 formulation (algebraically identical, chosen for conditioning at
-// lam up to 1e3, where 2 lam (E kappa - 1) amplifies any absolute error in
-// 1 - u by 2 lam):
-//   s2      = |d x z|^2                 (= 1 - u^2 without cancellation)
-//   1 - u   = s2 / (1 + u) for u >= 0, else 1 - u
-//   ln kappa = log1p(-(1 - u)/2)
+// FP32 formulation (algebraically identical, chosen for conditioning at lam
+// up to 1e3, where 2 lam (E kappa - 1) amplifies any absolute error in 1 - u
+// by 2 lam):
+//   s2       = |d x z|^2                 (= 1 - u^2 without cancellation)
+//   1 - u    = s2 / (1 + u) for u >= 0, else 1 - u   (and 1 + u symmetrically)
+//   ln kappa = log1p(-(1 - u)/2) for u >= 0, log((1 + u)/2) for u < 0
 //   E kappa - 1 = expm1((1 + tau) ln kappa)
-//   p E     = exp(2 lam (E kappa - 1) + tau ln kappa)
-//   h       = cos^2(k v / 2),  sin(k v) = 2 sin(k v/2) cos(k v/2)
+//   p E      = exp(2 lam (E kappa - 1) + tau ln kappa)
+//   h        = cos^2(k v / 2),  sin(k v) = 2 sin(k v/2) cos(k v/2)
 //   1 - e^{-2 lam} = -expm1(-2 lam)
-// Poles: where s2 == 0, u > 0 takes tau := 0 (G = C^-1 h(v)) and u < 0 gives
-// G := 0 with zero derivatives -- the same rule as the FP64 oracle.
+// Poles: where s2 == 0 in FP32 (below the normal range), u > 0 takes tau := 0
+// (G = C^-1 h(v)) and u < 0 gives G := 0 with zero derivatives -- the same
+// rule as the FP64 oracle.
 #pragma once
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "nasg_fastmath.cuh"
+
 namespace nasg {
 
 constexpr float kInvTwoPi = 0.159154943091895336f;  // 1 / (2 pi)
+constexpr float kFltMin = 1.17549435e-38f;
 
 // ---------------------------------------------------------------------------
 // Loads of stored parameters
@@ -34,57 +39,6 @@ constexpr float kInvTwoPi = 0.159154943091895336f;  // 1 / (2 pi)
 
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
-
-// Load V consecutive elements starting at p (V = 1 or 4; V = 4 requires
-// 16-byte alignment for float and 8-byte alignment for bfloat16).
-template <typename T, int V>
-struct VecLoad;
-
-template <>
-struct VecLoad<float, 1> {
-  static __device__ __forceinline__ void run(const float* p, float* o) { o[0] = __ldg(p); }
-};
-template <>
-struct VecLoad<float, 4> {
-  static __device__ __forceinline__ void run(const float* p, float* o) {
-    float4 t = __ldg(reinterpret_cast<const float4*>(p));
-    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
-  }
-};
-template <>
-struct VecLoad<__nv_bfloat16, 1> {
-  static __device__ __forceinline__ void run(const __nv_bfloat16* p, float* o) {
-    o[0] = __bfloat162float(p[0]);
-  }
-};
-template <>
-struct VecLoad<__nv_bfloat16, 4> {
-  static __device__ __forceinline__ void run(const __nv_bfloat16* p, float* o) {
-    uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
-    o[0] = bf16_lo(t.x); o[1] = bf16_hi(t.x); o[2] = bf16_lo(t.y); o[3] = bf16_hi(t.y);
-  }
-};
-
-template <int V>
-struct VecStore;
-template <>
-struct VecStore<1> {
-  static __device__ __forceinline__ void run(float* p, const float* v, bool acc) {
-    p[0] = acc ? p[0] + v[0] : v[0];
-  }
-};
-template <>
-struct VecStore<4> {
-  static __device__ __forceinline__ void run(float* p, const float* v, bool acc) {
-    float4* q = reinterpret_cast<float4*>(p);
-    float4 t = make_float4(v[0], v[1], v[2], v[3]);
-    if (acc) {
-      float4 o = *q;
-      t.x += o.x; t.y += o.y; t.z += o.z; t.w += o.w;
-    }
-    *q = t;
-  }
-};
 
 template <typename T>
 __device__ __forceinline__ float load1(const T* p);
@@ -95,79 +49,94 @@ __device__ __forceinline__ float load1<__nv_bfloat16>(const __nv_bfloat16* p) {
   return __bfloat162float(p[0]);
 }
 
+// Two consecutive elements (8 B f32 / 4 B bf16, aligned to that size).
+template <typename T>
+__device__ __forceinline__ P2 load2(const T* p);
+template <>
+__device__ __forceinline__ P2 load2<float>(const float* p) {
+  P2 r;
+  r.v = __ldg(reinterpret_cast<const float2*>(p));
+  return r;
+}
+template <>
+__device__ __forceinline__ P2 load2<__nv_bfloat16>(const __nv_bfloat16* p) {
+  const uint32_t w = __ldg(reinterpret_cast<const unsigned int*>(p));
+  return p2(bf16_lo(w), bf16_hi(w));
+}
+
 // ---------------------------------------------------------------------------
 // Activations (Supp. C table) and their slopes d(activated)/d(raw)
 // ---------------------------------------------------------------------------
 
+template <class V>
 struct Act {
-  float lam, a, k, w[3];
-  float s_lam, s_a, s_k, s_w[3];
+  V lam, a, k, w[3];
+  V s_lam, s_a, s_k, s_w[3];
 };
 
-__device__ __forceinline__ void activate(float lam_r, float a_r, float k_r, float w0, float w1,
-                                         float w2, bool identity, Act& o) {
+// r: lam_r, a_r, k_r, w_r, w_g, w_b
+template <class V>
+__device__ __forceinline__ void activate(const V* r, bool identity, Act<V>& o) {
   if (identity) {
-    o.lam = lam_r; o.a = a_r; o.k = k_r;
-    o.w[0] = w0; o.w[1] = w1; o.w[2] = w2;
-    o.s_lam = o.s_a = o.s_k = 1.f;
-    o.s_w[0] = o.s_w[1] = o.s_w[2] = 1.f;
+    const V one = vconst<V>(1.f);
+    o.lam = r[0]; o.a = r[1]; o.k = r[2];
+    o.w[0] = r[3]; o.w[1] = r[4]; o.w[2] = r[5];
+    o.s_lam = one; o.s_a = one; o.s_k = one;
+    o.s_w[0] = one; o.s_w[1] = one; o.s_w[2] = one;
     return;
   }
-  o.lam = expf(lam_r);
+  o.lam = vexp(r[0]);
   o.s_lam = o.lam;
-  o.a = expf(a_r);
+  o.a = vexp(r[1]);
   o.s_a = o.a;
   // k = 20 (tanh r + 1) = 40 sig(2r); dk/dr = 20 (1 - tanh^2 r) = 80 sig (1 - sig).
   // Written through sig so that k keeps relative accuracy as tanh r -> -1.
-  const float e = expf(-2.f * k_r);
-  const float sig = 1.f / (1.f + e);
-  const float one_m_sig = (k_r >= 0.f) ? e * sig : 1.f - sig;
+  const V e = vexp(-2.f * r[2]);
+  const V sig = vrcp(1.f + e);  // 0 when e overflows
+  const V one_m_sig = vsel(vge(r[2], 0.f), e * sig, 1.f - sig);
   o.k = 40.f * sig;
   o.s_k = 80.f * sig * one_m_sig;
-  const float wr[3] = {w0, w1, w2};
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const float t = tanhf(wr[c]);
-    o.w[c] = t;
-    o.s_w[c] = (1.f - t) * (1.f + t);
-  }
+  for (int c = 0; c < 3; ++c) vtanh(r[3 + c], o.w[c], o.s_w[c]);
 }
 
 // ---------------------------------------------------------------------------
 // Frames: x and z axes of the lobe (y = z x x never formed; G does not use it)
 // ---------------------------------------------------------------------------
 
+template <class V>
 struct QuatFrame {
-  float q[4];       // normalised quaternion (w, x, y, z)
-  float inv_norm;   // 1/|q_raw|
-  float x[3], z[3];
+  V q[4];       // normalised quaternion (w, x, y, z)
+  V inv_norm;   // 1/|q_raw|
+  V x[3], z[3];
 };
 
-__device__ __forceinline__ void quat_frame(float qw, float qx, float qy, float qz, QuatFrame& f) {
-  const float n2 = qw * qw + qx * qx + qy * qy + qz * qz;
-  const float inv = 1.f / sqrtf(n2);
+template <class V>
+__device__ __forceinline__ void quat_frame(const V* qr, QuatFrame<V>& f) {
+  const V n2 = vfma(qr[0], qr[0], vfma(qr[1], qr[1], vfma(qr[2], qr[2], qr[3] * qr[3])));
+  const V inv = vrsqrt(n2);
   f.inv_norm = inv;
-  const float w = qw * inv, x = qx * inv, y = qy * inv, z = qz * inv;
+  const V w = qr[0] * inv, x = qr[1] * inv, y = qr[2] * inv, z = qr[3] * inv;
   f.q[0] = w; f.q[1] = x; f.q[2] = y; f.q[3] = z;
   // first and third columns of the rotation matrix of the unit quaternion
-  f.x[0] = 1.f - 2.f * (y * y + z * z);
-  f.x[1] = 2.f * (x * y + w * z);
-  f.x[2] = 2.f * (x * z - w * y);
-  f.z[0] = 2.f * (x * z + w * y);
-  f.z[1] = 2.f * (y * z - w * x);
-  f.z[2] = 1.f - 2.f * (x * x + y * y);
+  f.x[0] = 1.f - 2.f * vfma(y, y, z * z);
+  f.x[1] = 2.f * vfma(x, y, w * z);
+  f.x[2] = 2.f * vfma(x, z, -(w * y));
+  f.z[0] = 2.f * vfma(x, z, w * y);
+  f.z[1] = 2.f * vfma(y, z, -(w * x));
+  f.z[2] = 1.f - 2.f * vfma(x, x, y * y);
 }
 
-// dLoss/dq_raw from dLoss/dx and dLoss/dz (through the unit-quaternion
-// rotation columns and the normalisation q -> q/|q|).
-__device__ __forceinline__ void quat_frame_grad(const QuatFrame& f, const float L[3], const float M[3],
-                                                float g[4]) {
-  const float w = f.q[0], x = f.q[1], y = f.q[2], z = f.q[3];
-  float gw = 2.f * (L[1] * z - L[2] * y + M[0] * y - M[1] * x);
-  float gx = 2.f * (L[1] * y + L[2] * z + M[0] * z - M[1] * w - 2.f * M[2] * x);
-  float gy = 2.f * (-2.f * L[0] * y + L[1] * x - L[2] * w + M[0] * w + M[1] * z - 2.f * M[2] * y);
-  float gz = 2.f * (-2.f * L[0] * z + L[1] * w + L[2] * x + M[0] * x + M[1] * y);
-  const float dot = gw * w + gx * x + gy * y + gz * z;
+// dLoss/dq_raw from dLoss/dx (L) and dLoss/dz (M), through the unit-quaternion
+// rotation columns and the normalisation q -> q/|q|.
+template <class V>
+__device__ __forceinline__ void quat_frame_grad(const QuatFrame<V>& f, const V* L, const V* M, V* g) {
+  const V w = f.q[0], x = f.q[1], y = f.q[2], z = f.q[3];
+  const V gw = 2.f * (vfma(L[1], z, vfma(M[0], y, -(L[2] * y))) - M[1] * x);
+  const V gx = 2.f * (vfma(L[1], y, vfma(L[2], z, vfma(M[0], z, -(M[1] * w)))) - 2.f * M[2] * x);
+  const V gy = 2.f * (vfma(L[1], x, vfma(M[0], w, vfma(M[1], z, -(L[2] * w)))) - 2.f * (L[0] + M[2]) * y);
+  const V gz = 2.f * (vfma(L[1], w, vfma(L[2], x, vfma(M[0], x, M[1] * y))) - 2.f * L[0] * z);
+  const V dot = vfma(gw, w, vfma(gx, x, vfma(gy, y, gz * z)));
   g[0] = (gw - dot * w) * f.inv_norm;
   g[1] = (gx - dot * x) * f.inv_norm;
   g[2] = (gy - dot * y) * f.inv_norm;
@@ -177,116 +146,127 @@ __device__ __forceinline__ void quat_frame_grad(const QuatFrame& f, const float 
 // Supp. C frame from three cosines. RAW mode: c = tanh(r), s = sech(r) >= 0,
 // with dc/dr = s^2 and ds/dr = -c s (finite everywhere, including where tanh
 // saturates). IDENTITY mode: c = r, s = sqrt(1 - c^2), ds/dc = -c/s.
+template <class V>
 struct CosFrame {
-  float c[3], s[3];     // cos / sin of theta, phi, psi
-  float dc[3], ds[3];   // d c / d stored, d s / d stored
-  float x[3], z[3];
+  V c[3], s[3];     // cos / sin of theta, phi, psi
+  V dc[3], ds[3];   // d c / d stored, d s / d stored
+  V x[3], z[3];
 };
 
-__device__ __forceinline__ void cos_angle(float r, bool identity, float& c, float& s, float& dc, float& ds) {
+template <class V>
+__device__ __forceinline__ void cos_angle(V r, bool identity, V& c, V& s, V& dc, V& ds) {
   if (identity) {
     c = r;
-    s = sqrtf(fmaxf(0.f, (1.f - r) * (1.f + r)));
-    dc = 1.f;
-    ds = -c / s;
+    const V s2 = vmax((1.f - r) * (1.f + r), 0.f);
+    const V rs = vrsqrt(vmax(s2, kFltMin));
+    s = s2 * rs;
+    dc = vconst<V>(1.f);
+    ds = -(c * rs);
     return;
   }
-  const float ar = fabsf(r);
-  const float em = expf(-ar);                // e^{-|r|}
-  const float inv = 1.f / (1.f + em * em);
-  const float t = -expm1f(-2.f * ar) * inv;  // tanh|r|
-  c = copysignf(t, r);
-  s = 2.f * em * inv;                        // sech r
+  const V ar = vabs(r);
+  const V em = vexp(-ar);                      // e^{-|r|}
+  const V inv = vrcp(1.f + em * em);
+  const V t = -(vexpm1n(-2.f * ar) * inv);     // tanh|r|
+  c = vcopysign(t, r);
+  s = 2.f * em * inv;                          // sech r
   dc = s * s;
-  ds = -c * s;
+  ds = -(c * s);
 }
 
-__device__ __forceinline__ void cos_frame(float rt, float rp, float rs, bool identity, CosFrame& f) {
-  cos_angle(rt, identity, f.c[0], f.s[0], f.dc[0], f.ds[0]);
-  cos_angle(rp, identity, f.c[1], f.s[1], f.dc[1], f.ds[1]);
-  cos_angle(rs, identity, f.c[2], f.s[2], f.dc[2], f.ds[2]);
-  const float ct = f.c[0], st = f.s[0], cp = f.c[1], sp = f.s[1], cs = f.c[2], ss = f.s[2];
+template <class V>
+__device__ __forceinline__ void cos_frame(const V* r, bool identity, CosFrame<V>& f) {
+  cos_angle(r[0], identity, f.c[0], f.s[0], f.dc[0], f.ds[0]);
+  cos_angle(r[1], identity, f.c[1], f.s[1], f.dc[1], f.ds[1]);
+  cos_angle(r[2], identity, f.c[2], f.s[2], f.dc[2], f.ds[2]);
+  const V ct = f.c[0], st = f.s[0], cp = f.c[1], sp = f.s[1], cs = f.c[2], ss = f.s[2];
   f.z[0] = ct * sp; f.z[1] = st * sp; f.z[2] = cp;
-  f.x[0] = ct * cp * cs - st * ss;
-  f.x[1] = st * cp * cs + ct * ss;
-  f.x[2] = -sp * cs;
+  f.x[0] = vfma(ct * cp, cs, -(st * ss));
+  f.x[1] = vfma(st * cp, cs, ct * ss);
+  f.x[2] = -(sp * cs);
 }
 
-__device__ __forceinline__ void cos_frame_grad(const CosFrame& f, const float gx[3], const float gz[3],
-                                               float g[3]) {
-  const float ct = f.c[0], st = f.s[0], cp = f.c[1], sp = f.s[1], cs = f.c[2], ss = f.s[2];
-  const float g_ct = gx[0] * cp * cs + gx[1] * ss + gz[0] * sp;
-  const float g_st = -gx[0] * ss + gx[1] * cp * cs + gz[1] * sp;
-  const float g_cp = gx[0] * ct * cs + gx[1] * st * cs + gz[2];
-  const float g_sp = -gx[2] * cs + gz[0] * ct + gz[1] * st;
-  const float g_cs = gx[0] * ct * cp + gx[1] * st * cp - gx[2] * sp;
-  const float g_ss = -gx[0] * st + gx[1] * ct;
-  g[0] = g_ct * f.dc[0] + g_st * f.ds[0];
-  g[1] = g_cp * f.dc[1] + g_sp * f.ds[1];
-  g[2] = g_cs * f.dc[2] + g_ss * f.ds[2];
+template <class V>
+__device__ __forceinline__ void cos_frame_grad(const CosFrame<V>& f, const V* gx, const V* gz, V* g) {
+  const V ct = f.c[0], st = f.s[0], cp = f.c[1], sp = f.s[1], cs = f.c[2], ss = f.s[2];
+  const V g_ct = vfma(gx[0] * cp, cs, vfma(gx[1], ss, gz[0] * sp));
+  const V g_st = vfma(gx[1] * cp, cs, vfma(gz[1], sp, -(gx[0] * ss)));
+  const V g_cp = vfma(vfma(gx[0], ct, gx[1] * st), cs, gz[2]);
+  const V g_sp = vfma(gz[0], ct, vfma(gz[1], st, -(gx[2] * cs)));
+  const V g_cs = vfma(vfma(gx[0], ct, gx[1] * st), cp, -(gx[2] * sp));
+  const V g_ss = vfma(gx[1], ct, -(gx[0] * st));
+  g[0] = vfma(g_ct, f.dc[0], g_st * f.ds[0]);
+  g[1] = vfma(g_cp, f.dc[1], g_sp * f.ds[1]);
+  g[2] = vfma(g_cs, f.dc[2], g_ss * f.ds[2]);
 }
 
 // ---------------------------------------------------------------------------
 // The lobe and its partial derivatives
 // ---------------------------------------------------------------------------
 
+template <class V>
 struct LobePartials {
-  float G_u, G_v, G_lam, G_a, G_k;  // dG/du, dG/dv, dG/dlam, dG/da, dG/dk
+  V G_u, G_v, G_lam, G_a, G_k;  // dG/du, dG/dv, dG/dlam, dG/da, dG/dk
 };
 
-template <bool GRAD>
-__device__ __forceinline__ float lobe(const float d[3], const float x[3], const float z[3], float lam,
-                                      float a, float k, bool normalised, LobePartials* pd) {
-  const float u = d[0] * z[0] + d[1] * z[1] + d[2] * z[2];
-  const float v = d[0] * x[0] + d[1] * x[1] + d[2] * x[2];
-  const float cx = d[1] * z[2] - d[2] * z[1];
-  const float cy = d[2] * z[0] - d[0] * z[2];
-  const float cz = d[0] * z[1] - d[1] * z[0];
-  const float s2 = cx * cx + cy * cy + cz * cz;  // 1 - u^2
-  const bool pole = !(s2 > 0.f);
-  const bool anti = pole && (u < 0.f);
-  const float inv_s2 = pole ? 0.f : 1.f / s2;
-  const float omu = (u >= 0.f) ? s2 / (1.f + u) : 1.f - u;  // 1 - u
-  const float ln_k = anti ? 0.f : log1pf(-0.5f * omu);      // ln kappa
-  const float tau = a * v * v * inv_s2;
-  const float ln_e = tau * ln_k;                            // ln E
-  const float em1 = expm1f(ln_e + ln_k);                    // E kappa - 1
-  const float pe = expf(2.f * lam * em1 + ln_e);            // p E
-  float sh, ch;
-  sincosf(0.5f * k * v, &sh, &ch);
-  const float h = ch * ch;
-  float cinv = 1.f, dlnc_dlam = 0.f, dlnc_da = 0.f;
+template <bool GRAD, class V>
+__device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a, V k, bool normalised,
+                                  LobePartials<V>* pd) {
+  using M = typename VecTraits<V>::Mask;
+  const V u = vfma(d[0], z[0], vfma(d[1], z[1], d[2] * z[2]));
+  const V v = vfma(d[0], x[0], vfma(d[1], x[1], d[2] * x[2]));
+  const V cx = vfma(d[1], z[2], -(d[2] * z[1]));
+  const V cy = vfma(d[2], z[0], -(d[0] * z[2]));
+  const V cz = vfma(d[0], z[1], -(d[1] * z[0]));
+  const V s2 = vfma(cx, cx, vfma(cy, cy, cz * cz));  // 1 - u^2
+  // pole: s2 below the normal range (the FP32 zero of 1 - u^2)
+  const M pole = vlt(s2, kFltMin);
+  const M up = vge(u, 0.f);
+  const M anti = vand(pole, vnot(up));
+  const V inv_s2 = vsel(pole, 0.f, vrcp(s2));
+  // 1 - u and 1 + u, each from s2 on the side where it is small
+  const V one_m_u = 1.f - u, one_p_u = 1.f + u;
+  const V rd = vrcp(vsel(up, one_p_u, one_m_u));
+  const V omu = vsel(up, s2 * rd, one_m_u);
+  const V opu = vsel(up, one_p_u, s2 * rd);
+  const V inv_opu = vsel(up, rd, one_m_u * inv_s2);  // 1/(1+u) = 1/(2 kappa)
+  const V t = -0.5f * omu;
+  const V kap = vsel(up, 1.f + t, 0.5f * opu);
+  const V ln_k = vsel(anti, 0.f, vlnkappa(t, vmax(kap, kFltMin)));  // ln kappa
+  const V tau = a * v * v * inv_s2;
+  const V ln_e = tau * ln_k;                                      // ln E
+  const V em1 = vexpm1n(ln_e + ln_k);                             // E kappa - 1
+  const V pe = vexp(vfma(2.f * lam, em1, ln_e));                  // p E
+  V sh, ch;
+  vsincos(0.5f * k * v, sh, ch);
+  const V h = ch * ch;
+  V cinv = vconst<V>(1.f), dlnc_dlam = vconst<V>(0.f), dlnc_da = vconst<V>(0.f);
   if (normalised) {
-    const float em = expm1f(-2.f * lam);  // e^{-2 lam} - 1 (negative)
-    const float sq = sqrtf(1.f + a);
-    cinv = lam * sq * kInvTwoPi / (-em);
+    const V em = vexpm1n(-2.f * lam);  // e^{-2 lam} - 1 (negative)
+    const V r_em = vrcp(em);
+    const V opa = 1.f + a;
+    cinv = -((lam * (opa * vrsqrt(opa))) * (kInvTwoPi * r_em));
     if (GRAD) {
       // d ln C^-1/d lam = 1/lam - 2 e^{-2 lam}/(1 - e^{-2 lam}); d ln C^-1/d a = 1/(2 (1+a))
-      dlnc_dlam = 1.f / lam + 2.f * (1.f + em) / em;
-      dlnc_da = 0.5f / (1.f + a);
+      dlnc_dlam = vfma(2.f * (1.f + em), r_em, vrcp(lam));
+      dlnc_da = 0.5f * vrcp(opa);
     }
   }
-  const float cpe = cinv * pe;
-  const float G = anti ? 0.f : cpe * h;
+  const V cpe = cinv * pe;
+  const V G = vsel(anti, 0.f, cpe * h);
   if (GRAD) {
-    if (anti) {
-      pd->G_u = pd->G_v = pd->G_lam = pd->G_a = pd->G_k = 0.f;
-    } else {
-      // 1/(1+u) = 1/(2 kappa); for u < 0, 1 + u = s2/(1 - u) without cancellation
-      const float inv_opu = (u >= 0.f) ? 1.f / (1.f + u) : (1.f - u) * inv_s2;
-      const float ek = em1 + 1.f;                       // E kappa
-      const float two_lam_ek = 2.f * lam * ek;
-      const float dtau_du = 2.f * u * tau * inv_s2;
-      const float dtau_dv = 2.f * a * v * inv_s2;
-      const float dlne_du = ln_k * dtau_du + tau * inv_opu;
-      const float dlne_dv = ln_k * dtau_dv;
-      const float sin_kv = 2.f * sh * ch;
-      pd->G_u = G * (two_lam_ek * (dlne_du + inv_opu) + dlne_du);
-      pd->G_v = G * (two_lam_ek + 1.f) * dlne_dv - cpe * (0.5f * k) * sin_kv;
-      pd->G_k = -cpe * (0.5f * v) * sin_kv;
-      pd->G_lam = G * (2.f * em1 + dlnc_dlam);
-      pd->G_a = G * ((two_lam_ek + 1.f) * ln_k * v * v * inv_s2 + dlnc_da);
-    }
+    const V ek = em1 + 1.f;                             // E kappa
+    const V two_lam_ek = 2.f * lam * ek;
+    const V dtau_du = 2.f * u * tau * inv_s2;
+    const V dtau_dv = 2.f * a * v * inv_s2;
+    const V dlne_du = vfma(ln_k, dtau_du, tau * inv_opu);
+    const V dlne_dv = ln_k * dtau_dv;
+    const V cpe_sin = cpe * (2.f * sh * ch);            // C^-1 p E sin(k v)
+    pd->G_u = vsel(anti, 0.f, G * vfma(two_lam_ek, dlne_du + inv_opu, dlne_du));
+    pd->G_v = vsel(anti, 0.f, vfma(G * (two_lam_ek + 1.f), dlne_dv, -(cpe_sin * (0.5f * k))));
+    pd->G_k = vsel(anti, 0.f, -(cpe_sin * (0.5f * v)));
+    pd->G_lam = vsel(anti, 0.f, G * vfma(2.f, em1, dlnc_dlam));
+    pd->G_a = vsel(anti, 0.f, G * vfma((two_lam_ek + 1.f) * ln_k, v * v * inv_s2, dlnc_da));
   }
   return G;
 }
@@ -300,8 +280,7 @@ __device__ __forceinline__ float view_dir(const float* means, int64_t i, float c
   const float rx = __ldg(means + 3 * i + 0) - cx;
   const float ry = __ldg(means + 3 * i + 1) - cy;
   const float rz = __ldg(means + 3 * i + 2) - cz;
-  const float dist = sqrtf(rx * rx + ry * ry + rz * rz);
-  const float inv = 1.f / dist;
+  const float inv = rsqrtf(rx * rx + ry * ry + rz * rz);
   d[0] = rx * inv; d[1] = ry * inv; d[2] = rz * inv;
   return inv;
 }

@@ -177,6 +177,7 @@ using namespace nasg;
 extern "C" nasg_status sh_eval_fwd(int32_t degree, int64_t n, const float* coeffs, const float* means,
                                    const float* cam, float* rgb, void* stream) {
   if (degree < 0 || degree > 3 || n < 0) return NASG_ERR_RANGE;
+  if (n == 0) return NASG_OK;
   if (!coeffs || !means || !cam || !rgb) return NASG_ERR_NULL;
   if (!aligned(coeffs, 4) || !aligned(means, 4) || !aligned(rgb, 4)) return NASG_ERR_ALIGN;
   if (n == 0) return NASG_OK;
@@ -193,6 +194,7 @@ extern "C" nasg_status sh_eval_bwd(int32_t degree, int64_t n, const float* coeff
                                    const float* cam, const float* g_rgb, float* g_coeffs, float* g_means,
                                    void* stream) {
   if (degree < 0 || degree > 3 || n < 0) return NASG_ERR_RANGE;
+  if (n == 0) return NASG_OK;
   if (!coeffs || !means || !cam || !g_rgb || !g_coeffs) return NASG_ERR_NULL;
   if (!aligned(coeffs, 4) || !aligned(means, 4) || !aligned(g_rgb, 4) || !aligned(g_coeffs, 4) ||
       (g_means && !aligned(g_means, 4)))
