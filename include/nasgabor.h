@@ -53,7 +53,7 @@ typedef int32_t nasg_status;
 #define NASG_ERR_ALIGN       -3  /* a pointer is not aligned to its element type       */
 #define NASG_ERR_UNSUPPORTED -4  /* valid but not built (e.g. an unsupported mode mix) */
 #define NASG_ERR_CUDA        -5  /* a CUDA runtime call or launch failed               */
-#define NASG_ERR_DEVICE      -6  /* no usable CUDA device                              */
+#define NASG_ERR_DEVICE      -6  /* a kernel reported a device-side error (see nasg_device_status) */
 
 #define NASG_FRAME_QUAT 0   /* frame from a quaternion (4 raw scalars)              */
 #define NASG_FRAME_COS  1   /* frame from three cosines (Supp. C parameterisation)  */
@@ -89,6 +89,12 @@ const char* nasg_status_string(nasg_status status);
 /* The cudaError_t of the most recent failed CUDA call made by this library on
  * the calling thread (0 if none); reading it does not clear it. */
 int32_t nasg_last_cuda_error(void);
+
+/* Synchronises `stream` and reads the library's device error word, which a
+ * kernel sets when one of its bounded waits (on a bulk-copy barrier) gives up
+ * instead of hanging. Returns NASG_OK if clear, NASG_ERR_DEVICE if set (and
+ * clears it), NASG_ERR_CUDA if the query itself failed. */
+nasg_status nasg_device_status(void* stream);
 
 /* ABI version of this header (bumped on any incompatible change). */
 #define NASG_ABI_VERSION 1
@@ -165,6 +171,15 @@ nasg_status sh_eval_bwd(int32_t degree, int64_t n, const float* coeffs, const fl
  * x, y, y2 device [n] f32. Errors: NASG_ERR_RANGE (fn or n), NASG_ERR_NULL.
  */
 nasg_status nasg_math_probe(int32_t fn, const float* x, float* y, float* y2, int64_t n, void* stream);
+
+/*
+ * Diagnostic: launches one block that waits, with an iteration limit of
+ * `limit` (1..2^20), on a shared-memory barrier that nothing completes, so that
+ * tests can check the bounded-wait path: afterwards nasg_device_status()
+ * returns NASG_ERR_DEVICE. The paper has no counterpart; this exercises the
+ * library's failure detection without faulting or hanging the GPU.
+ */
+nasg_status nasg_probe_wait_timeout(int32_t limit, void* stream);
 
 #ifdef __cplusplus
 }  /* extern "C" */

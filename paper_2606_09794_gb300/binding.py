@@ -50,6 +50,8 @@ _decl("nasg_lobe_planes", [_i32])
 _decl("nasg_status_string", [_i32], ctypes.c_char_p)
 _decl("nasg_last_cuda_error", [])
 _decl("nasg_abi_version", [])
+_decl("nasg_device_status", [_vp])
+_decl("nasg_probe_wait_timeout", [_i32, _vp])
 _decl("nasgabor_eval_fwd", [_P(NasgDesc), _vp, _vp, _vp, _P(ctypes.c_float), _vp, _i64, _vp, _vp])
 _decl("nasgabor_eval_bwd", [_P(NasgDesc), _vp, _vp, _P(ctypes.c_float), _vp, _i64, _vp, _vp, _vp, _vp, _vp])
 _decl("nasgabor_fused_fwd_bwd", [_P(NasgDesc), _vp, _vp, _vp, _P(ctypes.c_float), _vp, _vp, _vp, _vp, _vp, _vp])
@@ -113,6 +115,16 @@ def make_desc(n, n_lobes, frame_mode="quat", param_dtype=torch.float32, norm_mod
               accumulate=False) -> NasgDesc:
     return NasgDesc(int(n), int(n_lobes), FRAME[frame_mode], 1 if param_dtype == torch.bfloat16 else 0,
                     NORM[norm_mode], ACT[act_mode], 1 if accumulate else 0)
+
+
+def nasg_device_status(stream=None):
+    """Synchronise the stream and raise NasgError if a kernel's bounded wait gave up."""
+    _check(lib.nasg_device_status(_stream(stream)), "nasg_device_status")
+
+
+def nasg_probe_wait_timeout(limit=1024, stream=None):
+    """Diagnostic: run a bounded wait that cannot complete (sets the device error word)."""
+    _check(lib.nasg_probe_wait_timeout(int(limit), _stream(stream)), "nasg_probe_wait_timeout")
 
 
 def lobe_planes(frame_mode="quat") -> int:

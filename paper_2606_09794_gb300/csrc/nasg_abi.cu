@@ -3,8 +3,24 @@
 #include <cuda_runtime.h>
 
 #include "nasg_host.h"
+#include "nasg_tma.cuh"
 
 namespace nasg {
+
+// Set by a kernel whose bounded wait gave up; see nasg_device_status().
+__device__ int g_device_error = 0;
+
+int* device_error_word() {
+  static int* cached[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!cached[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
+    cached[dev] = static_cast<int*>(p);
+  }
+  return cached[dev];
+}
 
 static thread_local int32_t g_last_cuda_error = 0;
 
@@ -38,7 +54,7 @@ extern "C" const char* nasg_status_string(nasg_status status) {
     case NASG_ERR_ALIGN: return "a pointer is misaligned for its element type";
     case NASG_ERR_UNSUPPORTED: return "unsupported combination of modes";
     case NASG_ERR_CUDA: return "a CUDA call or kernel launch failed";
-    case NASG_ERR_DEVICE: return "no usable CUDA device";
+    case NASG_ERR_DEVICE: return "a kernel reported a device-side error (bounded wait gave up)";
     default: return "unknown status";
   }
 }
@@ -46,6 +62,24 @@ extern "C" const char* nasg_status_string(nasg_status status) {
 extern "C" int32_t nasg_last_cuda_error(void) { return nasg::g_last_cuda_error; }
 
 extern "C" int32_t nasg_abi_version(void) { return NASG_ABI_VERSION; }
+
+extern "C" nasg_status nasg_device_status(void* stream) {
+  int v = 0;
+  cudaStream_t s = nasg::as_stream(stream);
+  if (cudaMemcpyFromSymbolAsync(&v, nasg::g_device_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    nasg::record_cuda_error(cudaGetLastError());
+    return NASG_ERR_CUDA;
+  }
+  if (v == 0) return NASG_OK;
+  const int zero = 0;
+  if (cudaMemcpyToSymbolAsync(nasg::g_device_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    nasg::record_cuda_error(cudaGetLastError());
+    return NASG_ERR_CUDA;
+  }
+  return NASG_ERR_DEVICE;
+}
 
 // ---------------------------------------------------------------------------
 // Diagnostic probe of the elementary functions (nasg_fastmath.cuh)
@@ -78,5 +112,29 @@ extern "C" nasg_status nasg_math_probe(int32_t fn, const float* x, float* y, flo
   if (n == 0) return NASG_OK;
   if (!x || !y || (fn > 0 && !y2)) return NASG_ERR_NULL;
   nasg::math_probe_kernel<<<nasg::grid_for(n, 256), 256, 0, nasg::as_stream(stream)>>>(fn, x, y, y2, n);
+  return nasg::check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostic: a bounded wait on a barrier that nothing completes
+// ---------------------------------------------------------------------------
+namespace nasg {
+__global__ void wait_timeout_probe_kernel(int* err, uint32_t limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  // no thread arrives and no copy is issued: the phase never completes
+  mbar_wait(&bar, 0, err, limit);
+}
+}  // namespace nasg
+
+extern "C" nasg_status nasg_probe_wait_timeout(int32_t limit, void* stream) {
+  if (limit < 1 || limit > (1 << 20)) return NASG_ERR_RANGE;
+  int* err = nasg::device_error_word();
+  if (!err) return NASG_ERR_CUDA;
+  nasg::wait_timeout_probe_kernel<<<1, 32, 0, nasg::as_stream(stream)>>>(err, uint32_t(limit));
   return nasg::check_launch();
 }

@@ -40,6 +40,11 @@ constexpr float kFltMin = 1.17549435e-38f;
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
+__device__ __forceinline__ float to_float(float v) { return v; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// One element from GLOBAL memory (read-only path for f32); never use it on a
+// shared-memory address.
 template <typename T>
 __device__ __forceinline__ float load1(const T* p);
 template <>

@@ -28,6 +28,10 @@ inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// Device address of the library's device error word on the current device
+// (resolved once per device); nullptr if it cannot be resolved.
+int* device_error_word();
+
 // Grid for a grid-stride loop over `items` with `block` threads: one item per
 // thread, capped so that a 64-bit item count never overflows the grid.
 inline unsigned grid_for(int64_t items, int block) {

@@ -17,6 +17,7 @@
 
 #include "nasg_device.cuh"
 #include "nasg_host.h"
+#include "nasg_tma.cuh"
 
 namespace nasg {
 
@@ -41,6 +42,7 @@ struct EvalArgs {
   float* g_params;
   float* g_c0;
   float* g_means;
+  int* dev_err;         // device error word (bounded waits)
 };
 
 template <int FRAME>
@@ -109,7 +111,8 @@ __device__ __forceinline__ void store2(float* p, P2 v, bool acc) {
 
 // Raw words of one lane's work item, fetched one item ahead of the compute:
 // the two lobes' P stored scalars (one 32-bit word per plane for bf16 pairs, a
-// float2 for f32), the primitive's mean and upstream gradient.
+// float2 for f32), the primitive's mean, upstream gradient and (first lane of
+// the slice) diffuse colour.
 template <typename T>
 struct RawWord;
 template <>
@@ -126,41 +129,56 @@ struct RawItem {
   typename RawWord<T>::type w[P];
   float mu[3];
   float gc[3];
-  int64_t i;  // primitive, -1 if none
+  float c0[3];
+  int32_t ok;   // item holds a primitive
+  uint32_t i;   // primitive (IDX = uint32_t) -- see EvalItem for 64-bit
 };
 
-template <typename T, int P, bool EVEN, bool BWD>
-__device__ __forceinline__ void fetch_item(const EvalArgs& a, int64_t t, int l0, RawItem<T, P>& r) {
+// Element offsets use IDX (uint32_t when P*N*L < 2^31, else uint64_t).
+template <typename T, int P, typename IDX, bool EVEN, bool FWD, bool BWD>
+__device__ __forceinline__ void fetch_item(const EvalArgs& a, IDX t, int l0, RawItem<T, P>& r, IDX& prim) {
   const T* __restrict__ params = static_cast<const T*>(a.params);
-  const int64_t total = a.n_items << a.slice_log2;
-  r.i = -1;
+  const IDX n = IDX(a.n);
+  const IDX total = IDX(a.n_items) << a.slice_log2;
+  r.ok = 0;
   if (t >= total) return;
-  const int64_t item = t >> a.slice_log2;
-  const int64_t i = a.idx ? int64_t(__ldg(a.idx + item)) : item;
-  if (i < 0 || i >= a.n) return;  // out-of-range index entries are skipped
-  r.i = i;
+  const IDX item = t >> a.slice_log2;
+  IDX i = item;
+  if (a.idx) {
+    const int32_t v = __ldg(a.idx + item);
+    if (v < 0) return;  // out-of-range index entries are skipped
+    i = IDX(v);
+  }
+  if (i >= n) return;
+  r.ok = 1;
+  prim = i;
 #pragma unroll
   for (int c = 0; c < 3; ++c) r.mu[c] = __ldg(a.means + 3 * i + c);
   if (BWD) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) r.gc[c] = __ldg(a.g_rgb + 3 * i + c);
   }
-  const int L = a.n_lobes;
-  if (l0 >= L) return;
-  const int64_t NL = a.n * L;
-  const T* pb = params + i * L + l0;
-  const bool second = l0 + 1 < L;
+  if (FWD && l0 == 0) {
+    const T* __restrict__ c0 = static_cast<const T*>(a.c0);
 #pragma unroll
-  for (int p = 0; p < P; ++p) {
+    for (int c = 0; c < 3; ++c) r.c0[c] = load1<T>(c0 + c * n + i);
+  }
+  const IDX L = IDX(a.n_lobes);
+  if (IDX(l0) >= L) return;
+  const IDX NL = n * L;
+  IDX off = i * L + IDX(l0);
+  const bool second = IDX(l0) + 1 < L;
+#pragma unroll
+  for (int p = 0; p < P; ++p, off += NL) {
     if (EVEN) {
-      r.w[p] = __ldg(reinterpret_cast<const typename RawWord<T>::type*>(pb + p * NL));
+      r.w[p] = __ldg(reinterpret_cast<const typename RawWord<T>::type*>(params + off));
     } else if (sizeof(T) == 4) {
-      const float lo = load1<T>(pb + p * NL);
-      float2 v = make_float2(lo, second ? load1<T>(pb + p * NL + 1) : lo);
+      const float lo = load1<T>(params + off);
+      float2 v = make_float2(lo, second ? load1<T>(params + off + 1) : lo);
       r.w[p] = *reinterpret_cast<typename RawWord<T>::type*>(&v);
     } else {
-      const uint32_t lo = *reinterpret_cast<const uint16_t*>(pb + p * NL);
-      const uint32_t hi = second ? *reinterpret_cast<const uint16_t*>(pb + p * NL + 1) : lo;
+      const uint32_t lo = *reinterpret_cast<const uint16_t*>(params + off);
+      const uint32_t hi = second ? *reinterpret_cast<const uint16_t*>(params + off + 1) : lo;
       uint32_t w = lo | (hi << 16);
       r.w[p] = *reinterpret_cast<typename RawWord<T>::type*>(&w);
     }
@@ -170,101 +188,239 @@ __device__ __forceinline__ void fetch_item(const EvalArgs& a, int64_t t, int l0,
 __device__ __forceinline__ P2 unpack(float2 w) { P2 r; r.v = w; return r; }
 __device__ __forceinline__ P2 unpack(uint32_t w) { return p2(bf16_lo(w), bf16_hi(w)); }
 
-// Each lane evaluates two lobes (2g, 2g+1) of its primitive in packed FP32x2
-// arithmetic; a slice of S = next_pow2(ceil(L/2)) lanes covers the primitive.
-// EVEN (L even, planes 2-element aligned): one 2-element load / store per plane.
-// The grid is persistent (a few blocks per SM) and each thread fetches its next
-// item's raw words before computing the current one, so that the loads of one
-// item overlap the arithmetic of the previous.
-template <int FRAME, typename T, int MODE, bool EVEN>
-__global__ void __launch_bounds__(256, 2) eval_kernel(const EvalArgs a) {
+// Evaluates one fetched item: the lane's two lobes, the slice reductions and the
+// per-primitive outputs (first lane of the slice).
+template <int FRAME, typename T, typename IDX, int MODE, bool EVEN>
+__device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, FrameTraits<FRAME>::P>& cur, IDX i,
+                                          int l0) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr bool FWD = (MODE & kFwd) != 0;
   constexpr bool BWD = (MODE & kBwd) != 0;
-  const int64_t n = a.n;
-  const int L = a.n_lobes;
-  const int64_t NL = n * L;
-  const bool identity = a.identity != 0;
-  const bool normalised = a.normalised != 0;
+  const IDX n = IDX(a.n);
+  const IDX L = IDX(a.n_lobes);
   const bool acc = a.accumulate != 0;
-  const int S = a.slice;
-  const int l0 = 2 * (threadIdx.x & (S - 1));
-  const int64_t total = a.n_items << a.slice_log2;
-  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  RawItem<T, P> cur, nxt;
-  int64_t t0 = int64_t(blockIdx.x) * blockDim.x;
-  fetch_item<T, P, EVEN, BWD>(a, t0 + threadIdx.x, l0, cur);
-  // block-uniform loop: every lane of a warp reaches the shuffles below
-  for (; t0 < total; t0 += stride) {
-    fetch_item<T, P, EVEN, BWD>(a, t0 + stride + threadIdx.x, l0, nxt);
-    const int64_t i = cur.i;
-    float rgb[3] = {0.f, 0.f, 0.f};
-    float gd[3] = {0.f, 0.f, 0.f};
-    float d[3] = {0.f, 0.f, 1.f};
-    float inv_dist = 0.f;
-    if (i >= 0) {
-      const float rx = cur.mu[0] - a.cam[0], ry = cur.mu[1] - a.cam[1], rz = cur.mu[2] - a.cam[2];
-      inv_dist = rsqrtf(rx * rx + ry * ry + rz * rz);
-      d[0] = rx * inv_dist; d[1] = ry * inv_dist; d[2] = rz * inv_dist;
-      if (l0 < L) {
-        const bool second = EVEN || (l0 + 1 < L);
-        P2 pv[P];
+  const bool ok = cur.ok != 0;
+  float rgb[3] = {0.f, 0.f, 0.f};
+  float gd[3] = {0.f, 0.f, 0.f};
+  float d[3] = {0.f, 0.f, 1.f};
+  float inv_dist = 0.f;
+  if (ok) {
+    const float rx = cur.mu[0] - a.cam[0], ry = cur.mu[1] - a.cam[1], rz = cur.mu[2] - a.cam[2];
+    inv_dist = rsqrtf(rx * rx + ry * ry + rz * rz);
+    d[0] = rx * inv_dist; d[1] = ry * inv_dist; d[2] = rz * inv_dist;
+    if (IDX(l0) < L) {
+      const bool second = EVEN || (IDX(l0) + 1 < L);
+      P2 pv[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) pv[p] = unpack(cur.w[p]);
-        const P2 dv[3] = {p2(d[0]), p2(d[1]), p2(d[2])};
-        P2 gcv[3] = {p2(0.f), p2(0.f), p2(0.f)};
-        if (BWD) {
+      for (int p = 0; p < P; ++p) pv[p] = unpack(cur.w[p]);
+      const P2 dv[3] = {p2(d[0]), p2(d[1]), p2(d[2])};
+      P2 gcv[3] = {p2(0.f), p2(0.f), p2(0.f)};
+      if (BWD) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) gcv[c] = p2(cur.gc[c]);
-        }
-        P2 rgbv[3] = {p2(0.f), p2(0.f), p2(0.f)};
-        P2 gdv[3] = {p2(0.f), p2(0.f), p2(0.f)};
-        P2 gp[P];
-        lobe_step<FRAME, FWD, BWD>(pv, dv, gcv, identity, normalised, rgbv, gdv, gp);
+        for (int c = 0; c < 3; ++c) gcv[c] = p2(cur.gc[c]);
+      }
+      P2 rgbv[3] = {p2(0.f), p2(0.f), p2(0.f)};
+      P2 gdv[3] = {p2(0.f), p2(0.f), p2(0.f)};
+      P2 gp[P];
+      lobe_step<FRAME, FWD, BWD>(pv, dv, gcv, a.identity != 0, a.normalised != 0, rgbv, gdv, gp);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          rgb[c] = rgbv[c].v.x + (second ? rgbv[c].v.y : 0.f);
-          gd[c] = gdv[c].v.x + (second ? gdv[c].v.y : 0.f);
-        }
-        if (BWD) {
-          float* gb = a.g_params + i * L + l0;
+      for (int c = 0; c < 3; ++c) {
+        rgb[c] = rgbv[c].v.x + (second ? rgbv[c].v.y : 0.f);
+        gd[c] = gdv[c].v.x + (second ? gdv[c].v.y : 0.f);
+      }
+      if (BWD) {
+        const IDX NL = n * L;
+        IDX off = i * L + IDX(l0);
 #pragma unroll
-          for (int p = 0; p < P; ++p) {
-            if (EVEN) {
-              store2(gb + p * NL, gp[p], acc);
-            } else {
-              store1(gb + p * NL, gp[p].v.x, acc);
-              if (second) store1(gb + p * NL + 1, gp[p].v.y, acc);
-            }
+        for (int p = 0; p < P; ++p, off += NL) {
+          if (EVEN) {
+            store2(a.g_params + off, gp[p], acc);
+          } else {
+            store1(a.g_params + off, gp[p].v.x, acc);
+            if (second) store1(a.g_params + off + 1, gp[p].v.y, acc);
           }
         }
       }
     }
-    for (int o = S >> 1; o >= 1; o >>= 1) {
+  }
+  for (int o = a.slice >> 1; o >= 1; o >>= 1) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if (FWD) rgb[c] += __shfl_xor_sync(0xffffffffu, rgb[c], o);
-        if (BWD) gd[c] += __shfl_xor_sync(0xffffffffu, gd[c], o);
+    for (int c = 0; c < 3; ++c) {
+      if (FWD) rgb[c] += __shfl_xor_sync(0xffffffffu, rgb[c], o);
+      if (BWD) gd[c] += __shfl_xor_sync(0xffffffffu, gd[c], o);
+    }
+  }
+  if (ok && l0 == 0) {
+    if (FWD) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a.rgb[3 * i + c] = rgb[c] + cur.c0[c];
+    }
+    if (BWD) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) store1(a.g_c0 + c * n + i, cur.gc[c], acc);
+      if (a.g_means) {
+        float gm[3];
+        dir_grad(d, gd, inv_dist, gm);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) store1(a.g_means + 3 * i + c, gm[c], acc);
       }
     }
-    if (i >= 0 && l0 == 0) {
-      if (FWD) {
-        const T* __restrict__ c0 = static_cast<const T*>(a.c0);
+  }
+}
+
+// Each lane evaluates two lobes (2g, 2g+1) of its primitive in packed FP32x2
+// arithmetic; a slice of S = next_pow2(ceil(L/2)) lanes covers the primitive.
+// EVEN (L even, planes 2-element aligned): one 2-element load / store per plane.
+// The grid is persistent (as many blocks as fit) and each thread fetches its
+// next item's raw words before computing the current one (two buffers used in
+// turn), so that the loads of one item overlap the arithmetic of the previous.
+template <int FRAME, typename T, typename IDX, int MODE, bool EVEN>
+__global__ void __launch_bounds__(256, 2) eval_kernel(const EvalArgs a) {
+  constexpr int P = FrameTraits<FRAME>::P;
+  constexpr bool FWD = (MODE & kFwd) != 0;
+  constexpr bool BWD = (MODE & kBwd) != 0;
+  const int l0 = 2 * (threadIdx.x & (a.slice - 1));
+  const IDX total = IDX(a.n_items) << a.slice_log2;
+  const IDX stride = IDX(gridDim.x) * blockDim.x;
+  RawItem<T, P> b0, b1;
+  IDX i0 = 0, i1 = 0;
+  IDX t0 = IDX(blockIdx.x) * blockDim.x;
+  fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, t0 + threadIdx.x, l0, b0, i0);
+  // block-uniform loop: every lane of a warp reaches the shuffles
+  while (t0 < total) {
+    fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, t0 + stride + threadIdx.x, l0, b1, i1);
+    eval_item<FRAME, T, IDX, MODE, EVEN>(a, b0, i0, l0);
+    t0 += stride;
+    if (t0 >= total) break;
+    fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, t0 + stride + threadIdx.x, l0, b0, i0);
+    eval_item<FRAME, T, IDX, MODE, EVEN>(a, b1, i1, l0);
+    t0 += stride;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged variant: tiles of TP = 256/S consecutive primitives. For a tile,
+// every parameter plane is one contiguous span of TP*L elements, and the means,
+// upstream gradients and diffuse colours are contiguous too, so one elected
+// thread moves a whole tile into shared memory with bulk asynchronous copies
+// (cp.async.bulk) completing on the stage's mbarrier. kStages tiles are in
+// flight per block; the threads of the block read their lane's words from the
+// stage, release it with a block barrier, and the elected thread refills it
+// with the tile kStages ahead. Requirements (checked on the host): no index
+// list, N % 8 == 0, L even, 16-byte aligned buffers, 32-bit offsets.
+// ---------------------------------------------------------------------------
+constexpr int kStages = 3;
+
+struct TileGeom {
+  uint32_t tp;          // primitives per tile
+  uint32_t plane_bytes; // bytes of one plane's span in a stage
+  uint32_t off_mu, off_gc, off_c0, stage_bytes;
+};
+
+template <typename T, int P>
+__host__ __device__ inline TileGeom tile_geom(int slice_log2, int n_lobes) {
+  TileGeom g;
+  g.tp = 256u >> slice_log2;
+  g.plane_bytes = g.tp * uint32_t(n_lobes) * uint32_t(sizeof(T));
+  g.off_mu = P * g.plane_bytes;
+  g.off_gc = g.off_mu + g.tp * 12u;
+  g.off_c0 = g.off_gc + g.tp * 12u;
+  g.stage_bytes = (g.off_c0 + 3u * g.tp * uint32_t(sizeof(T)) + 127u) & ~127u;
+  return g;
+}
+
+template <typename T, int P, bool FWD, bool BWD>
+__device__ __forceinline__ void issue_tile(const EvalArgs& a, const TileGeom& g, uint32_t tile, unsigned char* st,
+                                           uint64_t* bar) {
+  const uint32_t n = uint32_t(a.n), L = uint32_t(a.n_lobes);
+  const uint32_t p0 = tile * g.tp;
+  const uint32_t count = min(g.tp, n - p0);
+  const uint32_t bp = count * L * uint32_t(sizeof(T));
+  const uint32_t bm = count * 12u;
+  const uint32_t bc = count * uint32_t(sizeof(T));
+  const uint32_t total = P * bp + bm + (BWD ? bm : 0u) + (FWD ? 3u * bc : 0u);
+  mbar_arrive_expect_tx(bar, total);
+  const T* params = static_cast<const T*>(a.params);
+  const uint32_t NL = n * L;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) a.rgb[3 * i + c] = rgb[c] + load1<T>(c0 + c * n + i);
-      }
+  for (int p = 0; p < P; ++p) bulk_g2s(st + p * g.plane_bytes, params + p * NL + p0 * L, bp, bar);
+  bulk_g2s(st + g.off_mu, a.means + 3u * p0, bm, bar);
+  if (BWD) bulk_g2s(st + g.off_gc, a.g_rgb + 3u * p0, bm, bar);
+  if (FWD) {
+    const T* c0 = static_cast<const T*>(a.c0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) bulk_g2s(st + g.off_c0 + c * g.tp * sizeof(T), c0 + c * n + p0, bc, bar);
+  }
+}
+
+template <int FRAME, typename T, int MODE>
+__global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
+  constexpr int P = FrameTraits<FRAME>::P;
+  constexpr bool FWD = (MODE & kFwd) != 0;
+  constexpr bool BWD = (MODE & kBwd) != 0;
+  using W = typename RawWord<T>::type;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const TileGeom g = tile_geom<T, P>(a.slice_log2, a.n_lobes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * g.stage_bytes);
+  const uint32_t n = uint32_t(a.n), L = uint32_t(a.n_lobes);
+  const uint32_t n_tiles = (n + g.tp - 1) / g.tp;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < kStages; ++s) {
+      const uint32_t tile = blockIdx.x + s * gridDim.x;
+      if (tile < n_tiles) issue_tile<T, P, FWD, BWD>(a, g, tile, smem + s * g.stage_bytes, &bars[s]);
+    }
+  }
+  const uint32_t local = threadIdx.x >> a.slice_log2;
+  const int l0 = 2 * (threadIdx.x & (a.slice - 1));
+  for (uint32_t it = 0;; ++it) {
+    const uint32_t tile = blockIdx.x + it * gridDim.x;
+    if (tile >= n_tiles) break;  // block-uniform
+    const int s = it % kStages;
+    unsigned char* st = smem + s * g.stage_bytes;
+    const bool arrived = mbar_wait(&bars[s], (it / kStages) & 1u, a.dev_err);
+    const uint32_t p0 = tile * g.tp;
+    const uint32_t count = min(g.tp, n - p0);
+    RawItem<T, P> r;
+    r.ok = arrived && local < count;
+    const uint32_t i = p0 + local;
+    if (r.ok) {
+      const float* mu = reinterpret_cast<const float*>(st + g.off_mu);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) r.mu[c] = mu[3 * local + c];
       if (BWD) {
+        const float* gc = reinterpret_cast<const float*>(st + g.off_gc);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) store1(a.g_c0 + c * n + i, cur.gc[c], acc);
-        if (a.g_means) {
-          float gm[3];
-          dir_grad(d, gd, inv_dist, gm);
+        for (int c = 0; c < 3; ++c) r.gc[c] = gc[3 * local + c];
+      }
+      if (FWD && l0 == 0) {
+        // plain shared-memory reads (load1 uses the global read-only path)
+        const T* c0 = reinterpret_cast<const T*>(st + g.off_c0);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) store1(a.g_means + 3 * i + c, gm[c], acc);
-        }
+        for (int c = 0; c < 3; ++c) r.c0[c] = to_float(c0[c * g.tp + local]);
+      }
+      if (uint32_t(l0) < L) {
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+          r.w[p] = *reinterpret_cast<const W*>(st + p * g.plane_bytes + (local * L + l0) * sizeof(T));
       }
     }
-    cur = nxt;
+    // the stage is read: release it (and leave together if a wait timed out)
+    if (__syncthreads_or(!arrived)) return;
+    if (threadIdx.x == 0) {
+      const uint32_t next = tile + kStages * gridDim.x;
+      if (next < n_tiles) {
+        fence_proxy_async();
+        issue_tile<T, P, FWD, BWD>(a, g, next, st, &bars[s]);
+      }
+    }
+    eval_item<FRAME, T, uint32_t, MODE, true>(a, r, i, l0);
   }
 }
 
@@ -293,22 +449,66 @@ unsigned persistent_grid(K kernel, int64_t threads, int block) {
   return need < cap ? need : cap;
 }
 
-template <int MODE, int FRAME, typename T>
-nasg_status launch_frame_dtype(const EvalArgs& a, bool even, cudaStream_t s) {
+template <int MODE, int FRAME, typename T, typename IDX>
+nasg_status launch_idx(const EvalArgs& a, bool even, cudaStream_t s) {
   constexpr int kBlock = kEvalBlock;
   const int64_t threads = a.n_items << a.slice_log2;
   if (even) {
-    auto k = eval_kernel<FRAME, T, MODE, true>;
+    auto k = eval_kernel<FRAME, T, IDX, MODE, true>;
     k<<<persistent_grid(k, threads, kBlock), kBlock, 0, s>>>(a);
   } else {
-    auto k = eval_kernel<FRAME, T, MODE, false>;
+    auto k = eval_kernel<FRAME, T, IDX, MODE, false>;
     k<<<persistent_grid(k, threads, kBlock), kBlock, 0, s>>>(a);
   }
   return check_launch();
 }
 
+// The TMA-staged kernel applies (see its requirements above).
+template <int FRAME, typename T>
+bool tma_eligible(const EvalArgs& a, bool even) {
+  if (!even || a.idx != nullptr || a.n % 8 != 0 || a.n_items != a.n) return false;
+  if (a.n * a.n_lobes * FrameTraits<FRAME>::P >= (int64_t(1) << 31)) return false;
+  const void* ptrs[] = {a.params, a.means, a.c0, a.g_rgb};
+  for (const void* p : ptrs)
+    if (p && !aligned(p, 16)) return false;
+  return true;
+}
+
+template <int MODE, int FRAME, typename T>
+nasg_status launch_tma(const EvalArgs& a, cudaStream_t s) {
+  constexpr int P = FrameTraits<FRAME>::P;
+  const TileGeom g = tile_geom<T, P>(a.slice_log2, a.n_lobes);
+  const size_t smem = size_t(kStages) * g.stage_bytes + kStages * sizeof(uint64_t);
+  auto k = eval_tma_kernel<FRAME, T, MODE>;
+  static size_t configured = 0;  // per instantiation
+  if (smem > configured) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+      return check_launch();
+    configured = smem;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+  const uint32_t n_tiles = uint32_t((a.n + g.tp - 1) / g.tp);
+  const uint32_t cap = uint32_t(sm_count() * per_sm);
+  k<<<n_tiles < cap ? n_tiles : cap, 256, smem, s>>>(a);
+  return check_launch();
+}
+
+template <int MODE, int FRAME, typename T>
+nasg_status launch_frame_dtype(const EvalArgs& a, bool even, cudaStream_t s) {
+  if (tma_eligible<FRAME, T>(a, even)) return launch_tma<MODE, FRAME, T>(a, s);
+  // 32-bit element offsets when every offset the kernel forms (P*N*L elements,
+  // 3*N, and the thread index including one stride of prefetch) stays below 2^31.
+  const int64_t NL = a.n * a.n_lobes;
+  const int64_t threads = a.n_items << a.slice_log2;
+  const int64_t lim = int64_t(1) << 31;
+  const bool idx32 = NL * FrameTraits<FRAME>::P < lim && 3 * a.n < lim && 2 * threads + (int64_t(1) << 24) < lim;
+  return idx32 ? launch_idx<MODE, FRAME, T, uint32_t>(a, even, s) : launch_idx<MODE, FRAME, T, uint64_t>(a, even, s);
+}
+
 template <int MODE>
 nasg_status launch_eval(const nasg_desc* desc, EvalArgs a, cudaStream_t s) {
+  a.dev_err = device_error_word();
   a.slice_log2 = slice_log2(desc->n_lobes);
   a.slice = 1 << a.slice_log2;
   const int es = elem_size(desc->param_dtype);

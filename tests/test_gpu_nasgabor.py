@@ -234,3 +234,40 @@ def test_empty_problem(lib):
     assert g[0].shape == (10, 0)
     assert lib.sh_eval_fwd(torch.zeros((16, 3, 0), device="cuda"), torch.zeros((0, 3), device="cuda"),
                            (0, 0, 3)).shape == (0, 3)
+
+
+def test_bounded_wait_reports_device_error(lib):
+    """A kernel whose barrier never completes gives up after its iteration limit and
+    sets the device error word; the context stays usable."""
+    import torch
+    lib.nasg_device_status()  # clear
+    lib.nasg_probe_wait_timeout(1024)
+    with pytest.raises(lib.NasgError) as ei:
+        lib.nasg_device_status()
+    assert ei.value.status == -6
+    lib.nasg_device_status()  # cleared by the previous query
+    x = torch.ones(16, device="cuda")
+    assert float((x * 2).sum()) == 32.0
+
+
+@pytest.mark.parametrize("bf16,n,L", [(True, 4096, 8), (False, 4096, 8), (True, 1000, 4), (True, 2056, 16),
+                                      (False, 1048, 2), (True, 8, 8)])
+def test_staged_path_matches_oracle(lib, bf16, n, L):
+    """Sizes that take the bulk-copy staged kernel (N % 8 == 0, even L), with a
+    ragged last tile, against the oracle; and the same against the register path
+    (an offset view breaks the 16-byte alignment the staged kernel needs)."""
+    import torch
+    w = inputs.point_cloud_workload(n, L, 31 + n + L)
+    _check_forward(lib, w, bf16)
+    _check_backward(lib, w, bf16)
+    params, c0, _, _ = _prepare(w, bf16)
+    means, g_rgb = _dev(w.means), _dev(w.g_rgb)
+    f = lib.nasgabor_fused_fwd_bwd(params, c0, means, w.cam, g_rgb, L)
+    big = torch.empty(params.numel() + 16, device="cuda", dtype=params.dtype)
+    shifted = big[2:2 + params.numel()].view(params.shape)   # 4 or 8 bytes off 16-byte alignment
+    shifted.copy_(params)
+    r = lib.nasgabor_fused_fwd_bwd(shifted, c0, means, w.cam, g_rgb, L)
+    lib.nasg_device_status()
+    torch.testing.assert_close(r[0], f[0], rtol=1e-6, atol=1e-6)
+    fg, rg = f[1].cpu().numpy(), r[1].cpu().numpy()
+    assert max(rel_l2(rg[p], fg[p]) for p in range(fg.shape[0])) < 1e-6
