@@ -242,9 +242,8 @@ __device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a
   const V ln_e = tau * ln_k;                                      // ln E
   const V em1 = vexpm1n(ln_e + ln_k);                             // E kappa - 1
   const V pe = vexp(vfma(2.f * lam, em1, ln_e));                  // p E
-  V sh, ch;
-  vsincos(0.5f * k * v, sh, ch);
-  const V h = ch * ch;
+  V h, sin_kv;  // (1 + cos(k v))/2 and sin(k v)
+  vcarrier(0.5f * k * v, h, sin_kv);
   V cinv = vconst<V>(1.f), dlnc_dlam = vconst<V>(0.f), dlnc_da = vconst<V>(0.f);
   if (normalised) {
     const V em = vexpm1n(-2.f * lam);  // e^{-2 lam} - 1 (negative)
@@ -257,8 +256,10 @@ __device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a
       dlnc_da = 0.5f * vrcp(opa);
     }
   }
-  const V cpe = cinv * pe;
-  const V G = vsel(anti, 0.f, cpe * h);
+  // the antipode (G := 0 with zero derivatives) is applied once, through C^-1 p E;
+  // every other factor below is finite there (tau, ln kappa, 1/(1+u) are 0)
+  const V cpe = vsel(anti, 0.f, cinv * pe);
+  const V G = cpe * h;
   if (GRAD) {
     const V ek = em1 + 1.f;                             // E kappa
     const V two_lam_ek = 2.f * lam * ek;
@@ -266,12 +267,12 @@ __device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a
     const V dtau_dv = 2.f * a * v * inv_s2;
     const V dlne_du = vfma(ln_k, dtau_du, tau * inv_opu);
     const V dlne_dv = ln_k * dtau_dv;
-    const V cpe_sin = cpe * (2.f * sh * ch);            // C^-1 p E sin(k v)
-    pd->G_u = vsel(anti, 0.f, G * vfma(two_lam_ek, dlne_du + inv_opu, dlne_du));
-    pd->G_v = vsel(anti, 0.f, vfma(G * (two_lam_ek + 1.f), dlne_dv, -(cpe_sin * (0.5f * k))));
-    pd->G_k = vsel(anti, 0.f, -(cpe_sin * (0.5f * v)));
-    pd->G_lam = vsel(anti, 0.f, G * vfma(2.f, em1, dlnc_dlam));
-    pd->G_a = vsel(anti, 0.f, G * vfma((two_lam_ek + 1.f) * ln_k, v * v * inv_s2, dlnc_da));
+    const V cpe_sin = cpe * sin_kv;                     // C^-1 p E sin(k v)
+    pd->G_u = G * vfma(two_lam_ek, dlne_du + inv_opu, dlne_du);
+    pd->G_v = vfma(G * (two_lam_ek + 1.f), dlne_dv, -(cpe_sin * (0.5f * k)));
+    pd->G_k = -(cpe_sin * (0.5f * v));
+    pd->G_lam = G * vfma(2.f, em1, dlnc_dlam);
+    pd->G_a = G * vfma((two_lam_ek + 1.f) * ln_k, v * v * inv_s2, dlnc_da);
   }
   return G;
 }

@@ -9,15 +9,16 @@
 //   vexpm1n(y)    e^y - 1 for y <= 0: Taylor polynomial to y^9 on [-0.5, 0]
 //                 (truncation < 3e-10 relative), 2^(y log2 e) - 1 below -0.5
 //                 (|result| >= 0.39 there, so the subtraction loses nothing).
-//   vtanh(x)      e = e^{-2|x|} - 1, tanh|x| = -e/(2 + e), and
-//                 1 - tanh^2 x = 4 e^{-2|x|}/(2 + e)^2 without cancellation.
+//   vtanh(x)      odd Taylor series to x^9 for |x| < 1/4, else
+//                 (1 - e)/(1 + e) with e = e^{-2|x|}; 1 - tanh^2 x = 4 e/(1 + e)^2.
 //   vlnkappa(t)   ln(1 + t) for t in [-1, 0]: 2 atanh(t/(2 + t)) series to
 //                 s^9 where 1 + t >= 0.75, lg2.approx elsewhere.
-//   vsincos(x)    |x| <= 6400: Cody-Waite reduction x = n pi/2 + r with pi/2
-//                 split in three float parts (the first two with 12
-//                 significant bits, so n*C1 and n*C2 are exact), Taylor
-//                 polynomials of sin (to r^9) and cos (to r^10) on
-//                 |r| <= pi/4 (truncation < 3e-9), then the quadrant rotation.
+//   vcarrier(x)   cos^2 x and sin 2x (the NASGabor carrier and its slope) for
+//                 |x| <= 6400; vsincos(x) gives sin x, cos x from the same
+//                 Cody-Waite reduction x = n pi/2 + r with pi/2 split in three
+//                 float parts (the first two with 12 significant bits, so n*C1
+//                 and n*C2 are exact) and the Taylor polynomials of sin (to r^9)
+//                 and cos (to r^10) on |r| <= pi/4 (truncation < 3e-9).
 #pragma once
 
 #include "nasg_vec.cuh"
@@ -57,12 +58,20 @@ __device__ __forceinline__ V vexpm1n(V y) {
 
 template <class V>
 __device__ __forceinline__ void vtanh(V x, V& t, V& sech2) {
-  const V y = -2.f * vabs(x);
-  const V ex = vex2(y * kLog2e);                        // e^{-2|x|}
-  const V e = vsel(vgt(y, -0.5f), taylor_expm1(y), ex - 1.f);  // e^{-2|x|} - 1
-  const V inv = vrcp(2.f + e);
-  t = vcopysign(-e * inv, x);
-  sech2 = 4.f * ex * inv * inv;
+  // |x| < 1/4: odd Taylor series x - x^3/3 + 2x^5/15 - 17x^7/315 + 62x^9/2835
+  // (truncation < 3e-9 relative); else tanh|x| = (1 - e)/(1 + e), e = e^{-2|x|}
+  // (1 - e >= 0.39 there, no cancellation).
+  const V x2 = x * x;
+  V q = vfma(x2, 62.f / 2835.f, -17.f / 315.f);
+  q = vfma(q, x2, 2.f / 15.f);
+  q = vfma(q, x2, -1.f / 3.f);
+  q = vfma(q, x2, 1.f);
+  const V ax = vabs(x);
+  const V ex = vex2(ax * (-2.f * kLog2e));  // e^{-2|x|}
+  const V inv = vrcp(1.f + ex);
+  const V tl = vcopysign((1.f - ex) * inv, x);
+  t = vsel(vlt(ax, 0.25f), x * q, tl);
+  sech2 = 4.f * ex * (inv * inv);           // 1 - tanh^2 = 4 e/(1 + e)^2
 }
 
 template <class V>
@@ -78,20 +87,27 @@ __device__ __forceinline__ V vlnkappa(V t, V kap) {
   return vsel(vge(kap, 0.75f), ser, lg);
 }
 
-__device__ __forceinline__ void quadrant(float n, float ps, float pc, float& s, float& c) {
-  const int q = static_cast<int>(n) & 3;
-  const float ss = (q & 1) ? pc : ps;
-  const float cc = (q & 1) ? ps : pc;
-  s = (q & 2) ? -ss : ss;
-  c = ((q + 1) & 2) ? -cc : cc;
+// Parity of the integer-valued float n.
+__device__ __forceinline__ bool odd(float n) { return (static_cast<int>(n) & 1) != 0; }
+
+__device__ __forceinline__ void carrier_fix(float n, float ps, float pc, float& h, float& s2x) {
+  const bool o = odd(n);
+  h = o ? ps * ps : pc * pc;
+  const float sc = 2.f * ps * pc;
+  s2x = o ? -sc : sc;
 }
-__device__ __forceinline__ void quadrant(P2 n, P2 ps, P2 pc, P2& s, P2& c) {
-  quadrant(n.v.x, ps.v.x, pc.v.x, s.v.x, c.v.x);
-  quadrant(n.v.y, ps.v.y, pc.v.y, s.v.y, c.v.y);
+__device__ __forceinline__ void carrier_fix(P2 n, P2 ps, P2 pc, P2& h, P2& s2x) {
+  carrier_fix(n.v.x, ps.v.x, pc.v.x, h.v.x, s2x.v.x);
+  carrier_fix(n.v.y, ps.v.y, pc.v.y, h.v.y, s2x.v.y);
 }
 
+// The NASGabor carrier at x = k v / 2 (|x| <= 6400): h = cos^2 x = (1 + cos(k v))/2
+// and sin 2x = sin(k v). With x = n pi/2 + r (Cody-Waite, pi/2 in three float
+// parts, the first two with 12 significant bits so n*C1 and n*C2 are exact),
+// cos^2 x is cos^2 r or sin^2 r by the parity of n, and sin 2x = (-1)^n 2 sin r cos r,
+// with the Taylor polynomials of sin (to r^9) and cos (to r^10) on |r| <= pi/4.
 template <class V>
-__device__ __forceinline__ void vsincos(V x, V& s, V& c) {
+__device__ __forceinline__ void vcarrier(V x, V& h, V& s2x) {
   constexpr float kTwoOverPi = 0.636619772367581343f;
   constexpr float kC1 = 1.5703125f;                // pi/2, first 12 bits
   constexpr float kC2 = 4.837512969970703125e-4f;  // next 12 bits
@@ -101,18 +117,51 @@ __device__ __forceinline__ void vsincos(V x, V& s, V& c) {
   r = vfma(n, -kC2, r);
   r = vfma(n, -kC3, r);
   const V r2 = r * r;
-  // sin r = r (1 - r^2/3! + r^4/5! - r^6/7! + r^8/9!)
   V ps = vfma(r2, kF9, -kF7);
   ps = vfma(ps, r2, kF5);
   ps = vfma(ps, r2, -kF3);
   ps = vfma(ps, r2, 1.f);
   ps = ps * r;
-  // cos r = 1 - r^2/2! + r^4/4! - r^6/6! + r^8/8! - r^10/10!
   V pc = vfma(r2, -1.f / 3628800.f, kF8);
   pc = vfma(pc, r2, -kF6);
   pc = vfma(pc, r2, kF4);
   pc = vfma(pc, r2, -kF2);
   pc = vfma(pc, r2, 1.f);
+  carrier_fix(n, ps, pc, h, s2x);
+}
+
+// sin x and cos x (|x| <= 6400) from the same reduction, with the quadrant rotation.
+__device__ __forceinline__ void quadrant(float n, float ps, float pc, float& s, float& c) {
+  const int q = static_cast<int>(n) & 3;
+  const float ss = (q & 1) ? pc : ps;
+  const float cc = (q & 1) ? ps : pc;
+  s = (q & 2) ? -ss : ss;
+  c = ((q + 1) & 2) ? -cc : cc;
+}
+
+template <class V>
+__device__ __forceinline__ void vsincos(V x, V& s, V& c);
+template <>
+__device__ __forceinline__ void vsincos<float>(float x, float& s, float& c) {
+  constexpr float kTwoOverPi = 0.636619772367581343f;
+  constexpr float kC1 = 1.5703125f;
+  constexpr float kC2 = 4.837512969970703125e-4f;
+  constexpr float kC3 = 7.549790126404332e-8f;
+  const float n = rintf(x * kTwoOverPi);
+  float r = fmaf(-n, kC1, x);
+  r = fmaf(-n, kC2, r);
+  r = fmaf(-n, kC3, r);
+  const float r2 = r * r;
+  float ps = fmaf(r2, kF9, -kF7);
+  ps = fmaf(ps, r2, kF5);
+  ps = fmaf(ps, r2, -kF3);
+  ps = fmaf(ps, r2, 1.f);
+  ps = ps * r;
+  float pc = fmaf(r2, -1.f / 3628800.f, kF8);
+  pc = fmaf(pc, r2, -kF6);
+  pc = fmaf(pc, r2, kF4);
+  pc = fmaf(pc, r2, -kF2);
+  pc = fmaf(pc, r2, 1.f);
   quadrant(n, ps, pc, s, c);
 }
 

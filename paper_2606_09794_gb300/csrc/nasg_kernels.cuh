@@ -158,7 +158,7 @@ __device__ __forceinline__ void fetch_item(const EvalArgs& a, IDX t, int l0, Raw
 #pragma unroll
     for (int c = 0; c < 3; ++c) r.gc[c] = __ldg(a.g_rgb + 3 * i + c);
   }
-  if (FWD && l0 == 0) {
+  if (FWD) {
     const T* __restrict__ c0 = static_cast<const T*>(a.c0);
 #pragma unroll
     for (int c = 0; c < 3; ++c) r.c0[c] = load1<T>(c0 + c * n + i);
@@ -188,9 +188,32 @@ __device__ __forceinline__ void fetch_item(const EvalArgs& a, IDX t, int l0, Raw
 __device__ __forceinline__ P2 unpack(float2 w) { P2 r; r.v = w; return r; }
 __device__ __forceinline__ P2 unpack(uint32_t w) { return p2(bf16_lo(w), bf16_hi(w)); }
 
+// Mode flags: FLAGS < 0 reads act_mode / norm_mode / accumulate from the
+// arguments at run time; FLAGS >= 0 fixes them at compile time (bit 0 identity
+// activations, bit 1 unnormalised, bit 2 accumulate) so that the common mode
+// (raw activations, normalised, overwrite: kFlagsDefault) carries no untaken
+// predicated paths.
+constexpr int kFlagsRuntime = -1;
+constexpr int kFlagsDefault = 0;
+
+template <int FLAGS>
+struct Flags {
+  __device__ __forceinline__ static bool identity(const EvalArgs& a) {
+    return FLAGS < 0 ? a.identity != 0 : (FLAGS & 1) != 0;
+  }
+  __device__ __forceinline__ static bool normalised(const EvalArgs& a) {
+    return FLAGS < 0 ? a.normalised != 0 : (FLAGS & 2) == 0;
+  }
+  __device__ __forceinline__ static bool accumulate(const EvalArgs& a) {
+    return FLAGS < 0 ? a.accumulate != 0 : (FLAGS & 4) != 0;
+  }
+};
+
+__device__ __forceinline__ float pick3(const float v[3], int c) { return c == 0 ? v[0] : (c == 1 ? v[1] : v[2]); }
+
 // Evaluates one fetched item: the lane's two lobes, the slice reductions and the
-// per-primitive outputs (first lane of the slice).
-template <int FRAME, typename T, typename IDX, int MODE, bool EVEN>
+// per-primitive outputs, whose three channels are spread over the slice's lanes.
+template <int FRAME, typename T, typename IDX, int MODE, bool EVEN, int FLAGS>
 __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, FrameTraits<FRAME>::P>& cur, IDX i,
                                           int l0) {
   constexpr int P = FrameTraits<FRAME>::P;
@@ -198,7 +221,7 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
   constexpr bool BWD = (MODE & kBwd) != 0;
   const IDX n = IDX(a.n);
   const IDX L = IDX(a.n_lobes);
-  const bool acc = a.accumulate != 0;
+  const bool acc = Flags<FLAGS>::accumulate(a);
   const bool ok = cur.ok != 0;
   float rgb[3] = {0.f, 0.f, 0.f};
   float gd[3] = {0.f, 0.f, 0.f};
@@ -222,7 +245,8 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
       P2 rgbv[3] = {p2(0.f), p2(0.f), p2(0.f)};
       P2 gdv[3] = {p2(0.f), p2(0.f), p2(0.f)};
       P2 gp[P];
-      lobe_step<FRAME, FWD, BWD>(pv, dv, gcv, a.identity != 0, a.normalised != 0, rgbv, gdv, gp);
+      lobe_step<FRAME, FWD, BWD>(pv, dv, gcv, Flags<FLAGS>::identity(a), Flags<FLAGS>::normalised(a), rgbv, gdv,
+                                 gp);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         rgb[c] = rgbv[c].v.x + (second ? rgbv[c].v.y : 0.f);
@@ -231,18 +255,31 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
       if (BWD) {
         const IDX NL = n * L;
         IDX off = i * L + IDX(l0);
+        if (acc) {
 #pragma unroll
-        for (int p = 0; p < P; ++p, off += NL) {
-          if (EVEN) {
-            store2(a.g_params + off, gp[p], acc);
-          } else {
-            store1(a.g_params + off, gp[p].v.x, acc);
-            if (second) store1(a.g_params + off + 1, gp[p].v.y, acc);
+          for (int p = 0; p < P; ++p, off += NL) {
+            if (EVEN) {
+              store2(a.g_params + off, gp[p], true);
+            } else {
+              store1(a.g_params + off, gp[p].v.x, true);
+              if (second) store1(a.g_params + off + 1, gp[p].v.y, true);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int p = 0; p < P; ++p, off += NL) {
+            if (EVEN) {
+              store2(a.g_params + off, gp[p], false);
+            } else {
+              store1(a.g_params + off, gp[p].v.x, false);
+              if (second) store1(a.g_params + off + 1, gp[p].v.y, false);
+            }
           }
         }
       }
     }
   }
+  // xor-butterfly over the slice: every lane ends with the primitive's sums
   for (int o = a.slice >> 1; o >= 1; o >>= 1) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -250,19 +287,14 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
       if (BWD) gd[c] += __shfl_xor_sync(0xffffffffu, gd[c], o);
     }
   }
-  if (ok && l0 == 0) {
-    if (FWD) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) a.rgb[3 * i + c] = rgb[c] + cur.c0[c];
-    }
-    if (BWD) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) store1(a.g_c0 + c * n + i, cur.gc[c], acc);
-      if (a.g_means) {
-        float gm[3];
-        dir_grad(d, gd, inv_dist, gm);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) store1(a.g_means + 3 * i + c, gm[c], acc);
+  if (ok) {
+    const float dot = BWD ? gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2] : 0.f;
+    for (int c = l0 >> 1; c < 3; c += a.slice) {
+      if (FWD) a.rgb[3 * i + c] = pick3(rgb, c) + pick3(cur.c0, c);
+      if (BWD) {
+        store1(a.g_c0 + c * n + i, pick3(cur.gc, c), acc);
+        // dLoss/dmu = (I - d d^T) dLoss/dd / |mu - cam|
+        if (a.g_means) store1(a.g_means + 3 * i + c, (pick3(gd, c) - dot * pick3(d, c)) * inv_dist, acc);
       }
     }
   }
@@ -276,6 +308,7 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
 // turn), so that the loads of one item overlap the arithmetic of the previous.
 template <int FRAME, typename T, typename IDX, int MODE, bool EVEN>
 __global__ void __launch_bounds__(256, 2) eval_kernel(const EvalArgs a) {
+  constexpr int FLAGS = kFlagsRuntime;
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr bool FWD = (MODE & kFwd) != 0;
   constexpr bool BWD = (MODE & kBwd) != 0;
@@ -289,11 +322,11 @@ __global__ void __launch_bounds__(256, 2) eval_kernel(const EvalArgs a) {
   // block-uniform loop: every lane of a warp reaches the shuffles
   while (t0 < total) {
     fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, t0 + stride + threadIdx.x, l0, b1, i1);
-    eval_item<FRAME, T, IDX, MODE, EVEN>(a, b0, i0, l0);
+    eval_item<FRAME, T, IDX, MODE, EVEN, FLAGS>(a, b0, i0, l0);
     t0 += stride;
     if (t0 >= total) break;
     fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, t0 + stride + threadIdx.x, l0, b0, i0);
-    eval_item<FRAME, T, IDX, MODE, EVEN>(a, b1, i1, l0);
+    eval_item<FRAME, T, IDX, MODE, EVEN, FLAGS>(a, b1, i1, l0);
     t0 += stride;
   }
 }
@@ -303,13 +336,15 @@ __global__ void __launch_bounds__(256, 2) eval_kernel(const EvalArgs a) {
 // every parameter plane is one contiguous span of TP*L elements, and the means,
 // upstream gradients and diffuse colours are contiguous too, so one elected
 // thread moves a whole tile into shared memory with bulk asynchronous copies
-// (cp.async.bulk) completing on the stage's mbarrier. kStages tiles are in
-// flight per block; the threads of the block read their lane's words from the
-// stage, release it with a block barrier, and the elected thread refills it
-// with the tile kStages ahead. Requirements (checked on the host): no index
-// list, N % 8 == 0, L even, 16-byte aligned buffers, 32-bit offsets.
+// (cp.async.bulk) completing on the stage's "full" mbarrier. kStages tiles are
+// in flight per block; each warp reads its lanes' words from the stage and
+// arrives on the stage's "empty" mbarrier; one iteration later the elected
+// thread waits for that stage to be empty and refills it with the tile kStages
+// ahead. No block-wide barrier is taken inside the loop, and every wait is
+// bounded. Requirements (checked on the host): no index list, N % 8 == 0,
+// L even, 16-byte aligned buffers, 32-bit offsets.
 // ---------------------------------------------------------------------------
-constexpr int kStages = 3;
+constexpr int kStages = 4;
 
 struct TileGeom {
   uint32_t tp;          // primitives per tile
@@ -353,7 +388,7 @@ __device__ __forceinline__ void issue_tile(const EvalArgs& a, const TileGeom& g,
   }
 }
 
-template <int FRAME, typename T, int MODE>
+template <int FRAME, typename T, int MODE, int FLAGS>
 __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr bool FWD = (MODE & kFwd) != 0;
@@ -361,12 +396,17 @@ __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
   using W = typename RawWord<T>::type;
   extern __shared__ __align__(128) unsigned char smem[];
   const TileGeom g = tile_geom<T, P>(a.slice_log2, a.n_lobes);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * g.stage_bytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * g.stage_bytes);  // tile landed
+  uint64_t* empty = full + kStages;                                             // tile read by all warps
   const uint32_t n = uint32_t(a.n), L = uint32_t(a.n_lobes);
   const uint32_t n_tiles = (n + g.tp - 1) / g.tp;
+  const uint32_t n_warps = blockDim.x >> 5;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], n_warps);
+    }
     fence_barrier_init();
   }
   __syncthreads();
@@ -374,7 +414,7 @@ __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
 #pragma unroll
     for (int s = 0; s < kStages; ++s) {
       const uint32_t tile = blockIdx.x + s * gridDim.x;
-      if (tile < n_tiles) issue_tile<T, P, FWD, BWD>(a, g, tile, smem + s * g.stage_bytes, &bars[s]);
+      if (tile < n_tiles) issue_tile<T, P, FWD, BWD>(a, g, tile, smem + s * g.stage_bytes, &full[s]);
     }
   }
   const uint32_t local = threadIdx.x >> a.slice_log2;
@@ -382,13 +422,25 @@ __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
   for (uint32_t it = 0;; ++it) {
     const uint32_t tile = blockIdx.x + it * gridDim.x;
     if (tile >= n_tiles) break;  // block-uniform
+    // producer: refill the stage read in the previous iteration (one iteration
+    // of slack, so the wait for its last reader is normally already over)
+    if (threadIdx.x == 0 && it >= 1) {
+      const uint32_t pit = it - 1;
+      const uint32_t next = blockIdx.x + (pit + kStages) * gridDim.x;
+      const int ps = pit % kStages;
+      if (next < n_tiles && mbar_wait(&empty[ps], (pit / kStages) & 1u, a.dev_err)) {
+        fence_proxy_async();
+        issue_tile<T, P, FWD, BWD>(a, g, next, smem + ps * g.stage_bytes, &full[ps]);
+      }
+    }
     const int s = it % kStages;
-    unsigned char* st = smem + s * g.stage_bytes;
-    const bool arrived = mbar_wait(&bars[s], (it / kStages) & 1u, a.dev_err);
+    const unsigned char* st = smem + s * g.stage_bytes;
+    const bool arrived = __all_sync(0xffffffffu, mbar_wait(&full[s], (it / kStages) & 1u, a.dev_err));
+    if (!arrived) return;  // warp-uniform; the other warps give up on their own waits
     const uint32_t p0 = tile * g.tp;
     const uint32_t count = min(g.tp, n - p0);
     RawItem<T, P> r;
-    r.ok = arrived && local < count;
+    r.ok = local < count;
     const uint32_t i = p0 + local;
     if (r.ok) {
       const float* mu = reinterpret_cast<const float*>(st + g.off_mu);
@@ -399,7 +451,7 @@ __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) r.gc[c] = gc[3 * local + c];
       }
-      if (FWD && l0 == 0) {
+      if (FWD) {
         // plain shared-memory reads (load1 uses the global read-only path)
         const T* c0 = reinterpret_cast<const T*>(st + g.off_c0);
 #pragma unroll
@@ -411,16 +463,9 @@ __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
           r.w[p] = *reinterpret_cast<const W*>(st + p * g.plane_bytes + (local * L + l0) * sizeof(T));
       }
     }
-    // the stage is read: release it (and leave together if a wait timed out)
-    if (__syncthreads_or(!arrived)) return;
-    if (threadIdx.x == 0) {
-      const uint32_t next = tile + kStages * gridDim.x;
-      if (next < n_tiles) {
-        fence_proxy_async();
-        issue_tile<T, P, FWD, BWD>(a, g, next, st, &bars[s]);
-      }
-    }
-    eval_item<FRAME, T, uint32_t, MODE, true>(a, r, i, l0);
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
+    eval_item<FRAME, T, uint32_t, MODE, true, FLAGS>(a, r, i, l0);
   }
 }
 
@@ -474,12 +519,12 @@ bool tma_eligible(const EvalArgs& a, bool even) {
   return true;
 }
 
-template <int MODE, int FRAME, typename T>
+template <int MODE, int FRAME, typename T, int FLAGS>
 nasg_status launch_tma(const EvalArgs& a, cudaStream_t s) {
   constexpr int P = FrameTraits<FRAME>::P;
   const TileGeom g = tile_geom<T, P>(a.slice_log2, a.n_lobes);
-  const size_t smem = size_t(kStages) * g.stage_bytes + kStages * sizeof(uint64_t);
-  auto k = eval_tma_kernel<FRAME, T, MODE>;
+  const size_t smem = size_t(kStages) * g.stage_bytes + 2 * kStages * sizeof(uint64_t);
+  auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS>;
   static size_t configured = 0;  // per instantiation
   if (smem > configured) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
@@ -496,7 +541,10 @@ nasg_status launch_tma(const EvalArgs& a, cudaStream_t s) {
 
 template <int MODE, int FRAME, typename T>
 nasg_status launch_frame_dtype(const EvalArgs& a, bool even, cudaStream_t s) {
-  if (tma_eligible<FRAME, T>(a, even)) return launch_tma<MODE, FRAME, T>(a, s);
+  if (tma_eligible<FRAME, T>(a, even)) {
+    const bool dflt = a.identity == 0 && a.normalised != 0 && a.accumulate == 0;
+    return dflt ? launch_tma<MODE, FRAME, T, kFlagsDefault>(a, s) : launch_tma<MODE, FRAME, T, kFlagsRuntime>(a, s);
+  }
   // 32-bit element offsets when every offset the kernel forms (P*N*L elements,
   // 3*N, and the thread index including one stride of prefetch) stays below 2^31.
   const int64_t NL = a.n * a.n_lobes;
