@@ -82,10 +82,14 @@ def load_peaks():
 
 
 def kernel_source_hash():
+    """Hash of every source the headline kernel is compiled from (csrc/nasg_*.cuh, nasg_eval*.cu)."""
+    csrc = os.path.join(ROOT, "paper_2606_09794_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("nasg_eval.cu", "nasg_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2606_09794_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for f in sorted(os.listdir(csrc)):
+        if (f.startswith("nasg_") and f.endswith(".cuh")) or (f.startswith("nasg_eval") and f.endswith(".cu")) \
+                or f == "nasg_host.h":
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
@@ -411,7 +415,7 @@ def main():
                        "l2": "no flush: inputs 190 MB + outputs 356 MB per step exceed the 129 MB L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "eval_kernel<QUAT, bf16, V=4, fwd+bwd>",
+                         "kernel": "eval_tma_kernel<QUAT, bf16, fwd+bwd, default flags>",
                          "algorithmic_bytes_per_launch": alg_bytes},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
