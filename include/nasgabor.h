@@ -145,6 +145,65 @@ nasg_status nasgabor_fused_fwd_bwd(const nasg_desc* desc, const void* params, co
                                    float* rgb, float* g_params, float* g_c0, float* g_means,
                                    void* stream);
 
+/* Adam hyperparameters of one step (bias-corrected, torch.optim.Adam order). */
+typedef struct nasg_adam_hparams {
+  float lr;       /* learning rate (>= 0)                        */
+  float beta1;    /* [0, 1)                                      */
+  float beta2;    /* [0, 1)                                      */
+  float eps;      /* > 0                                         */
+  int32_t step;   /* t >= 1: the step being taken (bias corrections 1 - beta^t) */
+} nasg_adam_hparams;
+
+/* Optimiser state of one parameter set, all device pointers, updated in place. */
+typedef struct nasg_train_state {
+  float* master;        /* [P][N*L] f32 raw lobe parameters (FP32 master)          */
+  float* m;             /* [P][N*L] f32 first moments                              */
+  float* v;             /* [P][N*L] f32 second moments                             */
+  void* params_bf16;    /* [P][N*L] bf16 copy: RNE(master) of the updated entries; nullable */
+  float* c0_master;     /* [3][N] f32 diffuse colours                              */
+  float* c0_m;          /* [3][N] f32                                              */
+  float* c0_v;          /* [3][N] f32                                              */
+  void* c0_bf16;        /* [3][N] bf16 copy, nullable                              */
+} nasg_train_state;
+
+/*
+ * Fused training step for the listed primitives: forward (eq:app_model), the
+ * Supp. F backward for the given upstream gradient g_rgb [N][3] f32, and one
+ * Adam update of master, m, v (lobe parameters and c0) in one pass, the
+ * gradients never being written to memory. With desc->param_dtype = BF16 the
+ * model is evaluated at RNE_bf16(master) (the stored BF16 copy); with F32 at
+ * master. Primitives not listed are left untouched (their m, v do not advance).
+ *   idx/n_idx     device list of primitives (NULL: all N). Entries outside [0, N) are skipped.
+ *   n_idx_device  device int32, nullable: when given, the list length is
+ *                 min(n_idx, *n_idx_device) (so the count produced by
+ *                 nasg_frustum_compact can be used without a host round trip).
+ *   rgb, g_means  device [N][3] f32 outputs for the listed primitives, nullable.
+ * desc->accumulate must be 0. Errors as nasgabor_eval_bwd; NASG_ERR_RANGE for
+ * bad hyperparameters.
+ */
+nasg_status nasgabor_fused_step(const nasg_desc* desc, const nasg_train_state* state, const float* means,
+                                const float* cam, const int32_t* idx, int64_t n_idx,
+                                const int32_t* n_idx_device, const float* g_rgb,
+                                const nasg_adam_hparams* hparams, float* rgb, float* g_means, void* stream);
+
+/* Bytes of device workspace nasg_frustum_compact needs for n primitives. */
+size_t nasg_frustum_workspace_bytes(int64_t n);
+
+/*
+ * Ordered list of the primitives whose centre lies in a pinhole frustum (the
+ * primitives a frame sees, Sec. 4.2): with p = R (mu - center), visible iff
+ * p_z > near_z, |p_x| <= t p_z and |p_y| <= t p_z, t = tan_half_fov.
+ *   rot      HOST 9 f32, row-major world->camera rotation (rows right, up, forward)
+ *   center   HOST 3 f32
+ *   idx      device [n] int32 output, ascending primitive indices of the visible set
+ *   n_visible device int32 output (the list length)
+ *   workspace device scratch of nasg_frustum_workspace_bytes(n) bytes, 16-byte aligned
+ * Deterministic. n < 2^31. Three kernel launches on `stream`, no host synchronisation.
+ */
+nasg_status nasg_frustum_compact(int64_t n, const float* means, const float* rot, const float* center,
+                                 float tan_half_fov, float near_z, int32_t* idx, int32_t* n_visible,
+                                 void* workspace, size_t workspace_bytes, void* stream);
+
 /*
  * Real spherical harmonics of degree 0..3 (Sec. 3.2): orthonormal real basis
  * with the Condon-Shortley phase, coefficient j = l^2 + l + m (m = -l..l).

@@ -9,9 +9,10 @@ Modules:
   nasgabor  -- NASGabor lobe, appearance model forward/backward (Sec. 3.2, 4.1, Supp. C/E/F)
   sh        -- real spherical harmonics forward/backward (Sec. 3.2)
   adam      -- Adam update, fused BF16 step and the teacher/student fitting step
+  frustum   -- pinhole visibility of primitive centres
 
 Parity pins: every function here is checked in ``tests/test_oracle_*.py``
 against closed forms, special cases that reduce to textbook or library
 routines, invariances and central finite differences.
 """
-from . import adam, nasgabor, sh  # noqa: F401
+from . import adam, frustum, nasgabor, sh  # noqa: F401

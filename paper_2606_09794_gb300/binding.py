@@ -38,6 +38,16 @@ class NasgDesc(ctypes.Structure):
                 ("norm_mode", _i32), ("act_mode", _i32), ("accumulate", _i32)]
 
 
+class NasgAdam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("step", _i32)]
+
+
+class NasgTrainState(ctypes.Structure):
+    _fields_ = [("master", _vp), ("m", _vp), ("v", _vp), ("params_bf16", _vp),
+                ("c0_master", _vp), ("c0_m", _vp), ("c0_v", _vp), ("c0_bf16", _vp)]
+
+
 def _decl(name, argtypes, restype=_i32):
     fn = getattr(lib, name)
     fn.argtypes = argtypes
@@ -58,6 +68,11 @@ _decl("nasgabor_fused_fwd_bwd", [_P(NasgDesc), _vp, _vp, _vp, _P(ctypes.c_float)
 _decl("sh_eval_fwd", [_i32, _i64, _vp, _vp, _P(ctypes.c_float), _vp, _vp])
 _decl("sh_eval_bwd", [_i32, _i64, _vp, _vp, _P(ctypes.c_float), _vp, _vp, _vp, _vp])
 _decl("nasg_math_probe", [_i32, _vp, _vp, _vp, _i64, _vp])
+_decl("nasgabor_fused_step", [_P(NasgDesc), _P(NasgTrainState), _vp, _P(ctypes.c_float), _vp, _i64, _vp, _vp,
+                              _P(NasgAdam), _vp, _vp, _vp])
+_decl("nasg_frustum_workspace_bytes", [_i64], ctypes.c_size_t)
+_decl("nasg_frustum_compact", [_i64, _vp, _P(ctypes.c_float), _P(ctypes.c_float), ctypes.c_float, ctypes.c_float,
+                               _vp, _vp, _vp, ctypes.c_size_t, _vp])
 
 
 class NasgError(RuntimeError):
@@ -236,6 +251,74 @@ def nasg_math_probe(fn, x, stream=None):
     y2 = torch.empty_like(x) if fn > 0 else None
     _check(lib.nasg_math_probe(fn, _ptr(x), _ptr(y), _ptr(y2), x.numel(), _stream(stream)), "nasg_math_probe")
     return y, y2
+
+
+class TrainState:
+    """FP32 master, Adam moments and BF16 copies of one parameter set (device tensors)."""
+
+    def __init__(self, master, c0_master, m=None, v=None, c0_m=None, c0_v=None, bf16_copies=True):
+        self.master = _cuda(master, "master", torch.float32)
+        self.c0_master = _cuda(c0_master, "c0_master", torch.float32)
+        self.m = torch.zeros_like(master) if m is None else _cuda(m, "m", torch.float32)
+        self.v = torch.zeros_like(master) if v is None else _cuda(v, "v", torch.float32)
+        self.c0_m = torch.zeros_like(c0_master) if c0_m is None else _cuda(c0_m, "c0_m", torch.float32)
+        self.c0_v = torch.zeros_like(c0_master) if c0_v is None else _cuda(c0_v, "c0_v", torch.float32)
+        self.params_bf16 = master.to(torch.bfloat16) if bf16_copies else None
+        self.c0_bf16 = c0_master.to(torch.bfloat16) if bf16_copies else None
+
+    def as_c(self):
+        return NasgTrainState(_ptr(self.master), _ptr(self.m), _ptr(self.v), _ptr(self.params_bf16),
+                              _ptr(self.c0_master), _ptr(self.c0_m), _ptr(self.c0_v), _ptr(self.c0_bf16))
+
+
+def nasgabor_fused_step(state, means, cam, g_rgb, n_lobes, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                        idx=None, n_idx_device=None, frame_mode="quat", norm_mode="approx", act_mode="raw",
+                        evaluate_bf16=True, rgb=None, g_means=None, stream=None):
+    """Forward + backward + Adam for the listed primitives; state (TrainState) updated in place."""
+    _cuda(means, "means", torch.float32)
+    _cuda(g_rgb, "g_rgb", torch.float32)
+    n = means.shape[0]
+    if idx is not None:
+        _cuda(idx, "idx", torch.int32)
+    if n_idx_device is not None:
+        _cuda(n_idx_device, "n_idx_device", torch.int32)
+    for t, nm in ((rgb, "rgb"), (g_means, "g_means")):
+        if t is not None:
+            _cuda(t, nm, torch.float32)
+    desc = make_desc(n, n_lobes, frame_mode, torch.bfloat16 if evaluate_bf16 else torch.float32,
+                     norm_mode, act_mode)
+    hp = NasgAdam(lr, beta1, beta2, eps, int(step))
+    st = state.as_c()
+    _check(lib.nasgabor_fused_step(ctypes.byref(desc), ctypes.byref(st), _ptr(means), _cam(cam), _ptr(idx),
+                                   0 if idx is None else idx.numel(), _ptr(n_idx_device), _ptr(g_rgb),
+                                   ctypes.byref(hp), _ptr(rgb), _ptr(g_means), _stream(stream)),
+           "nasgabor_fused_step")
+    return rgb
+
+
+def nasg_frustum_workspace_bytes(n):
+    return int(lib.nasg_frustum_workspace_bytes(int(n)))
+
+
+def nasg_frustum_compact(means, rot, center, tan_half_fov, near=0.0, idx=None, n_visible=None, workspace=None,
+                         stream=None):
+    """Ordered indices of the primitives inside the frustum; returns (idx [N] int32, n_visible [1] int32)."""
+    _cuda(means, "means", torch.float32)
+    n = means.shape[0]
+    dev = means.device
+    if idx is None:
+        idx = torch.empty(max(n, 1), device=dev, dtype=torch.int32)
+    if n_visible is None:
+        n_visible = torch.empty(1, device=dev, dtype=torch.int32)
+    wsb = nasg_frustum_workspace_bytes(n)
+    if workspace is None:
+        workspace = torch.empty(max(wsb, 16), device=dev, dtype=torch.uint8)
+    r = (ctypes.c_float * 9)(*[float(x) for x in torch.as_tensor(rot, dtype=torch.float32).reshape(-1).tolist()])
+    c = _cam(center)
+    _check(lib.nasg_frustum_compact(n, _ptr(means), r, c, float(tan_half_fov), float(near), _ptr(idx),
+                                    _ptr(n_visible), _ptr(workspace), workspace.numel(), _stream(stream)),
+           "nasg_frustum_compact")
+    return idx, n_visible
 
 
 # ---------------------------------------------------------------------------

@@ -135,11 +135,12 @@ struct RawItem {
 };
 
 // Element offsets use IDX (uint32_t when P*N*L < 2^31, else uint64_t).
+// `total` is the number of lane items (items << slice_log2).
 template <typename T, int P, typename IDX, bool EVEN, bool FWD, bool BWD>
-__device__ __forceinline__ void fetch_item(const EvalArgs& a, IDX t, int l0, RawItem<T, P>& r, IDX& prim) {
+__device__ __forceinline__ void fetch_item(const EvalArgs& a, IDX total, IDX t, int l0, RawItem<T, P>& r,
+                                           IDX& prim) {
   const T* __restrict__ params = static_cast<const T*>(a.params);
   const IDX n = IDX(a.n);
-  const IDX total = IDX(a.n_items) << a.slice_log2;
   r.ok = 0;
   if (t >= total) return;
   const IDX item = t >> a.slice_log2;
@@ -318,14 +319,14 @@ __global__ void __launch_bounds__(256, 2) eval_kernel(const EvalArgs a) {
   RawItem<T, P> b0, b1;
   IDX i0 = 0, i1 = 0;
   IDX t0 = IDX(blockIdx.x) * blockDim.x;
-  fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, t0 + threadIdx.x, l0, b0, i0);
+  fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, total, t0 + threadIdx.x, l0, b0, i0);
   // block-uniform loop: every lane of a warp reaches the shuffles
   while (t0 < total) {
-    fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, t0 + stride + threadIdx.x, l0, b1, i1);
+    fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, total, t0 + stride + threadIdx.x, l0, b1, i1);
     eval_item<FRAME, T, IDX, MODE, EVEN, FLAGS>(a, b0, i0, l0);
     t0 += stride;
     if (t0 >= total) break;
-    fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, t0 + stride + threadIdx.x, l0, b0, i0);
+    fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, total, t0 + stride + threadIdx.x, l0, b0, i0);
     eval_item<FRAME, T, IDX, MODE, EVEN, FLAGS>(a, b1, i1, l0);
     t0 += stride;
   }

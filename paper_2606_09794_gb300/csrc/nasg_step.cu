@@ -1,0 +1,397 @@
+// Fused forward + backward + Adam training step of the NASGabor appearance
+// model (nasgabor_fused_step) and the frustum visibility compaction that
+// produces its index list (nasg_frustum_compact).
+//
+// Step: for every listed primitive, the lobes are evaluated at the stored
+// parameter values (RNE bfloat16 of the FP32 master when desc->param_dtype is
+// BF16), the Supp. F gradients for the given upstream dLoss/dRGB are formed in
+// registers (never written to memory), and Adam (bias-corrected, in
+// torch.optim.Adam's operation order) updates master, m and v in place and
+// writes the BF16 copy. Primitives not listed are not touched. Mapping and
+// numerics are those of the evaluation kernels (nasg_kernels.cuh): a lane holds
+// two lobes in packed FP32x2 arithmetic and a slice of lanes covers a primitive.
+//
+// Compaction: an ordered (deterministic, ascending) list of the primitives
+// whose centre is inside a pinhole frustum, in three launches: per-chunk
+// counts (and a visibility byte per primitive), one-block exclusive scan of the
+// counts (also the total), and the ordered scatter.
+#include <cmath>
+
+#include "nasg_kernels.cuh"
+
+namespace nasg {
+
+struct StepArgs {
+  EvalArgs e;            // params = master, c0 = c0 master, g_rgb, rgb (nullable), g_means (nullable)
+  float* m;              // [P][N*L]
+  float* v;              // [P][N*L]
+  uint16_t* pbf;         // [P][N*L] bf16 copy, nullable
+  float* c0m;            // [3][N]
+  float* c0v;            // [3][N]
+  uint16_t* c0bf;        // [3][N] bf16 copy, nullable
+  const int32_t* n_dev;  // device item count (min with e.n_items), nullable
+  float b1, b2, omb1, omb2, step_size, inv_sqrt_bc2, eps;
+  int32_t quantize;      // evaluate at RNE_bf16(master)
+};
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float bf16_rne(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+
+// One bias-corrected Adam update: m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
+// th <- th - (lr/bc1) m / (sqrt(v)/sqrt(bc2) + eps).
+__device__ __forceinline__ void adam(const StepArgs& s, float g, float& th, float& m, float& v) {
+  m = fmaf(s.b1, m, s.omb1 * g);
+  v = fmaf(s.b2, v, s.omb2 * (g * g));
+  const float den = fmaf(sqrt_approx(v), s.inv_sqrt_bc2, s.eps);
+  th = fmaf(-s.step_size, m * rcpa(den), th);
+}
+
+template <int FRAME, typename IDX, bool EVEN>
+__device__ __forceinline__ void step_item(const StepArgs& s, const RawItem<float, FrameTraits<FRAME>::P>& cur, IDX i,
+                                          int l0) {
+  constexpr int P = FrameTraits<FRAME>::P;
+  const EvalArgs& a = s.e;
+  const IDX n = IDX(a.n);
+  const IDX L = IDX(a.n_lobes);
+  const bool ok = cur.ok != 0;
+  const bool quant = s.quantize != 0;
+  float rgb[3] = {0.f, 0.f, 0.f};
+  float gd[3] = {0.f, 0.f, 0.f};
+  float d[3] = {0.f, 0.f, 1.f};
+  float inv_dist = 0.f;
+  if (ok) {
+    const float rx = cur.mu[0] - a.cam[0], ry = cur.mu[1] - a.cam[1], rz = cur.mu[2] - a.cam[2];
+    inv_dist = rsqrtf(rx * rx + ry * ry + rz * rz);
+    d[0] = rx * inv_dist; d[1] = ry * inv_dist; d[2] = rz * inv_dist;
+    if (IDX(l0) < L) {
+      const bool second = EVEN || (IDX(l0) + 1 < L);
+      P2 pv[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const float2 w = cur.w[p];
+        pv[p] = quant ? p2(bf16_rne(w.x), bf16_rne(w.y)) : p2(w.x, w.y);
+      }
+      const P2 dv[3] = {p2(d[0]), p2(d[1]), p2(d[2])};
+      const P2 gcv[3] = {p2(cur.gc[0]), p2(cur.gc[1]), p2(cur.gc[2])};
+      P2 rgbv[3] = {p2(0.f), p2(0.f), p2(0.f)};
+      P2 gdv[3] = {p2(0.f), p2(0.f), p2(0.f)};
+      P2 gp[P];
+      lobe_step<FRAME, true, true>(pv, dv, gcv, a.identity != 0, a.normalised != 0, rgbv, gdv, gp);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        rgb[c] = rgbv[c].v.x + (second ? rgbv[c].v.y : 0.f);
+        gd[c] = gdv[c].v.x + (second ? gdv[c].v.y : 0.f);
+      }
+      const IDX NL = n * L;
+      IDX off = i * L + IDX(l0);
+#pragma unroll
+      for (int p = 0; p < P; ++p, off += NL) {
+        float2 th = cur.w[p];
+        float2 mm, vv;
+        if (EVEN) {
+          mm = *reinterpret_cast<const float2*>(s.m + off);
+          vv = *reinterpret_cast<const float2*>(s.v + off);
+        } else {
+          mm = make_float2(s.m[off], second ? s.m[off + 1] : 0.f);
+          vv = make_float2(s.v[off], second ? s.v[off + 1] : 0.f);
+        }
+        adam(s, gp[p].v.x, th.x, mm.x, vv.x);
+        adam(s, gp[p].v.y, th.y, mm.y, vv.y);
+        float* master = static_cast<float*>(const_cast<void*>(a.params));
+        if (EVEN) {
+          *reinterpret_cast<float2*>(master + off) = th;
+          *reinterpret_cast<float2*>(s.m + off) = mm;
+          *reinterpret_cast<float2*>(s.v + off) = vv;
+          if (s.pbf) {
+            const uint32_t w2 = uint32_t(bf16_bits(th.x)) | (uint32_t(bf16_bits(th.y)) << 16);
+            *reinterpret_cast<uint32_t*>(s.pbf + off) = w2;
+          }
+        } else {
+          master[off] = th.x; s.m[off] = mm.x; s.v[off] = vv.x;
+          if (s.pbf) s.pbf[off] = bf16_bits(th.x);
+          if (second) {
+            master[off + 1] = th.y; s.m[off + 1] = mm.y; s.v[off + 1] = vv.y;
+            if (s.pbf) s.pbf[off + 1] = bf16_bits(th.y);
+          }
+        }
+      }
+    }
+  }
+  for (int o = a.slice >> 1; o >= 1; o >>= 1) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      rgb[c] += __shfl_xor_sync(0xffffffffu, rgb[c], o);
+      gd[c] += __shfl_xor_sync(0xffffffffu, gd[c], o);
+    }
+  }
+  if (ok) {
+    const float dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+    for (int c = l0 >> 1; c < 3; c += a.slice) {
+      float th = pick3(cur.c0, c);
+      if (a.rgb) a.rgb[3 * i + c] = pick3(rgb, c) + (quant ? bf16_rne(th) : th);
+      if (a.g_means) a.g_means[3 * i + c] = (pick3(gd, c) - dot * pick3(d, c)) * inv_dist;
+      const IDX o = IDX(c) * n + i;
+      float mm = s.c0m[o], vv = s.c0v[o];
+      adam(s, pick3(cur.gc, c), th, mm, vv);
+      float* c0master = static_cast<float*>(const_cast<void*>(a.c0));
+      c0master[o] = th;
+      s.c0m[o] = mm;
+      s.c0v[o] = vv;
+      if (s.c0bf) s.c0bf[o] = bf16_bits(th);
+    }
+  }
+}
+
+template <int FRAME, typename IDX, bool EVEN>
+__global__ void __launch_bounds__(256, 2) step_kernel(const StepArgs s) {
+  constexpr int P = FrameTraits<FRAME>::P;
+  const EvalArgs& a = s.e;
+  int64_t items = a.n_items;
+  if (s.n_dev) {
+    const int64_t dn = int64_t(__ldg(s.n_dev));
+    items = dn < 0 ? 0 : (dn < items ? dn : items);
+  }
+  const int l0 = 2 * (threadIdx.x & (a.slice - 1));
+  const IDX total = IDX(items) << a.slice_log2;
+  const IDX stride = IDX(gridDim.x) * blockDim.x;
+  // block-uniform loop: every lane of a warp reaches the shuffles in step_item.
+  // No register prefetch here: the step moves ~2 KB per primitive, and the
+  // moment loads of phase two already keep enough bytes in flight.
+  for (IDX t0 = IDX(blockIdx.x) * blockDim.x; t0 < total; t0 += stride) {
+    RawItem<float, P> cur;
+    IDX i = 0;
+    fetch_item<float, P, IDX, EVEN, true, true>(a, total, t0 + threadIdx.x, l0, cur, i);
+    step_item<FRAME, IDX, EVEN>(s, cur, i, l0);
+  }
+}
+
+template <int FRAME, typename IDX>
+static nasg_status launch_step_idx(const StepArgs& s, bool even, cudaStream_t st) {
+  const int64_t threads = s.e.n_items << s.e.slice_log2;
+  if (even) {
+    auto k = step_kernel<FRAME, IDX, true>;
+    k<<<persistent_grid(k, threads, 256), 256, 0, st>>>(s);
+  } else {
+    auto k = step_kernel<FRAME, IDX, false>;
+    k<<<persistent_grid(k, threads, 256), 256, 0, st>>>(s);
+  }
+  return check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Frustum compaction
+// ---------------------------------------------------------------------------
+
+constexpr int kCompactBlock = 256;
+constexpr int kCompactChunk = 4096;  // primitives per block (16 rounds of 256)
+
+struct FrustumArgs {
+  const float* means;
+  int64_t n;
+  float r[9];  // world -> camera rows: right, up, forward
+  float c[3];  // camera centre
+  float t;     // tan(fov/2)
+  float near_z;
+};
+
+// Visibility of one centre with explicitly rounded operations, so that every
+// launch makes the identical decision.
+__device__ __forceinline__ bool in_frustum(const FrustumArgs& f, int64_t i) {
+  const float x = __fsub_rn(f.means[3 * i + 0], f.c[0]);
+  const float y = __fsub_rn(f.means[3 * i + 1], f.c[1]);
+  const float z = __fsub_rn(f.means[3 * i + 2], f.c[2]);
+  const float px = __fmaf_rn(f.r[0], x, __fmaf_rn(f.r[1], y, __fmul_rn(f.r[2], z)));
+  const float py = __fmaf_rn(f.r[3], x, __fmaf_rn(f.r[4], y, __fmul_rn(f.r[5], z)));
+  const float pz = __fmaf_rn(f.r[6], x, __fmaf_rn(f.r[7], y, __fmul_rn(f.r[8], z)));
+  const float lim = __fmul_rn(f.t, pz);
+  return pz > f.near_z && fabsf(px) <= lim && fabsf(py) <= lim;
+}
+
+__global__ void __launch_bounds__(kCompactBlock) frustum_count_kernel(FrustumArgs f, uint8_t* flags,
+                                                                      int32_t* counts) {
+  const int64_t base = int64_t(blockIdx.x) * kCompactChunk;
+  int local = 0;
+  for (int r = 0; r < kCompactChunk / kCompactBlock; ++r) {
+    const int64_t i = base + r * kCompactBlock + threadIdx.x;
+    const bool v = i < f.n && in_frustum(f, i);
+    if (i < f.n) flags[i] = v ? 1 : 0;
+    local += __syncthreads_count(v);
+  }
+  if (threadIdx.x == 0) counts[blockIdx.x] = local;
+}
+
+// One block: exclusive prefix over counts[0..nb) -> offsets, total -> *n_visible.
+__global__ void __launch_bounds__(1024) frustum_scan_kernel(const int32_t* counts, int32_t* offsets, int32_t nb,
+                                                            int32_t* n_visible) {
+  __shared__ int32_t part[1024];
+  const int per = (nb + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per;
+  int32_t sum = 0;
+  for (int j = 0; j < per; ++j)
+    if (b0 + j < nb) sum += counts[b0 + j];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  // Hillis-Steele inclusive scan of the per-thread sums
+  for (int o = 1; o < int(blockDim.x); o <<= 1) {
+    const int32_t add = threadIdx.x >= unsigned(o) ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  int32_t run = part[threadIdx.x] - sum;  // exclusive
+  for (int j = 0; j < per; ++j) {
+    if (b0 + j < nb) {
+      offsets[b0 + j] = run;
+      run += counts[b0 + j];
+    }
+  }
+  if (threadIdx.x == blockDim.x - 1) *n_visible = part[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kCompactBlock) frustum_scatter_kernel(int64_t n, const uint8_t* flags,
+                                                                        const int32_t* offsets, int32_t* idx) {
+  __shared__ int32_t warp_tot[kCompactBlock / 32];
+  const int64_t base = int64_t(blockIdx.x) * kCompactChunk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t run = offsets[blockIdx.x];
+  for (int r = 0; r < kCompactChunk / kCompactBlock; ++r) {
+    const int64_t i = base + r * kCompactBlock + threadIdx.x;
+    const bool v = i < n && flags[i] != 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, v);
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    int32_t before = 0, round = 0;
+#pragma unroll
+    for (int w = 0; w < kCompactBlock / 32; ++w) {
+      const int32_t t = warp_tot[w];
+      before += w < warp ? t : 0;
+      round += t;
+    }
+    if (v) idx[run + before + __popc(bal & ((1u << lane) - 1u))] = int32_t(i);
+    run += round;
+    __syncthreads();
+  }
+}
+
+static int64_t compact_blocks(int64_t n) { return (n + kCompactChunk - 1) / kCompactChunk; }
+
+}  // namespace nasg
+
+using namespace nasg;
+
+extern "C" size_t nasg_frustum_workspace_bytes(int64_t n) {
+  if (n < 0) return 0;
+  const int64_t nb = compact_blocks(n);
+  return size_t((n + 15) / 16 * 16) + size_t(2 * nb) * sizeof(int32_t);
+}
+
+extern "C" nasg_status nasg_frustum_compact(int64_t n, const float* means, const float* rot, const float* center,
+                                            float tan_half_fov, float near_z, int32_t* idx, int32_t* n_visible,
+                                            void* workspace, size_t workspace_bytes, void* stream) {
+  if (n < 0 || n >= (int64_t(1) << 31)) return NASG_ERR_RANGE;
+  if (!rot || !center || !n_visible) return NASG_ERR_NULL;
+  if (!(tan_half_fov > 0.f)) return NASG_ERR_RANGE;
+  cudaStream_t s = as_stream(stream);
+  if (n == 0) {
+    if (cudaMemsetAsync(n_visible, 0, sizeof(int32_t), s) != cudaSuccess) return check_launch();
+    return NASG_OK;
+  }
+  if (!means || !idx || !workspace) return NASG_ERR_NULL;
+  if (!aligned(means, 4) || !aligned(idx, 4) || !aligned(n_visible, 4) || !aligned(workspace, 16))
+    return NASG_ERR_ALIGN;
+  if (workspace_bytes < nasg_frustum_workspace_bytes(n)) return NASG_ERR_RANGE;
+  const int64_t nb = compact_blocks(n);
+  uint8_t* flags = static_cast<uint8_t*>(workspace);
+  int32_t* counts = reinterpret_cast<int32_t*>(flags + (n + 15) / 16 * 16);
+  int32_t* offsets = counts + nb;
+  FrustumArgs f{};
+  f.means = means;
+  f.n = n;
+  for (int j = 0; j < 9; ++j) f.r[j] = rot[j];
+  for (int j = 0; j < 3; ++j) f.c[j] = center[j];
+  f.t = tan_half_fov;
+  f.near_z = near_z;
+  frustum_count_kernel<<<unsigned(nb), kCompactBlock, 0, s>>>(f, flags, counts);
+  frustum_scan_kernel<<<1, 1024, 0, s>>>(counts, offsets, int32_t(nb), n_visible);
+  frustum_scatter_kernel<<<unsigned(nb), kCompactBlock, 0, s>>>(n, flags, offsets, idx);
+  return check_launch();
+}
+
+extern "C" nasg_status nasgabor_fused_step(const nasg_desc* desc, const nasg_train_state* st, const float* means,
+                                           const float* cam, const int32_t* idx, int64_t n_idx,
+                                           const int32_t* n_idx_device, const float* g_rgb,
+                                           const nasg_adam_hparams* hp, float* rgb, float* g_means, void* stream) {
+  nasg_status e = check_desc(desc);
+  if (e != NASG_OK) return e;
+  if (desc->accumulate != 0) return NASG_ERR_RANGE;
+  if (!st || !hp || !cam) return NASG_ERR_NULL;
+  if (idx && n_idx < 0) return NASG_ERR_RANGE;
+  if (hp->step < 1 || !(hp->lr >= 0.f) || !(hp->beta1 >= 0.f && hp->beta1 < 1.f) ||
+      !(hp->beta2 >= 0.f && hp->beta2 < 1.f) || !(hp->eps > 0.f))
+    return NASG_ERR_RANGE;
+  if (desc->n == 0 || (idx && n_idx == 0)) return NASG_OK;
+  if (!st->master || !st->m || !st->v || !st->c0_master || !st->c0_m || !st->c0_v || !means || !g_rgb)
+    return NASG_ERR_NULL;
+  const void* f32[] = {st->master, st->m, st->v, st->c0_master, st->c0_m, st->c0_v, means, g_rgb, rgb, g_means};
+  for (const void* p : f32)
+    if (p && !aligned(p, 4)) return NASG_ERR_ALIGN;
+  if ((st->params_bf16 && !aligned(st->params_bf16, 2)) || (st->c0_bf16 && !aligned(st->c0_bf16, 2)) ||
+      (idx && !aligned(idx, 4)) || (n_idx_device && !aligned(n_idx_device, 4)))
+    return NASG_ERR_ALIGN;
+  StepArgs s{};
+  EvalArgs& a = s.e;
+  a.params = st->master;
+  a.c0 = st->c0_master;
+  a.means = means;
+  a.cam[0] = cam[0];
+  a.cam[1] = cam[1];
+  a.cam[2] = cam[2];
+  a.idx = idx;
+  a.n_items = idx ? n_idx : desc->n;
+  a.n = desc->n;
+  a.n_lobes = desc->n_lobes;
+  a.slice_log2 = slice_log2(desc->n_lobes);
+  a.slice = 1 << a.slice_log2;
+  a.identity = desc->act_mode == NASG_ACT_IDENTITY;
+  a.normalised = desc->norm_mode == NASG_NORM_APPROX;
+  a.g_rgb = g_rgb;
+  a.rgb = rgb;
+  a.g_means = g_means;
+  a.dev_err = device_error_word();
+  s.m = st->m;
+  s.v = st->v;
+  s.pbf = static_cast<uint16_t*>(st->params_bf16);
+  s.c0m = st->c0_m;
+  s.c0v = st->c0_v;
+  s.c0bf = static_cast<uint16_t*>(st->c0_bf16);
+  s.n_dev = n_idx_device;
+  const double b1 = hp->beta1, b2 = hp->beta2;
+  const double bc1 = 1.0 - std::pow(b1, double(hp->step));
+  const double bc2 = 1.0 - std::pow(b2, double(hp->step));
+  s.b1 = float(b1);
+  s.b2 = float(b2);
+  s.omb1 = float(1.0 - b1);
+  s.omb2 = float(1.0 - b2);
+  s.step_size = float(double(hp->lr) / bc1);
+  s.inv_sqrt_bc2 = float(1.0 / std::sqrt(bc2));
+  s.eps = hp->eps;
+  s.quantize = desc->param_dtype == NASG_DTYPE_BF16;
+  const bool even = desc->n_lobes % 2 == 0 && aligned(st->master, 8) && aligned(st->m, 8) && aligned(st->v, 8) &&
+                    (!st->params_bf16 || aligned(st->params_bf16, 4));
+  const int64_t NL = desc->n * desc->n_lobes;
+  const int64_t lim = int64_t(1) << 31;
+  const bool idx32 = NL * nasg_lobe_planes(desc->frame_mode) < lim && 3 * desc->n < lim &&
+                     2 * (a.n_items << a.slice_log2) + (int64_t(1) << 24) < lim;
+  cudaStream_t cs = as_stream(stream);
+  if (desc->frame_mode == NASG_FRAME_QUAT) {
+    return idx32 ? launch_step_idx<NASG_FRAME_QUAT, uint32_t>(s, even, cs)
+                 : launch_step_idx<NASG_FRAME_QUAT, uint64_t>(s, even, cs);
+  }
+  return idx32 ? launch_step_idx<NASG_FRAME_COS, uint32_t>(s, even, cs)
+               : launch_step_idx<NASG_FRAME_COS, uint64_t>(s, even, cs);
+}
