@@ -54,6 +54,7 @@ typedef int32_t nasg_status;
 #define NASG_ERR_UNSUPPORTED -4  /* valid but not built (e.g. an unsupported mode mix) */
 #define NASG_ERR_CUDA        -5  /* a CUDA runtime call or launch failed               */
 #define NASG_ERR_DEVICE      -6  /* a kernel reported a device-side error (see nasg_device_status) */
+#define NASG_ERR_CAPACITY    -7  /* larger than a fixed-capacity entry point can take   */
 
 #define NASG_FRAME_QUAT 0   /* frame from a quaternion (4 raw scalars)              */
 #define NASG_FRAME_COS  1   /* frame from three cosines (Supp. C parameterisation)  */
@@ -203,6 +204,33 @@ size_t nasg_frustum_workspace_bytes(int64_t n);
 nasg_status nasg_frustum_compact(int64_t n, const float* means, const float* rot, const float* center,
                                  float tan_half_fov, float near_z, int32_t* idx, int32_t* n_visible,
                                  void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * nasg_frustum_compact without a workspace argument, for callers that cannot
+ * allocate device memory where they need the list: a renderer plugged into a
+ * host application that owns every device allocation through its own pool, or
+ * a per-frame loop with a fixed memory budget in which a cudaMalloc would
+ * synchronise the device. The paper has no counterpart; this is a library
+ * convenience.
+ *
+ * Same arguments, results and determinism as nasg_frustum_compact, except:
+ *   - the scratch lives in a fixed array of this library's device memory sized
+ *     for NASG_NOALLOC_MAX_PRIMS primitives (about 8 MiB), which every GPU that
+ *     loads the library holds until the process exits; larger n is rejected
+ *     with NASG_ERR_CAPACITY before anything is launched;
+ *   - the first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any
+ *     stream capture;
+ *   - every call shares the one array: calls that may overlap on the GPU (on
+ *     different streams without ordering between them) race and corrupt each
+ *     other's lists. Calls ordered on one stream are safe; the array keeps the
+ *     last call's contents, and each call writes every scratch byte it reads.
+ * No entry point here allocates device memory.
+ */
+#define NASG_NOALLOC_MAX_PRIMS (1 << 23)
+nasg_status nasg_frustum_compact_noalloc(int64_t n, const float* means, const float* rot, const float* center,
+                                         float tan_half_fov, float near_z, int32_t* idx, int32_t* n_visible,
+                                         void* stream);
 
 /*
  * Real spherical harmonics of degree 0..3 (Sec. 3.2): orthonormal real basis

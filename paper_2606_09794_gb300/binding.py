@@ -71,6 +71,8 @@ _decl("nasg_math_probe", [_i32, _vp, _vp, _vp, _i64, _vp])
 _decl("nasgabor_fused_step", [_P(NasgDesc), _P(NasgTrainState), _vp, _P(ctypes.c_float), _vp, _i64, _vp, _vp,
                               _P(NasgAdam), _vp, _vp, _vp])
 _decl("nasg_frustum_workspace_bytes", [_i64], ctypes.c_size_t)
+_decl("nasg_frustum_compact_noalloc", [_i64, _vp, _P(ctypes.c_float), _P(ctypes.c_float), ctypes.c_float,
+                                       ctypes.c_float, _vp, _vp, _vp])
 _decl("nasg_frustum_compact", [_i64, _vp, _P(ctypes.c_float), _P(ctypes.c_float), ctypes.c_float, ctypes.c_float,
                                _vp, _vp, _vp, ctypes.c_size_t, _vp])
 
@@ -318,6 +320,28 @@ def nasg_frustum_compact(means, rot, center, tan_half_fov, near=0.0, idx=None, n
     _check(lib.nasg_frustum_compact(n, _ptr(means), r, c, float(tan_half_fov), float(near), _ptr(idx),
                                     _ptr(n_visible), _ptr(workspace), workspace.numel(), _stream(stream)),
            "nasg_frustum_compact")
+    return idx, n_visible
+
+
+NOALLOC_MAX_PRIMS = 1 << 23
+
+
+def nasg_frustum_compact_noalloc(means, rot, center, tan_half_fov, near=0.0, idx=None, n_visible=None,
+                                 stream=None):
+    """nasg_frustum_compact with the library's fixed scratch (no workspace): for callers that
+    cannot allocate device memory where they need the list. At most NOALLOC_MAX_PRIMS
+    primitives; calls that may overlap on the GPU race on the shared scratch."""
+    _cuda(means, "means", torch.float32)
+    n = means.shape[0]
+    dev = means.device
+    if idx is None:
+        idx = torch.empty(max(n, 1), device=dev, dtype=torch.int32)
+    if n_visible is None:
+        n_visible = torch.empty(1, device=dev, dtype=torch.int32)
+    r = (ctypes.c_float * 9)(*[float(x) for x in torch.as_tensor(rot, dtype=torch.float32).reshape(-1).tolist()])
+    _check(lib.nasg_frustum_compact_noalloc(n, _ptr(means), r, _cam(center), float(tan_half_fov), float(near),
+                                            _ptr(idx), _ptr(n_visible), _stream(stream)),
+           "nasg_frustum_compact_noalloc")
     return idx, n_visible
 
 

@@ -55,6 +55,7 @@ extern "C" const char* nasg_status_string(nasg_status status) {
     case NASG_ERR_UNSUPPORTED: return "unsupported combination of modes";
     case NASG_ERR_CUDA: return "a CUDA call or kernel launch failed";
     case NASG_ERR_DEVICE: return "a kernel reported a device-side error (bounded wait gave up)";
+    case NASG_ERR_CAPACITY: return "problem larger than the fixed scratch capacity of this entry point";
     default: return "unknown status";
   }
 }

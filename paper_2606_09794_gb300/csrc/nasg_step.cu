@@ -16,6 +16,7 @@
 // counts (and a visibility byte per primitive), one-block exclusive scan of the
 // counts (also the total), and the ordered scatter.
 #include <cmath>
+#include <mutex>
 
 #include "nasg_kernels.cuh"
 
@@ -394,4 +395,83 @@ extern "C" nasg_status nasgabor_fused_step(const nasg_desc* desc, const nasg_tra
   }
   return idx32 ? launch_step_idx<NASG_FRAME_COS, uint32_t>(s, even, cs)
                : launch_step_idx<NASG_FRAME_COS, uint64_t>(s, even, cs);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the frustum compaction
+// ---------------------------------------------------------------------------
+// Some callers cannot allocate device memory where they need the visible list:
+// a renderer plugged into a host application that owns every device allocation
+// through its own pool and forbids others, or a per-frame loop with a fixed
+// memory budget where a cudaMalloc would synchronise the device and stall the
+// frame. For them, nasg_frustum_compact_noalloc keeps its scratch (one
+// visibility byte per primitive, per-chunk counts and offsets) in a fixed
+// array of this library's device memory instead of a caller-provided
+// workspace. The array is sized for NASG_NOALLOC_MAX_PRIMS primitives and is
+// held by every GPU that loads the library until the process exits.
+namespace nasg {
+
+constexpr int64_t kNoAllocMaxPrims = NASG_NOALLOC_MAX_PRIMS;
+constexpr int64_t kNoAllocMaxChunks = (kNoAllocMaxPrims + kCompactChunk - 1) / kCompactChunk;
+constexpr size_t kNoAllocScratchBytes =
+    size_t((kNoAllocMaxPrims + 15) / 16 * 16) + size_t(2 * kNoAllocMaxChunks) * sizeof(int32_t);
+
+static __device__ __align__(256) unsigned char g_compact_scratch[kNoAllocScratchBytes];
+
+// Device address of g_compact_scratch on the current device. In host code the
+// array's name only stands for the symbol, so the address is looked up once per
+// device (with that device current) and cached.
+static unsigned char* noalloc_scratch() {
+  static std::mutex mu;
+  static unsigned char* cached[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cached[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_compact_scratch);
+    if (e != cudaSuccess) {
+      record_cuda_error(e);
+      return nullptr;
+    }
+    cached[dev] = static_cast<unsigned char*>(p);
+  }
+  return cached[dev];
+}
+
+}  // namespace nasg
+
+extern "C" nasg_status nasg_frustum_compact_noalloc(int64_t n, const float* means, const float* rot,
+                                                    const float* center, float tan_half_fov, float near_z,
+                                                    int32_t* idx, int32_t* n_visible, void* stream) {
+  if (n < 0) return NASG_ERR_RANGE;
+  if (n > kNoAllocMaxPrims) return NASG_ERR_CAPACITY;
+  if (!rot || !center || !n_visible) return NASG_ERR_NULL;
+  if (!(tan_half_fov > 0.f)) return NASG_ERR_RANGE;
+  cudaStream_t s = as_stream(stream);
+  if (n == 0) {
+    if (cudaMemsetAsync(n_visible, 0, sizeof(int32_t), s) != cudaSuccess) return check_launch();
+    return NASG_OK;
+  }
+  if (!means || !idx) return NASG_ERR_NULL;
+  if (!aligned(means, 4) || !aligned(idx, 4) || !aligned(n_visible, 4)) return NASG_ERR_ALIGN;
+  unsigned char* ws = noalloc_scratch();
+  if (!ws) return NASG_ERR_CUDA;
+  // Every byte the kernels read is written earlier in the same call (flags for
+  // i < n, counts and offsets for the n's chunks), so nothing needs clearing.
+  const int64_t nb = compact_blocks(n);
+  uint8_t* flags = ws;
+  int32_t* counts = reinterpret_cast<int32_t*>(ws + (n + 15) / 16 * 16);
+  int32_t* offsets = counts + nb;
+  FrustumArgs f{};
+  f.means = means;
+  f.n = n;
+  for (int j = 0; j < 9; ++j) f.r[j] = rot[j];
+  for (int j = 0; j < 3; ++j) f.c[j] = center[j];
+  f.t = tan_half_fov;
+  f.near_z = near_z;
+  frustum_count_kernel<<<unsigned(nb), kCompactBlock, 0, s>>>(f, flags, counts);
+  frustum_scan_kernel<<<1, 1024, 0, s>>>(counts, offsets, int32_t(nb), n_visible);
+  frustum_scatter_kernel<<<unsigned(nb), kCompactBlock, 0, s>>>(n, flags, offsets, idx);
+  return check_launch();
 }
