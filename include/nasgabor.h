@@ -232,6 +232,82 @@ nasg_status nasg_frustum_compact_noalloc(int64_t n, const float* means, const fl
                                          float tan_half_fov, float near_z, int32_t* idx, int32_t* n_visible,
                                          void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batched persistent forward+backward over many scenes in one launch.
+ * A scene is one parameter set with its own N, L, camera and buffers (the
+ * layouts of nasgabor_fused_fwd_bwd). The computation per scene is exactly
+ * nasgabor_fused_fwd_bwd's (eq:app_model, Supp. F), for the upstream gradient
+ * g_rgb given per scene; outputs are overwritten.
+ * ------------------------------------------------------------------------ */
+#define NASG_MAX_SCENES 256
+
+typedef struct nasg_scene {
+  int64_t n;              /* primitives (>= 0)                                  */
+  int32_t n_lobes;        /* 1..NASG_MAX_LOBES                                  */
+  int32_t reserved0;
+  const void* params;     /* device [P][N*L] (f32 or bf16, per nasg_batch_modes) */
+  const void* c0;         /* device [3][N]                                      */
+  const float* means;     /* device [N][3]                                      */
+  float cam[3];           /* camera centre (copied into the table)              */
+  float reserved1;
+  const float* g_rgb;     /* device [N][3] upstream dLoss/dRGB                  */
+  float* rgb;             /* device [N][3] output                               */
+  float* g_params;        /* device [P][N*L] f32 output                         */
+  float* g_c0;            /* device [3][N] f32 output                           */
+  float* g_means;         /* device [N][3] f32 output, nullable                 */
+} nasg_scene;
+
+typedef struct nasg_batch_modes {
+  int32_t frame_mode, param_dtype, norm_mode, act_mode;  /* shared by every scene */
+} nasg_batch_modes;
+
+/* Filled by nasgabor_batched_prepare; pass it to nasgabor_batched_run. */
+typedef struct nasg_batch_plan {
+  int32_t n_scenes, frame_mode, param_dtype, norm_mode, act_mode, sub_tiles;
+  int64_t total_tiles, total_prims, total_lobes;
+  void* workspace;
+} nasg_batch_plan;
+
+/* Launch schedule: dynamic (1: tiles from an atomic counter, 0: round-robin),
+ * blocks per SM (0: as many as fit), sub_tiles (the k prepare was called with). */
+typedef struct nasg_batch_tuning {
+  int32_t dynamic, blocks_per_sm, sub_tiles, reserved;
+} nasg_batch_tuning;
+
+/* Device workspace bytes for a batch of n_scenes (1..NASG_MAX_SCENES); 0 if out of range. */
+size_t nasgabor_batched_workspace_bytes(int32_t n_scenes);
+
+/*
+ * Validates the scenes (HOST array of n_scenes) and writes their device table
+ * and tile ranges (tiles of sub_tiles x 256/S primitives, 1 <= sub_tiles <= 64)
+ * into `workspace` (16-byte aligned, >= nasgabor_batched_workspace_bytes).
+ * Synchronises `stream` (not for use inside a stream capture). The buffers the
+ * scenes point to are read/written by later runs, not by this call.
+ */
+nasg_status nasgabor_batched_prepare(const nasg_scene* scenes, int32_t n_scenes, const nasg_batch_modes* modes,
+                                     int32_t sub_tiles, void* workspace, size_t workspace_bytes,
+                                     nasg_batch_plan* plan, void* stream);
+
+/*
+ * One persistent launch over every tile of the prepared batch (tuning may be
+ * NULL: dynamic scheduling, as many blocks as fit). Enqueues at most a 4-byte
+ * memset and one kernel on `stream` and makes no host synchronisation or
+ * allocation, so a stream capture of it records a replayable CUDA graph.
+ * Runs sharing one workspace must not overlap on the GPU.
+ */
+nasg_status nasgabor_batched_run(const nasg_batch_plan* plan, const nasg_batch_tuning* tuning, void* stream);
+
+/*
+ * Small autotuner: times every schedule (sub_tiles in {1, 2, 4, 8}, static or
+ * dynamic, 1 or 2 blocks per SM) on this batch, `reps` runs each, writes the
+ * fastest to *best (and its time to *best_ms, nullable) and leaves `workspace`
+ * and *plan prepared for it. Runs the batch's kernels (outputs are overwritten).
+ */
+nasg_status nasgabor_batched_autotune(const nasg_scene* scenes, int32_t n_scenes, const nasg_batch_modes* modes,
+                                      void* workspace, size_t workspace_bytes, int32_t reps,
+                                      nasg_batch_plan* plan, nasg_batch_tuning* best, float* best_ms,
+                                      void* stream);
+
 /*
  * Real spherical harmonics of degree 0..3 (Sec. 3.2): orthonormal real basis
  * with the Condon-Shortley phase, coefficient j = l^2 + l + m (m = -l..l).

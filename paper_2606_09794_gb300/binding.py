@@ -48,6 +48,26 @@ class NasgTrainState(ctypes.Structure):
                 ("c0_master", _vp), ("c0_m", _vp), ("c0_v", _vp), ("c0_bf16", _vp)]
 
 
+class NasgScene(ctypes.Structure):
+    _fields_ = [("n", _i64), ("n_lobes", _i32), ("reserved0", _i32), ("params", _vp), ("c0", _vp), ("means", _vp),
+                ("cam", ctypes.c_float * 3), ("reserved1", ctypes.c_float), ("g_rgb", _vp), ("rgb", _vp),
+                ("g_params", _vp), ("g_c0", _vp), ("g_means", _vp)]
+
+
+class NasgBatchModes(ctypes.Structure):
+    _fields_ = [("frame_mode", _i32), ("param_dtype", _i32), ("norm_mode", _i32), ("act_mode", _i32)]
+
+
+class NasgBatchPlan(ctypes.Structure):
+    _fields_ = [("n_scenes", _i32), ("frame_mode", _i32), ("param_dtype", _i32), ("norm_mode", _i32),
+                ("act_mode", _i32), ("sub_tiles", _i32), ("total_tiles", _i64), ("total_prims", _i64),
+                ("total_lobes", _i64), ("workspace", _vp)]
+
+
+class NasgBatchTuning(ctypes.Structure):
+    _fields_ = [("dynamic", _i32), ("blocks_per_sm", _i32), ("sub_tiles", _i32), ("reserved", _i32)]
+
+
 def _decl(name, argtypes, restype=_i32):
     fn = getattr(lib, name)
     fn.argtypes = argtypes
@@ -71,6 +91,12 @@ _decl("nasg_math_probe", [_i32, _vp, _vp, _vp, _i64, _vp])
 _decl("nasgabor_fused_step", [_P(NasgDesc), _P(NasgTrainState), _vp, _P(ctypes.c_float), _vp, _i64, _vp, _vp,
                               _P(NasgAdam), _vp, _vp, _vp])
 _decl("nasg_frustum_workspace_bytes", [_i64], ctypes.c_size_t)
+_decl("nasgabor_batched_workspace_bytes", [_i32], ctypes.c_size_t)
+_decl("nasgabor_batched_prepare", [_P(NasgScene), _i32, _P(NasgBatchModes), _i32, _vp, ctypes.c_size_t,
+                                   _P(NasgBatchPlan), _vp])
+_decl("nasgabor_batched_run", [_P(NasgBatchPlan), _P(NasgBatchTuning), _vp])
+_decl("nasgabor_batched_autotune", [_P(NasgScene), _i32, _P(NasgBatchModes), _vp, ctypes.c_size_t, _i32,
+                                    _P(NasgBatchPlan), _P(NasgBatchTuning), _P(ctypes.c_float), _vp])
 _decl("nasg_frustum_compact_noalloc", [_i64, _vp, _P(ctypes.c_float), _P(ctypes.c_float), ctypes.c_float,
                                        ctypes.c_float, _vp, _vp, _vp])
 _decl("nasg_frustum_compact", [_i64, _vp, _P(ctypes.c_float), _P(ctypes.c_float), ctypes.c_float, ctypes.c_float,
@@ -321,6 +347,67 @@ def nasg_frustum_compact(means, rot, center, tan_half_fov, near=0.0, idx=None, n
                                     _ptr(n_visible), _ptr(workspace), workspace.numel(), _stream(stream)),
            "nasg_frustum_compact")
     return idx, n_visible
+
+
+class Batch:
+    """Many scenes evaluated (forward + backward for a given upstream gradient) in one
+    persistent launch. `scenes` is a list of dicts with device tensors params, c0, means,
+    g_rgb and the camera `cam`; outputs rgb, g_params, g_c0, g_means are allocated here."""
+
+    def __init__(self, scenes, frame_mode="quat", norm_mode="approx", act_mode="raw", sub_tiles=2,
+                 want_means=True, stream=None):
+        if not scenes:
+            raise ValueError("empty batch")
+        dtype = scenes[0]["params"].dtype
+        self.modes = NasgBatchModes(FRAME[frame_mode], _param_dtype(scenes[0]["params"]), NORM[norm_mode],
+                                    ACT[act_mode])
+        self.scenes = scenes
+        arr = (NasgScene * len(scenes))()
+        for j, sc in enumerate(scenes):
+            p, c0, mu, g = sc["params"], sc["c0"], sc["means"], sc["g_rgb"]
+            for t, nm in ((p, "params"), (c0, "c0")):
+                _cuda(t, nm, dtype)
+            _cuda(mu, "means", torch.float32)
+            _cuda(g, "g_rgb", torch.float32)
+            n = mu.shape[0]
+            dev = mu.device
+            sc["rgb"] = torch.empty((n, 3), device=dev)
+            sc["g_params"] = torch.empty(p.shape, device=dev, dtype=torch.float32)
+            sc["g_c0"] = torch.empty((3, n), device=dev)
+            sc["g_means"] = torch.empty((n, 3), device=dev) if want_means else None
+            cam = [float(c) for c in sc["cam"]]
+            arr[j] = NasgScene(n, int(sc["n_lobes"]), 0, _ptr(p), _ptr(c0), _ptr(mu), (ctypes.c_float * 3)(*cam), 0.0,
+                               _ptr(g), _ptr(sc["rgb"]), _ptr(sc["g_params"]), _ptr(sc["g_c0"]),
+                               _ptr(sc["g_means"]))
+        self.arr = arr
+        nbytes = int(lib.nasgabor_batched_workspace_bytes(len(scenes)))
+        if nbytes == 0:
+            raise ValueError("too many scenes")
+        self.workspace = torch.empty(nbytes, device=scenes[0]["means"].device, dtype=torch.uint8)
+        self.plan = NasgBatchPlan()
+        self.tuning = NasgBatchTuning(1, 0, sub_tiles, 0)
+        _check(lib.nasgabor_batched_prepare(arr, len(scenes), ctypes.byref(self.modes), int(sub_tiles),
+                                            _ptr(self.workspace), nbytes, ctypes.byref(self.plan), _stream(stream)),
+               "nasgabor_batched_prepare")
+
+    @property
+    def total_lobes(self):
+        return int(self.plan.total_lobes)
+
+    def run(self, stream=None):
+        _check(lib.nasgabor_batched_run(ctypes.byref(self.plan), ctypes.byref(self.tuning), _stream(stream)),
+               "nasgabor_batched_run")
+
+    def autotune(self, reps=5, stream=None):
+        best = NasgBatchTuning()
+        ms = ctypes.c_float(0.0)
+        _check(lib.nasgabor_batched_autotune(self.arr, len(self.scenes), ctypes.byref(self.modes),
+                                             _ptr(self.workspace), self.workspace.numel(), int(reps),
+                                             ctypes.byref(self.plan), ctypes.byref(best), ctypes.byref(ms),
+                                             _stream(stream)), "nasgabor_batched_autotune")
+        self.tuning = best
+        return {"dynamic": best.dynamic, "blocks_per_sm": best.blocks_per_sm, "sub_tiles": best.sub_tiles,
+                "ms": ms.value}
 
 
 NOALLOC_MAX_PRIMS = 1 << 23

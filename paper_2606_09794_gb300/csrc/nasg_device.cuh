@@ -116,20 +116,27 @@ struct QuatFrame {
   V x[3], z[3];
 };
 
+// x = R(q/|q|) e_x, z = R(q/|q|) e_z from the homogeneous (degree-2) form of
+// the rotation columns divided by |q|^2: an error in the computed 1/|q|^2 then
+// only scales x and z, and the lobe math (1 - u from |d x z|^2) absorbs a
+// scale, whereas the unit-quaternion form with an approximate q/|q| would
+// rotate them slightly (which matters at sharpness ~1e3).
 template <class V>
 __device__ __forceinline__ void quat_frame(const V* qr, QuatFrame<V>& f) {
-  const V n2 = vfma(qr[0], qr[0], vfma(qr[1], qr[1], vfma(qr[2], qr[2], qr[3] * qr[3])));
+  const V qw = qr[0], qx = qr[1], qy = qr[2], qz = qr[3];
+  const V ww = qw * qw, xx = qx * qx, yy = qy * qy, zz = qz * qz;
+  const V n2 = (ww + xx) + (yy + zz);
   const V inv = vrsqrt(n2);
+  const V inv2 = vrcp(n2);
   f.inv_norm = inv;
-  const V w = qr[0] * inv, x = qr[1] * inv, y = qr[2] * inv, z = qr[3] * inv;
-  f.q[0] = w; f.q[1] = x; f.q[2] = y; f.q[3] = z;
-  // first and third columns of the rotation matrix of the unit quaternion
-  f.x[0] = 1.f - 2.f * vfma(y, y, z * z);
-  f.x[1] = 2.f * vfma(x, y, w * z);
-  f.x[2] = 2.f * vfma(x, z, -(w * y));
-  f.z[0] = 2.f * vfma(x, z, w * y);
-  f.z[1] = 2.f * vfma(y, z, -(w * x));
-  f.z[2] = 1.f - 2.f * vfma(x, x, y * y);
+  f.q[0] = qw * inv; f.q[1] = qx * inv; f.q[2] = qy * inv; f.q[3] = qz * inv;
+  const V two_inv2 = 2.f * inv2;
+  f.x[0] = ((ww + xx) - (yy + zz)) * inv2;
+  f.x[1] = vfma(qx, qy, qw * qz) * two_inv2;
+  f.x[2] = vfma(qx, qz, -(qw * qy)) * two_inv2;
+  f.z[0] = vfma(qx, qz, qw * qy) * two_inv2;
+  f.z[1] = vfma(qy, qz, -(qw * qx)) * two_inv2;
+  f.z[2] = ((ww + zz) - (xx + yy)) * inv2;
 }
 
 // dLoss/dq_raw from dLoss/dx (L) and dLoss/dz (M), through the unit-quaternion

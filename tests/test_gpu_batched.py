@@ -1,0 +1,120 @@
+"""The batched persistent launch: every scene's outputs equal the single-scene fused
+kernel's (same arithmetic, up to FMA contraction in a few scalar terms), oracle
+parity on sampled scenes, replay from a captured CUDA graph, and the autotuner."""
+import numpy as np
+import pytest
+
+from oracle import nasgabor as ong
+from paper_2606_09794_gb300 import inputs
+from tests._parity import colour_report, rel_l2, sensitivity_floor
+
+pytestmark = pytest.mark.gpu
+
+
+def _scenes(sizes, seed, bf16, frame="quat"):
+    import torch
+    out = []
+    for j, (n, L) in enumerate(sizes):
+        w = inputs.point_cloud_workload(n, L, seed + j, frame)
+        p = torch.from_numpy(w.params).cuda()
+        c0 = torch.from_numpy(w.c0).cuda()
+        if bf16:
+            p, c0 = p.to(torch.bfloat16), c0.to(torch.bfloat16)
+        cam = (0.1 * j, -0.05 * j, 3.0)
+        out.append(dict(params=p, c0=c0, means=torch.from_numpy(w.means).cuda(), g_rgb=torch.from_numpy(w.g_rgb).cuda(),
+                        cam=cam, n_lobes=L, w=w))
+    return out
+
+
+def _compare_with_single(lib, scenes, frame="quat"):
+    import torch
+    for sc in scenes:
+        if sc["means"].shape[0] == 0:
+            continue
+        ref = lib.nasgabor_fused_fwd_bwd(sc["params"], sc["c0"], sc["means"], sc["cam"], sc["g_rgb"], sc["n_lobes"],
+                                         frame_mode=frame)
+        torch.testing.assert_close(sc["rgb"], ref[0], rtol=1e-6, atol=1e-5)
+        gp, rp = sc["g_params"].cpu().numpy(), ref[1].cpu().numpy()
+        assert max(rel_l2(gp[p], rp[p]) for p in range(gp.shape[0])) < 1e-5
+        torch.testing.assert_close(sc["g_c0"], ref[2], rtol=0, atol=0)
+        assert rel_l2(sc["g_means"].cpu().numpy(), ref[3].cpu().numpy()) < 1e-5
+
+
+SIZES = [(5000, 8), (1, 4), (777, 16), (12345, 4), (0, 8), (4099, 3), (2048, 8), (301, 1)]
+
+
+@pytest.mark.parametrize("bf16", [True, False])
+@pytest.mark.parametrize("dynamic,sub_tiles", [(1, 1), (0, 3), (1, 8)])
+def test_batched_equals_single_scene_kernel(lib, bf16, dynamic, sub_tiles):
+    scenes = _scenes(SIZES, 300, bf16)
+    b = lib.Batch(scenes, sub_tiles=sub_tiles)
+    b.tuning.dynamic = dynamic
+    b.run()
+    lib.nasg_device_status()
+    _compare_with_single(lib, scenes)
+
+
+def test_batched_cos_frames(lib):
+    scenes = _scenes([(3000, 8), (1001, 5)], 400, True, "cos")
+    b = lib.Batch(scenes, frame_mode="cos")
+    b.run()
+    _compare_with_single(lib, scenes, "cos")
+
+
+def test_batched_oracle_parity(lib):
+    import torch
+    scenes = _scenes([(2000, 8), (900, 16), (1500, 4)], 500, True)
+    b = lib.Batch(scenes)
+    b.run()
+    torch.cuda.synchronize()
+    for sc in scenes:
+        w, L = sc["w"], sc["n_lobes"]
+        pq, cq = inputs.quantize_bf16(w.params), inputs.quantize_bf16(w.c0)
+        cam = np.asarray(sc["cam"], np.float32)
+
+        def fwd(p, c, m, cm):
+            return ong.forward(p, c, m, cm, L)
+
+        ref, nu = sensitivity_floor(fwd, (pq, cq, w.means, cam), (0, 1, 2, 3))
+        rep = colour_report(sc["rgb"].cpu().numpy(), ref, nu, 4e-3)
+        assert rep["violations"] == 0, rep
+        r_p, _, r_mu = ong.backward(pq, cq, w.means, cam, w.g_rgb, L)
+        gp = sc["g_params"].cpu().numpy()
+        assert max(rel_l2(gp[p], r_p[p]) for p in range(10)) <= 1e-4
+        assert rel_l2(sc["g_means"].cpu().numpy(), r_mu) <= 1e-4
+
+
+def test_batched_cuda_graph_replay_and_autotune(lib):
+    import torch
+    scenes = _scenes([(20000, 8), (3000, 16), (7000, 4), (50, 8)], 600, True)
+    b = lib.Batch(scenes)
+    best = b.autotune(reps=2)
+    assert best["sub_tiles"] in (1, 2, 4, 8) and best["ms"] > 0
+    b.run()
+    torch.cuda.synchronize()
+    eager = [sc["g_params"].clone() for sc in scenes]
+    for sc in scenes:
+        sc["g_params"].zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            b.run(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    for e, sc in zip(eager, scenes):
+        torch.testing.assert_close(sc["g_params"], e, rtol=0, atol=0)
+
+
+def test_batched_rejects_bad_batches(lib):
+    import ctypes
+    plan = lib.NasgBatchPlan()
+    modes = lib.NasgBatchModes(0, 0, 0, 0)
+    arr = (lib.NasgScene * 1)()
+    assert lib.lib.nasgabor_batched_prepare(arr, 0, ctypes.byref(modes), 1, ctypes.c_void_p(16), 1 << 20,
+                                            ctypes.byref(plan), None) == -2
+    assert lib.lib.nasgabor_batched_prepare(arr, 300, ctypes.byref(modes), 1, ctypes.c_void_p(16), 1 << 20,
+                                            ctypes.byref(plan), None) == -2
