@@ -397,6 +397,9 @@ def main():
     paths = None
     if rank == 0 and world == 1 and not args.no_paths:
         paths = measure_paths(nb, inputs, w, params, dev, stream, peak)
+        del w
+        paths["scene_step"] = measure_scene_step(nb, inputs, dev, stream, peak)
+        paths["batched"] = measure_batched(nb, inputs, dev, stream, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -488,6 +491,97 @@ def measure_paths(nb, inputs, w, params_bf16, dev, stream, peak, reps=200):
         "sh3_fwd_then_bwd": {"value": N / (t_sh * 1e-6), "unit": "primitives/s",
                              "value_basis_lobes": 16 * N / (t_sh * 1e-6), "us": t_sh},
     }
+
+
+def bytes_step(L, P=10):
+    """Fused forward+backward+Adam per visible primitive: per lobe master, m, v read and
+    written (3 x 2 x 4 B per scalar) and the bf16 copy written (2 B per scalar); per
+    primitive the index (4), mean (12), upstream gradient (12) read, colour written (12),
+    c0 master/m/v read and written (3 x 24) and its bf16 copy written (6)."""
+    return L * P * (24 + 2) + 4 + 12 + 12 + 12 + 72 + 6
+
+
+def measure_scene_step(nb, inputs, dev, stream, peak, n=6_000_000, L=8, seed=1003, order="morton"):
+    """Scene-scale training step: noisy-shell scene (primitives stored in Morton order of
+    their centres), 8 cameras on a ring, per camera the ordered frustum compaction then one
+    fused forward+backward+Adam step (BF16 copies of an FP32 master) on the visible
+    primitives, all on one stream with no host sync."""
+    import torch
+    sc = inputs.shell_scene(n, L, seed, order=order)
+    st = nb.TrainState(torch.from_numpy(sc.params).to(dev), torch.from_numpy(sc.c0).to(dev))
+    means = torch.from_numpy(sc.means).to(dev)
+    del sc.params
+    gs = [torch.from_numpy(inputs.ring_upstream(n, j, seed)).to(dev) for j in range(len(sc.cameras))]
+    ws = torch.empty(nb.nasg_frustum_workspace_bytes(n), device=dev, dtype=torch.uint8)
+    idx = torch.empty(n, device=dev, dtype=torch.int32)
+    nvis = [torch.empty(1, device=dev, dtype=torch.int32) for _ in sc.cameras]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * len(sc.cameras) + 1)]
+
+    def ring(t0, record):
+        for j, cam in enumerate(sc.cameras):
+            if record:
+                ev[3 * j].record(stream)
+            nb.nasg_frustum_compact(means, cam.rot, cam.center, cam.tan_half_fov, idx=idx, n_visible=nvis[j],
+                                    workspace=ws, stream=stream)
+            if record:
+                ev[3 * j + 1].record(stream)
+            nb.nasgabor_fused_step(st, means, cam.center, gs[j], L, t0 + j + 1, idx=idx, n_idx_device=nvis[j],
+                                   stream=stream)
+            if record:
+                ev[3 * j + 2].record(stream)
+
+    ring(0, False)
+    torch.cuda.synchronize(dev)
+    ring(len(sc.cameras), True)
+    torch.cuda.synchronize(dev)
+    vis = [int(v.item()) for v in nvis]
+    step_us = [ev[3 * j + 1].elapsed_time(ev[3 * j + 2]) * 1e3 for j in range(len(sc.cameras))]
+    comp_us = [ev[3 * j].elapsed_time(ev[3 * j + 1]) * 1e3 for j in range(len(sc.cameras))]
+    total_us = ev[0].elapsed_time(ev[3 * len(sc.cameras) - 1]) * 1e3
+    step_bytes = sum(v * bytes_step(L) for v in vis)
+    gbs = step_bytes / (sum(step_us) * 1e-6) / 1e9
+    return {"workload": f"noisy shell N={n} ({order} storage order), L={L}, 8 ring cameras, ~45% visible each, "
+                        "BF16 copies of FP32 master",
+            "visible_per_camera": vis, "step_us_per_camera": step_us, "compaction_us_per_camera": comp_us,
+            "total_us_8_cameras": total_us,
+            "value": sum(vis) * L / (total_us * 1e-6), "unit": "visible primitive-lobes/s (incl. compaction)",
+            "step_alg_bytes_per_visible_primitive": bytes_step(L), "step_gbs": gbs, "step_frac": gbs / peak}
+
+
+def measure_batched(nb, inputs, dev, stream, peak, n_scenes=32, seed=1004, reps=20):
+    """Batched persistent launch: 32 scenes, N log-uniform in [5e4, 3e6], L uniform in
+    {4, 8, 16}, BF16 parameters, fwd+bwd in one autotuned persistent kernel replayed
+    from a CUDA graph."""
+    import torch
+    sizes = inputs.batched_scene_sizes(n_scenes, seed)
+    scenes = [inputs.device_point_cloud(n, L, seed * 100 + j, dev, torch.bfloat16) for j, (n, L) in enumerate(sizes)]
+    b = nb.Batch(scenes)
+    tune = b.autotune(reps=3, stream=stream)
+    g = torch.cuda.CUDAGraph()
+    s2 = torch.cuda.Stream(dev)
+    s2.wait_stream(stream)
+    with torch.cuda.stream(s2):
+        with torch.cuda.graph(g, stream=s2):
+            b.run(stream=s2)
+    stream.wait_stream(s2)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(torch.cuda.current_stream(dev))
+    for _ in range(reps):
+        g.replay()
+    e1.record(torch.cuda.current_stream(dev))
+    e1.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / reps
+    alg = sum(n * bytes_fused_bf16(L) for n, L in sizes)
+    gbs = alg / (us * 1e-6) / 1e9
+    return {"workload": f"{n_scenes} scenes, N log-uniform [5e4, 3e6], L in {{4, 8, 16}}, BF16, one persistent launch "
+                        "replayed from a CUDA graph",
+            "total_primitives": int(sum(n for n, _ in sizes)), "total_lobes": b.total_lobes, "us": us,
+            "value": b.total_lobes / (us * 1e-6), "unit": UNIT, "tuning": tune, "alg_bytes": alg, "gbs": gbs,
+            "frac": gbs / peak}
 
 
 if __name__ == "__main__":

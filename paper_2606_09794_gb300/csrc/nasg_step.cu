@@ -52,15 +52,22 @@ __device__ __forceinline__ void adam(const StepArgs& s, float g, float& th, floa
   th = fmaf(-s.step_size, m * rcpa(den), th);
 }
 
+// Phase one of a step item: the lobe math. The lane's P gradient pairs are
+// parked in its own shared-memory slot (gslot[p * 256]) rather than kept in
+// registers, so that phase two starts with a fresh register budget and can
+// issue all of its moment and master loads at once. Also does the
+// per-primitive work (colour, dLoss/dmu, c0 Adam). Returns whether the lane
+// holds lobes to update.
 template <int FRAME, typename IDX, bool EVEN>
-__device__ __forceinline__ void step_item(const StepArgs& s, const RawItem<float, FrameTraits<FRAME>::P>& cur, IDX i,
-                                          int l0) {
+__device__ __forceinline__ bool step_phase1(const StepArgs& s, const RawItem<float, FrameTraits<FRAME>::P>& cur,
+                                            IDX i, int l0, float2* gslot) {
   constexpr int P = FrameTraits<FRAME>::P;
   const EvalArgs& a = s.e;
   const IDX n = IDX(a.n);
   const IDX L = IDX(a.n_lobes);
   const bool ok = cur.ok != 0;
   const bool quant = s.quantize != 0;
+  bool mine = false;
   float rgb[3] = {0.f, 0.f, 0.f};
   float gd[3] = {0.f, 0.f, 0.f};
   float d[3] = {0.f, 0.f, 1.f};
@@ -70,6 +77,7 @@ __device__ __forceinline__ void step_item(const StepArgs& s, const RawItem<float
     inv_dist = rsqrtf(rx * rx + ry * ry + rz * rz);
     d[0] = rx * inv_dist; d[1] = ry * inv_dist; d[2] = rz * inv_dist;
     if (IDX(l0) < L) {
+      mine = true;
       const bool second = EVEN || (IDX(l0) + 1 < L);
       P2 pv[P];
 #pragma unroll
@@ -88,39 +96,8 @@ __device__ __forceinline__ void step_item(const StepArgs& s, const RawItem<float
         rgb[c] = rgbv[c].v.x + (second ? rgbv[c].v.y : 0.f);
         gd[c] = gdv[c].v.x + (second ? gdv[c].v.y : 0.f);
       }
-      const IDX NL = n * L;
-      IDX off = i * L + IDX(l0);
 #pragma unroll
-      for (int p = 0; p < P; ++p, off += NL) {
-        float2 th = cur.w[p];
-        float2 mm, vv;
-        if (EVEN) {
-          mm = *reinterpret_cast<const float2*>(s.m + off);
-          vv = *reinterpret_cast<const float2*>(s.v + off);
-        } else {
-          mm = make_float2(s.m[off], second ? s.m[off + 1] : 0.f);
-          vv = make_float2(s.v[off], second ? s.v[off + 1] : 0.f);
-        }
-        adam(s, gp[p].v.x, th.x, mm.x, vv.x);
-        adam(s, gp[p].v.y, th.y, mm.y, vv.y);
-        float* master = static_cast<float*>(const_cast<void*>(a.params));
-        if (EVEN) {
-          *reinterpret_cast<float2*>(master + off) = th;
-          *reinterpret_cast<float2*>(s.m + off) = mm;
-          *reinterpret_cast<float2*>(s.v + off) = vv;
-          if (s.pbf) {
-            const uint32_t w2 = uint32_t(bf16_bits(th.x)) | (uint32_t(bf16_bits(th.y)) << 16);
-            *reinterpret_cast<uint32_t*>(s.pbf + off) = w2;
-          }
-        } else {
-          master[off] = th.x; s.m[off] = mm.x; s.v[off] = vv.x;
-          if (s.pbf) s.pbf[off] = bf16_bits(th.x);
-          if (second) {
-            master[off + 1] = th.y; s.m[off + 1] = mm.y; s.v[off + 1] = vv.y;
-            if (s.pbf) s.pbf[off + 1] = bf16_bits(th.y);
-          }
-        }
-      }
+      for (int p = 0; p < P; ++p) gslot[p * 256] = gp[p].v;
     }
   }
   for (int o = a.slice >> 1; o >= 1; o >>= 1) {
@@ -146,11 +123,69 @@ __device__ __forceinline__ void step_item(const StepArgs& s, const RawItem<float
       if (s.c0bf) s.c0bf[o] = bf16_bits(th);
     }
   }
+  return mine;
+}
+
+// Phase two: Adam on the lane's two lobes for every plane, in batches of
+// planes: all loads of a batch first (master, m, v), then the updates and stores.
+template <int P, typename IDX, bool EVEN>
+__device__ __forceinline__ void step_phase2(const StepArgs& s, IDX i, int l0, const float2* gslot) {
+  constexpr int kBatch = (P + 1) / 2;
+  const EvalArgs& a = s.e;
+  const IDX n = IDX(a.n);
+  const IDX L = IDX(a.n_lobes);
+  const IDX NL = n * L;
+  const IDX off0 = i * L + IDX(l0);
+  const bool second = EVEN || (IDX(l0) + 1 < L);
+  float* master = static_cast<float*>(const_cast<void*>(a.params));
+#pragma unroll
+  for (int p0 = 0; p0 < P; p0 += kBatch) {
+    float2 th[kBatch], mm[kBatch], vv[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      if (p0 + j >= P) break;
+      const IDX off = off0 + IDX(p0 + j) * NL;
+      if (EVEN) {
+        th[j] = *reinterpret_cast<const float2*>(master + off);
+        mm[j] = *reinterpret_cast<const float2*>(s.m + off);
+        vv[j] = *reinterpret_cast<const float2*>(s.v + off);
+      } else {
+        th[j] = make_float2(master[off], second ? master[off + 1] : 0.f);
+        mm[j] = make_float2(s.m[off], second ? s.m[off + 1] : 0.f);
+        vv[j] = make_float2(s.v[off], second ? s.v[off + 1] : 0.f);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      if (p0 + j >= P) break;
+      const float2 g = gslot[(p0 + j) * 256];
+      adam(s, g.x, th[j].x, mm[j].x, vv[j].x);
+      adam(s, g.y, th[j].y, mm[j].y, vv[j].y);
+      const IDX off = off0 + IDX(p0 + j) * NL;
+      if (EVEN) {
+        *reinterpret_cast<float2*>(master + off) = th[j];
+        *reinterpret_cast<float2*>(s.m + off) = mm[j];
+        *reinterpret_cast<float2*>(s.v + off) = vv[j];
+        if (s.pbf) {
+          const uint32_t w2 = uint32_t(bf16_bits(th[j].x)) | (uint32_t(bf16_bits(th[j].y)) << 16);
+          *reinterpret_cast<uint32_t*>(s.pbf + off) = w2;
+        }
+      } else {
+        master[off] = th[j].x; s.m[off] = mm[j].x; s.v[off] = vv[j].x;
+        if (s.pbf) s.pbf[off] = bf16_bits(th[j].x);
+        if (second) {
+          master[off + 1] = th[j].y; s.m[off + 1] = mm[j].y; s.v[off + 1] = vv[j].y;
+          if (s.pbf) s.pbf[off + 1] = bf16_bits(th[j].y);
+        }
+      }
+    }
+  }
 }
 
 template <int FRAME, typename IDX, bool EVEN>
 __global__ void __launch_bounds__(256, 2) step_kernel(const StepArgs s) {
   constexpr int P = FrameTraits<FRAME>::P;
+  __shared__ float2 gbuf[P * 256];  // per-thread gradient slots (no sharing, no barrier)
   const EvalArgs& a = s.e;
   int64_t items = a.n_items;
   if (s.n_dev) {
@@ -160,14 +195,13 @@ __global__ void __launch_bounds__(256, 2) step_kernel(const StepArgs s) {
   const int l0 = 2 * (threadIdx.x & (a.slice - 1));
   const IDX total = IDX(items) << a.slice_log2;
   const IDX stride = IDX(gridDim.x) * blockDim.x;
-  // block-uniform loop: every lane of a warp reaches the shuffles in step_item.
-  // No register prefetch here: the step moves ~2 KB per primitive, and the
-  // moment loads of phase two already keep enough bytes in flight.
+  float2* gslot = gbuf + threadIdx.x;
+  // block-uniform loop: every lane of a warp reaches the shuffles in phase one
   for (IDX t0 = IDX(blockIdx.x) * blockDim.x; t0 < total; t0 += stride) {
     RawItem<float, P> cur;
     IDX i = 0;
     fetch_item<float, P, IDX, EVEN, true, true>(a, total, t0 + threadIdx.x, l0, cur, i);
-    step_item<FRAME, IDX, EVEN>(s, cur, i, l0);
+    if (step_phase1<FRAME, IDX, EVEN>(s, cur, i, l0, gslot)) step_phase2<P, IDX, EVEN>(s, i, l0, gslot);
   }
 }
 

@@ -195,15 +195,30 @@ class ShellScene:
     cameras: list
 
 
+def morton_order(points: np.ndarray, bits: int = 10) -> np.ndarray:
+    """Permutation that sorts points by the Morton (Z-order) code of their
+    coordinates quantised to `bits` bits per axis over their bounding box."""
+    p = np.asarray(points, dtype=np.float64)
+    lo = p.min(axis=0)
+    span = np.maximum(p.max(axis=0) - lo, 1e-30)
+    q = np.minimum(((p - lo) / span * (1 << bits)).astype(np.int64), (1 << bits) - 1)
+    code = np.zeros(len(p), dtype=np.int64)
+    for b in range(bits):
+        for axis in range(3):
+            code |= ((q[:, axis] >> b) & 1) << (3 * b + axis)
+    return np.argsort(code, kind="stable")
+
+
 def shell_scene(n: int, n_lobes: int, seed: int, n_cams: int = 8, ring_radius: float = 4.0,
                 target_visible: float = 0.45, frame_mode: str = FRAME_QUAT,
-                fov_sample: int = 200_000) -> ShellScene:
+                fov_sample: int = 200_000, order: str = "random") -> ShellScene:
     """Gaussians on a noisy sphere shell (radius U[1, 2]) and a ring of pinhole cameras.
 
     Cameras sit on the z=0 circle of radius `ring_radius` at angles 2*pi*j/n_cams,
     look at the origin with +z up, and share one symmetric field of view chosen
     by bisection so that camera 0 sees `target_visible` of the primitives
-    (measured on a seeded subsample of `fov_sample` primitives).
+    (measured on a seeded subsample of `fov_sample` primitives). order="morton"
+    stores the primitives in Morton order of their centres (same values).
     """
     st = _streams(seed)
     dirs = st["positions"].standard_normal((n, 3))
@@ -230,6 +245,16 @@ def shell_scene(n: int, n_lobes: int, seed: int, n_cams: int = 8, ring_radius: f
             hi = mid
     t = float(np.float32(0.5 * (lo + hi)))
     cameras = [RingCamera(c.astype(np.float32), r.astype(np.float32), t) for c, r in cams]
+    if order == "morton":
+        # spatially coherent storage order (a layout choice: the primitives and
+        # their values are the same, permuted together)
+        perm = morton_order(means)
+        means = np.ascontiguousarray(means[perm])
+        c0 = np.ascontiguousarray(c0[:, perm])
+        params = np.ascontiguousarray(
+            params.reshape(params.shape[0], n, n_lobes)[:, perm, :].reshape(params.shape[0], -1))
+    elif order != "random":
+        raise ValueError(order)
     return ShellScene(n, n_lobes, frame_mode, params, c0, means, cameras)
 
 
@@ -268,3 +293,32 @@ def subsample_indices(n: int, count: int, seed: int) -> np.ndarray:
     """Sorted seeded subsample of primitive indices (int64)."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5AB]))
     return np.sort(rng.choice(n, size=min(count, n), replace=False))
+
+
+# ---------------------------------------------------------------------------
+# On-device generation for the large throughput workloads (same distributions,
+# drawn with torch's seeded generator on the GPU instead of numpy on the host).
+# ---------------------------------------------------------------------------
+
+def device_point_cloud(n: int, n_lobes: int, seed: int, device, param_dtype=None):
+    """Point-cloud workload drawn on `device`: dict with params [P][N*L], c0 [3][N],
+    means [N][3], g_rgb [N][3] (float32, params/c0 cast to param_dtype) and cam."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    count = n * n_lobes
+    q = torch.randn((4, count), generator=g, device=device)
+    q = q / q.norm(dim=0, keepdim=True)
+    lam_r = torch.rand(count, generator=g, device=device) * math.log(1e3)
+    a_r = torch.log(torch.rand(count, generator=g, device=device).clamp_min(_A_MIN))
+    k = (torch.rand(count, generator=g, device=device) * 8.0).clamp_min(_K_MIN)
+    k_r = torch.atanh(k / 20.0 - 1.0)
+    w_r = torch.atanh(torch.rand((3, count), generator=g, device=device).clamp_max(_W_MAX))
+    params = torch.cat([q, lam_r[None], a_r[None], k_r[None], w_r]).contiguous()
+    c0 = torch.rand((3, n), generator=g, device=device)
+    means = torch.rand((n, 3), generator=g, device=device)
+    g_rgb = torch.randn((n, 3), generator=g, device=device)
+    if param_dtype is not None:
+        params = params.to(param_dtype)
+        c0 = c0.to(param_dtype)
+    return {"params": params, "c0": c0, "means": means, "g_rgb": g_rgb, "cam": (0.0, 0.0, 3.0), "n_lobes": n_lobes}
