@@ -308,6 +308,28 @@ nasg_status nasgabor_batched_autotune(const nasg_scene* scenes, int32_t n_scenes
                                       nasg_batch_plan* plan, nasg_batch_tuning* best, float* best_ms,
                                       void* stream);
 
+/* Bytes of device workspace nasgabor_fit_step needs (per-block loss partials). */
+size_t nasgabor_fit_workspace_bytes(void);
+
+/*
+ * One step of fitting the student mixture (desc: N, L_s even, QUAT frames; the
+ * student lives in `state` as for nasgabor_fused_step, evaluated at the BF16
+ * values when desc->param_dtype is BF16) to a teacher field (teacher_params
+ * [P][N*L_t] raw f32, teacher_c0 [3][N] f32, L_t even with L_t/2 a power of two
+ * dividing the student's lanes per primitive) at the n_dirs unit directions
+ * dirs [n_dirs][3] (device, shared by all primitives). Per primitive the loss is
+ * the mean over (direction, channel) of (student - teacher colour)^2; its
+ * gradient summed over the directions takes one Adam step of every primitive
+ * (lobe parameters and c0). *loss (device f32) receives the mean squared error
+ * over all (primitive, direction, channel). workspace: device scratch of
+ * nasgabor_fit_workspace_bytes() bytes. Deterministic. NASG_ERR_UNSUPPORTED for
+ * COS frames or lobe counts outside the stated shapes.
+ */
+nasg_status nasgabor_fit_step(const nasg_desc* desc, const nasg_train_state* state, const float* teacher_params,
+                              const float* teacher_c0, int32_t teacher_lobes, const float* dirs, int32_t n_dirs,
+                              const nasg_adam_hparams* hparams, float* loss, void* workspace,
+                              size_t workspace_bytes, void* stream);
+
 /*
  * Real spherical harmonics of degree 0..3 (Sec. 3.2): orthonormal real basis
  * with the Condon-Shortley phase, coefficient j = l^2 + l + m (m = -l..l).

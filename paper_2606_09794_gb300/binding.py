@@ -92,6 +92,9 @@ _decl("nasgabor_fused_step", [_P(NasgDesc), _P(NasgTrainState), _vp, _P(ctypes.c
                               _P(NasgAdam), _vp, _vp, _vp])
 _decl("nasg_frustum_workspace_bytes", [_i64], ctypes.c_size_t)
 _decl("nasgabor_batched_workspace_bytes", [_i32], ctypes.c_size_t)
+_decl("nasgabor_fit_workspace_bytes", [], ctypes.c_size_t)
+_decl("nasgabor_fit_step", [_P(NasgDesc), _P(NasgTrainState), _vp, _vp, _i32, _vp, _i32, _P(NasgAdam), _vp, _vp,
+                            ctypes.c_size_t, _vp])
 _decl("nasgabor_batched_prepare", [_P(NasgScene), _i32, _P(NasgBatchModes), _i32, _vp, ctypes.c_size_t,
                                    _P(NasgBatchPlan), _vp])
 _decl("nasgabor_batched_run", [_P(NasgBatchPlan), _P(NasgBatchTuning), _vp])
@@ -408,6 +411,29 @@ class Batch:
         self.tuning = best
         return {"dynamic": best.dynamic, "blocks_per_sm": best.blocks_per_sm, "sub_tiles": best.sub_tiles,
                 "ms": ms.value}
+
+
+def nasgabor_fit_step(state, teacher_params, teacher_c0, teacher_lobes, dirs, n_lobes, step, lr=1e-3, beta1=0.9,
+                      beta2=0.999, eps=1e-8, evaluate_bf16=True, loss=None, workspace=None, norm_mode="approx",
+                      act_mode="raw", stream=None):
+    """One fitting step of the student (TrainState) to the teacher field at the directions
+    dirs [D][3]; returns the device scalar loss (mean squared colour error)."""
+    _cuda(teacher_params, "teacher_params", torch.float32)
+    _cuda(teacher_c0, "teacher_c0", torch.float32)
+    _cuda(dirs, "dirs", torch.float32)
+    n = state.c0_master.shape[1]
+    dev = dirs.device
+    if loss is None:
+        loss = torch.empty(1, device=dev, dtype=torch.float32)
+    if workspace is None:
+        workspace = torch.empty(int(lib.nasgabor_fit_workspace_bytes()), device=dev, dtype=torch.uint8)
+    desc = make_desc(n, n_lobes, "quat", torch.bfloat16 if evaluate_bf16 else torch.float32, norm_mode, act_mode)
+    hp = NasgAdam(lr, beta1, beta2, eps, int(step))
+    st = state.as_c()
+    _check(lib.nasgabor_fit_step(ctypes.byref(desc), ctypes.byref(st), _ptr(teacher_params), _ptr(teacher_c0),
+                                 int(teacher_lobes), _ptr(dirs), dirs.shape[0], ctypes.byref(hp), _ptr(loss),
+                                 _ptr(workspace), workspace.numel(), _stream(stream)), "nasgabor_fit_step")
+    return loss
 
 
 NOALLOC_MAX_PRIMS = 1 << 23

@@ -1,0 +1,90 @@
+"""GPU parity of the teacher-student fitting step against the FP64 oracle
+(oracle/adam.py fit_step: per-primitive mean squared colour error over the
+shared directions, gradient summed over them, one Adam step, BF16 storage)."""
+import numpy as np
+import pytest
+
+from oracle import adam as oad
+from paper_2606_09794_gb300 import inputs
+from tests._parity import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _setup(lib, n, ls, lt, seed, warm):
+    t = inputs.point_cloud_workload(n, lt, seed)
+    s = inputs.point_cloud_workload(n, ls, seed + 1)
+    rng = np.random.default_rng(seed)
+    m = (0.01 * rng.standard_normal(s.params.shape)).astype(np.float32) if warm else np.zeros_like(s.params)
+    v = (1e-4 * (1 + rng.random(s.params.shape))).astype(np.float32) if warm else np.zeros_like(s.params)
+    cm = (0.01 * rng.standard_normal(s.c0.shape)).astype(np.float32) if warm else np.zeros_like(s.c0)
+    cv = (1e-4 * (1 + rng.random(s.c0.shape))).astype(np.float32) if warm else np.zeros_like(s.c0)
+    st = lib.TrainState(_dev(s.params), _dev(s.c0), _dev(m), _dev(v), _dev(cm), _dev(cv))
+    return t, s, st, (m, v, cm, cv)
+
+
+@pytest.mark.parametrize("ls,lt,ndirs", [(16, 4, 64), (8, 4, 13), (4, 2, 7)])
+def test_fit_steps_match_oracle(lib, ls, lt, ndirs):
+    n = 96
+    t, s, st, (m, v, cm, cv) = _setup(lib, n, ls, lt, 41 + ls, warm=True)
+    tp, tc = _dev(t.params), _dev(t.c0)
+    state = {"student": s.params.astype(np.float64), "m": m.astype(np.float64), "v": v.astype(np.float64),
+             "c0": s.c0.astype(np.float64), "c0_m": cm.astype(np.float64), "c0_v": cv.astype(np.float64)}
+    for step in range(1, 4):
+        dirs = inputs.fit_directions(step, 7, ndirs)
+        loss = lib.nasgabor_fit_step(st, tp, tc, lt, _dev(dirs), ls, step)
+        new, mse = oad.fit_step(state["student"], state["m"], state["v"], state["c0"], state["c0_m"], state["c0_v"],
+                                t.params, t.c0, dirs, ls, lt, step)
+        assert abs(float(loss.item()) - mse) <= 1e-4 * mse + 1e-9, (float(loss.item()), mse)
+        got = st.master.cpu().numpy().astype(np.float64)
+        for p in range(10):
+            d_gpu = got[p] - state["student"][p]
+            d_ref = new["student"][p] - state["student"][p]
+            assert rel_l2(d_gpu, d_ref) < 2e-3, (step, p, rel_l2(d_gpu, d_ref))
+        assert rel_l2(st.m.cpu().numpy(), new["m"]) < 1e-4
+        # continue both from the GPU's state so that the comparison stays one step deep
+        state = {"student": got, "m": st.m.cpu().numpy().astype(np.float64), "v": st.v.cpu().numpy().astype(np.float64),
+                 "c0": st.c0_master.cpu().numpy().astype(np.float64),
+                 "c0_m": st.c0_m.cpu().numpy().astype(np.float64), "c0_v": st.c0_v.cpu().numpy().astype(np.float64)}
+    import torch
+    torch.testing.assert_close(st.params_bf16, st.master.to(torch.bfloat16), rtol=0, atol=0)
+
+
+def test_fit_run_matches_oracle_fit_on_a_sample(lib):
+    """200 steps of 64 directions on 4096 primitives (L_s = 16 BF16, L_t = 4 FP32);
+    the oracle runs the same fit from the same start on a seeded sample of 64
+    primitives (primitives are independent); final per-sample MSE within 1 %."""
+    n, ls, lt, steps = 4096, 16, 4, 200
+    t, s, st, _ = _setup(lib, n, ls, lt, 1005, warm=False)
+    tp, tc = _dev(t.params), _dev(t.c0)
+    for step in range(1, steps + 1):
+        lib.nasgabor_fit_step(st, tp, tc, lt, _dev(inputs.fit_directions(step, 1005)), ls, step)
+    sample = inputs.subsample_indices(n, 64, 3)
+    lobes_s = (sample[:, None] * ls + np.arange(ls)).reshape(-1)
+    lobes_t = (sample[:, None] * lt + np.arange(lt)).reshape(-1)
+    tps, tcs = t.params[:, lobes_t], t.c0[:, sample]
+    P = s.params.shape[0]
+    stt = {"student": s.params[:, lobes_s].astype(np.float64), "m": np.zeros((P, len(lobes_s))),
+           "v": np.zeros((P, len(lobes_s))), "c0": s.c0[:, sample].astype(np.float64),
+           "c0_m": np.zeros((3, len(sample))), "c0_v": np.zeros((3, len(sample)))}
+    for step in range(1, steps + 1):
+        new, _ = oad.fit_step(stt["student"], stt["m"], stt["v"], stt["c0"], stt["c0_m"], stt["c0_v"], tps, tcs,
+                              inputs.fit_directions(step, 1005), ls, lt, step)
+        stt = new
+    # final MSE of the sample, evaluated by the oracle for both final states
+    dirs = inputs.fit_directions(steps + 1, 1005)
+    target = oad.field_colours(tps, tcs, dirs, lt)
+    gpu_p = st.master.cpu().numpy()[:, lobes_s].astype(np.float64)
+    gpu_c = st.c0_master.cpu().numpy()[:, sample].astype(np.float64)
+    mse_gpu = np.mean((oad.field_colours(oad.bf16_round(gpu_p), oad.bf16_round(gpu_c), dirs, ls) - target) ** 2)
+    mse_ref = np.mean((oad.field_colours(oad.bf16_round(stt["student"]), oad.bf16_round(stt["c0"]), dirs, ls)
+                       - target) ** 2)
+    start = np.mean((oad.field_colours(oad.bf16_round(s.params[:, lobes_s]), oad.bf16_round(s.c0[:, sample]), dirs, ls)
+                     - target) ** 2)
+    assert mse_ref < 0.9 * start  # the fit makes progress
+    assert abs(mse_gpu - mse_ref) <= 0.01 * mse_ref, (mse_gpu, mse_ref, start)
