@@ -400,6 +400,7 @@ def main():
         del w
         paths["scene_step"] = measure_scene_step(nb, inputs, dev, stream, peak)
         paths["batched"] = measure_batched(nb, inputs, dev, stream, peak)
+        paths["fit"] = measure_fit(nb, inputs, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -582,6 +583,36 @@ def measure_batched(nb, inputs, dev, stream, peak, n_scenes=32, seed=1004, reps=
             "total_primitives": int(sum(n for n, _ in sizes)), "total_lobes": b.total_lobes, "us": us,
             "value": b.total_lobes / (us * 1e-6), "unit": UNIT, "tuning": tune, "alg_bytes": alg, "gbs": gbs,
             "frac": gbs / peak}
+
+
+def measure_fit(nb, inputs, dev, stream, n=2_000_000, ls=16, lt=4, steps=200, n_dirs=64, seed=1005):
+    """Fitting loop: a 16-lobe BF16 student (FP32 master, Adam lr 1e-3) fitted to a 4-lobe
+    FP32 teacher field on the same primitives, 64 random view directions per step shared by
+    all primitives, 200 steps of the fused fitting kernel (compute-bound)."""
+    import torch
+    t = inputs.device_point_cloud(n, lt, seed, dev)
+    s = inputs.device_point_cloud(n, ls, seed + 1, dev)
+    st = nb.TrainState(s["params"], s["c0"])
+    dirs = [torch.from_numpy(inputs.fit_directions(k, seed, n_dirs)).to(dev) for k in range(1, steps + 2)]
+    ws = torch.empty(int(nb.lib.nasgabor_fit_workspace_bytes()), device=dev, dtype=torch.uint8)
+    losses = torch.empty(steps, device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        nb.nasgabor_fit_step(st, t["params"], t["c0"], lt, dirs[k], ls, k + 1, loss=losses[k:k + 1], workspace=ws,
+                             stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    l = losses.cpu().numpy()
+    evals = n * n_dirs * (ls + lt) * steps
+    return {"workload": f"fit N={n}, student L={ls} BF16 (FP32 master), teacher L={lt} FP32, {n_dirs} directions/step, "
+                        f"{steps} Adam steps lr 1e-3", "ms_total": ms, "ms_per_step": ms / steps,
+            "loss_first": float(l[0]), "loss_last": float(l[-1]),
+            "lobe_evaluations_per_s": evals / (ms * 1e-3),
+            "note": "compute-bound; the final-MSE agreement with the oracle's replay is checked on a sample in "
+                    "tests/test_gpu_fit.py"}
 
 
 if __name__ == "__main__":
