@@ -297,9 +297,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paths", action="store_true")
+    ap.add_argument("--case", choices=["scene_step", "batched", "fit"], default=None,
+                    help="run only this secondary measurement (at --case-n primitives) and print its JSON")
+    ap.add_argument("--case-n", type=int, default=None)
+    ap.add_argument("--case-steps", type=int, default=None)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args)
     if args.warmup < 3:
         args.warmup = 3
 
@@ -432,6 +438,30 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+def run_case(args):
+    """One secondary measurement on its own (used for profiling captures of a smaller case)."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2606_09794_gb300 import binding as nb
+    from paper_2606_09794_gb300 import inputs
+    stream = torch.cuda.current_stream(dev)
+    peak, _ = load_peaks()
+    kw = {}
+    if args.case_n:
+        kw["n"] = args.case_n
+    if args.case == "scene_step":
+        res = measure_scene_step(nb, inputs, dev, stream, peak, **kw)
+    elif args.case == "batched":
+        res = measure_batched(nb, inputs, dev, stream, peak, **({"n_scenes": args.case_n} if args.case_n else {}))
+    else:
+        if args.case_steps:
+            kw["steps"] = args.case_steps
+        res = measure_fit(nb, inputs, dev, stream, **kw)
+    print(json.dumps({"case": args.case, **res}))
     return 0
 
 
