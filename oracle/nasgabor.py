@@ -203,21 +203,42 @@ def norm_approx(lam, a):
     return lam * np.sqrt(1.0 + a) / (2.0 * np.pi * (1.0 - np.exp(-2.0 * lam)))
 
 
+def _exp_sinhc(big, k):
+    """e^{-Lambda} sinhc(sqrt(Lambda^2 - k^2)) for real or complex arguments.
+
+    sinhc(s) = sinh(s)/s is an entire function of sigma = s^2 = Lambda^2 - k^2:
+    for sigma > 0 the product is (e^{s - Lambda} - e^{-s - Lambda}) / (2 s) with
+    s - Lambda = -k^2 / (s + Lambda) (the same value; no overflow of sinh at
+    Lambda up to 2e3); for sigma < 0, with t = sqrt(-sigma), it is
+    e^{-Lambda} sin(t)/t; near sigma = 0 its Taylor series in sigma. Each branch is
+    analytic, so the complex-step derivatives below go through it."""
+    big = np.asarray(big)
+    k = np.asarray(k)
+    sigma = (big - k) * (big + k)
+    small = np.abs(sigma) < 1e-3
+    pos = np.real(sigma) > 0
+    one = np.ones_like(sigma)
+    sig_p = np.where(pos & ~small, sigma, one)
+    s = np.sqrt(sig_p)
+    br_pos = (np.exp(-(k * k) / (s + big)) - np.exp(-s - big)) / (2.0 * s)
+    sig_n = np.where(~pos & ~small, -sigma, one)
+    t = np.sqrt(sig_n)
+    br_neg = np.exp(-big) * np.sin(t) / t
+    br_small = np.exp(-big) * (1.0 + sigma * (1.0 / 6.0 + sigma * (1.0 / 120.0 + sigma * (
+        1.0 / 5040.0 + sigma / 362880.0))))
+    return np.where(small, br_small, np.where(pos, br_pos, br_neg))
+
+
 def integral_closed_form(lam, a, k):
     """Sec. 4.1: int G = pi (1 - e^{-2 lam}) / (lam sqrt(1+a)) (1 + Psi),
     Psi = 2 Lambda e^{-Lambda} sinhc(sqrt(Lambda^2 - k^2)) / (1 - e^{-2 Lambda}), Lambda = lam (1+a),
-    sinhc(s) = sinh(s)/s, continued to sin(|s|)/|s| for imaginary s (k > Lambda) and 1 at s = 0."""
+    sinhc(s) = sinh(s)/s, continued to sin(|s|)/|s| for imaginary s (k > Lambda) and 1 at s = 0.
+    The product e^{-Lambda} sinhc is formed without overflow (_exp_sinhc)."""
     lam = np.asarray(lam, dtype=np.float64)
     a = np.asarray(a, dtype=np.float64)
     k = np.asarray(k, dtype=np.float64)
     big = lam * (1.0 + a)
-    disc = big * big - k * k
-    s = np.sqrt(np.abs(disc))
-    with np.errstate(invalid="ignore", divide="ignore"):
-        sinhc = np.where(disc > 0, np.sinh(s) / np.where(s == 0, 1.0, s),
-                         np.where(disc < 0, np.sin(s) / np.where(s == 0, 1.0, s), 1.0))
-    sinhc = np.where(s == 0, 1.0, sinhc)
-    psi = 2.0 * big * np.exp(-big) * sinhc / (1.0 - np.exp(-2.0 * big))
+    psi = 2.0 * big * _exp_sinhc(big, k) / (1.0 - np.exp(-2.0 * big))
     return np.pi * (1.0 - np.exp(-2.0 * lam)) / (lam * np.sqrt(1.0 + a)) * (1.0 + psi)
 
 
@@ -321,11 +342,7 @@ def _exact_norm_partials(lam, a, k):
 
 def _integral_closed_form_complex(lam, a, k):
     big = lam * (1.0 + a)
-    disc = big * big - k * k
-    s = np.sqrt(disc + 0j)
-    s_safe = np.where(np.abs(s) == 0, 1.0, s)
-    sinhc = np.where(np.abs(s) == 0, 1.0, np.sinh(s_safe) / s_safe)
-    psi = 2.0 * big * np.exp(-big) * sinhc / (1.0 - np.exp(-2.0 * big))
+    psi = 2.0 * big * _exp_sinhc(big, k) / (1.0 - np.exp(-2.0 * big))
     return np.pi * (1.0 - np.exp(-2.0 * lam)) / (lam * np.sqrt(1.0 + a)) * (1.0 + psi)
 
 

@@ -149,9 +149,57 @@ def test_closed_form_integral_is_approximate_for_anisotropic_carrier():
     assert 1e-3 < rel < 0.1
 
 
-def test_exact_normalisation_has_unit_mass_where_closed_form_exact():
-    val = integrate_lobe(ng.lobe, 3.0, 0.0, 9.0, ng.NORM_EXACT)
+@pytest.mark.parametrize("lam,k", [(3.0, 9.0), (500.0, 9.0), (800.0, 40.0), (40.0, 40.0)])
+def test_exact_normalisation_has_unit_mass_where_closed_form_exact(lam, k):
+    """a = 0: the exactly normalised lobe integrates to 1, also at lam where
+    sinh(Lambda) overflows FP64 and at k = Lambda."""
+    val = integrate_lobe(ng.lobe, lam, 0.0, k, ng.NORM_EXACT)
     assert abs(val - 1.0) < 1e-9
+
+
+@pytest.mark.parametrize("big", [1e-3, 0.7, 5.0, 300.0, 710.0, 2000.0])
+@pytest.mark.parametrize("k", [0.0, 0.3, 2.0, 8.0, 40.0])
+def test_exp_sinhc_against_arbitrary_precision(big, k):
+    """e^{-Lambda} sinhc(sqrt(Lambda^2 - k^2)) against mpmath at 50 digits, across
+    the sinh / sin / series branches and past FP64's sinh overflow."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    L, K = mpmath.mpf(big), mpmath.mpf(k)
+    sig = L * L - K * K
+    if sig > 0:
+        s = mpmath.sqrt(sig)
+        ref = mpmath.exp(-L) * mpmath.sinh(s) / s
+    elif sig < 0:
+        t = mpmath.sqrt(-sig)
+        ref = mpmath.exp(-L) * mpmath.sin(t) / t
+    else:
+        ref = mpmath.exp(-L)
+    got = float(ng._exp_sinhc(np.float64(big), np.float64(k)))
+    assert abs(got - float(ref)) <= 1e-13 * abs(float(ref)) + 1e-300
+
+
+@pytest.mark.parametrize("lam,a", [(0.05, 0.2), (1.0, 0.5), (700.0, 1.0), (1000.0, 0.0)])
+def test_closed_form_without_carrier_is_the_nasg_mass(lam, a):
+    """k = 0: Psi = 1, so the closed form is the NASG constant's reciprocal
+    2 pi (1 - e^{-2 lam}) / (lam sqrt(1+a)), at every Lambda."""
+    nasg = 2.0 * math.pi * -math.expm1(-2.0 * lam) / (lam * math.sqrt(1.0 + a))
+    assert abs(float(ng.integral_closed_form(lam, a, 0.0)) - nasg) <= 1e-13 * nasg
+
+
+@pytest.mark.parametrize("lam,a,k", [(0.8, 0.3, 1.3), (2.0, 0.5, 3.0), (600.0, 0.7, 6.0), (3.0, 0.0, 3.0),
+                                     (0.4, 0.2, 30.0)])
+def test_exact_normalisation_partials_against_finite_differences(lam, a, k):
+    """Complex-step partials of 1/int G against central differences of the real closed form."""
+    got = ng._exact_norm_partials(np.array(lam), np.array(a), np.array(k))
+    base = (lam, a, k)
+    for j in range(3):
+        h = 1e-6 * max(1.0, abs(base[j]))
+        hi = list(base)
+        lo = list(base)
+        hi[j] += h
+        lo[j] -= h
+        fd = (1.0 / ng.integral_closed_form(*hi) - 1.0 / ng.integral_closed_form(*lo)) / (2.0 * h)
+        assert abs(float(got[j]) - fd) <= 1e-6 * max(abs(fd), 1e-3 * abs(1.0 / ng.integral_closed_form(*base)))
 
 
 # ---------------------------------------------------------------------------
