@@ -64,6 +64,10 @@ typedef int32_t nasg_status;
 
 #define NASG_NORM_APPROX 0  /* C^-1 = lam sqrt(1+a) / (2 pi (1 - e^{-2 lam})) (Sec. 4.1, used for all results) */
 #define NASG_NORM_NONE   1  /* the unnormalised Sec. 4.1 kernel (G(z) = 1)          */
+#define NASG_NORM_EXACT  2  /* 1 / (Sec. 4.1 closed-form integral): the approximate C^-1 times
+                               2 / (1 + Psi), Psi = 2 Lam e^{-Lam} sinhc(sqrt(Lam^2 - k^2)) / (1 - e^{-2 Lam}),
+                               Lam = lam (1+a); the paper's "Exact" variant. The printed integral is
+                               exact for a = 0 or k = 0 and approximate otherwise.               */
 
 #define NASG_ACT_RAW      0 /* stored values are raw; Supp. C activations applied   */
 #define NASG_ACT_IDENTITY 1 /* stored values are the activated quantities           */

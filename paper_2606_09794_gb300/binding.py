@@ -24,7 +24,7 @@ if not os.path.exists(LIB_PATH):
 lib = ctypes.CDLL(LIB_PATH)
 
 FRAME = {"quat": 0, "cos": 1}
-NORM = {"approx": 0, "none": 1}
+NORM = {"approx": 0, "none": 1, "exact": 2}
 ACT = {"raw": 0, "identity": 1}
 PLANES = {"quat": 10, "cos": 9}
 

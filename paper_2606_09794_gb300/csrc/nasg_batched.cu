@@ -49,6 +49,7 @@ struct BatchArgs {
   int32_t dynamic;
   int32_t identity;
   int32_t normalised;
+  int32_t exact;
   int* dev_err;
 };
 
@@ -107,6 +108,7 @@ __device__ __forceinline__ EvalArgs scene_args(const SceneDev& sc, const BatchAr
   a.slice = 1 << sc.slice_log2;
   a.identity = b.identity;
   a.normalised = b.normalised;
+  a.exact = b.exact;
   a.accumulate = 0;
   a.g_rgb = sc.g_rgb;
   a.rgb = sc.rgb;
@@ -194,7 +196,9 @@ extern "C" nasg_status nasgabor_batched_prepare(const nasg_scene* scenes, int32_
   if (!aligned(workspace, 16)) return NASG_ERR_ALIGN;
   if (modes->frame_mode != NASG_FRAME_QUAT && modes->frame_mode != NASG_FRAME_COS) return NASG_ERR_RANGE;
   if (modes->param_dtype != NASG_DTYPE_F32 && modes->param_dtype != NASG_DTYPE_BF16) return NASG_ERR_RANGE;
-  if (modes->norm_mode != NASG_NORM_APPROX && modes->norm_mode != NASG_NORM_NONE) return NASG_ERR_RANGE;
+  if (modes->norm_mode != NASG_NORM_APPROX && modes->norm_mode != NASG_NORM_NONE &&
+      modes->norm_mode != NASG_NORM_EXACT)
+    return NASG_ERR_RANGE;
   if (modes->act_mode != NASG_ACT_RAW && modes->act_mode != NASG_ACT_IDENTITY) return NASG_ERR_RANGE;
   const int es = elem_size(modes->param_dtype);
   std::vector<SceneDev> tab(n_scenes);
@@ -288,7 +292,8 @@ extern "C" nasg_status nasgabor_batched_run(const nasg_batch_plan* plan, const n
   b.total_tiles = plan->total_tiles;
   b.dynamic = dynamic;
   b.identity = plan->act_mode == NASG_ACT_IDENTITY;
-  b.normalised = plan->norm_mode == NASG_NORM_APPROX;
+  b.normalised = plan->norm_mode != NASG_NORM_NONE;
+  b.exact = plan->norm_mode == NASG_NORM_EXACT;
   b.dev_err = device_error_word();
   if (dynamic && cudaMemsetAsync(b.counter, 0, sizeof(uint32_t), st) != cudaSuccess) return check_launch();
   const bool quat = plan->frame_mode == NASG_FRAME_QUAT;

@@ -5,7 +5,8 @@
 // The lobe (Sec. 4.1 definition, Supp. F factorisation):
 //   u = d.z, v = d.x, kappa = (1+u)/2, tau = a v^2 / (1-u^2), E = kappa^tau,
 //   p = exp(2 lam (E kappa - 1)), h = (1 + cos(k v))/2, G = C^-1 p E h,
-//   C^-1 = lam sqrt(1+a) / (2 pi (1 - e^{-2 lam}))  (Supp. E/F; used for all Sec. 5 results).
+//   C^-1 = lam sqrt(1+a) / (2 pi (1 - e^{-2 lam}))  (Supp. E/F; used for all Sec. 5 results),
+//   or, with exact normalisation, 1 / (the Sec. 4.1 closed-form integral).
 //
 // FP32 formulation (algebraically identical, chosen for conditioning at lam
 // up to 1e3, where 2 lam (E kappa - 1) amplifies any absolute error in 1 - u
@@ -221,8 +222,114 @@ struct LobePartials {
   V G_u, G_v, G_lam, G_a, G_k;  // dG/du, dG/dv, dG/dlam, dG/da, dG/dk
 };
 
+// ---------------------------------------------------------------------------
+// Exact normalisation (Sec. 4.1 closed-form integral)
+// ---------------------------------------------------------------------------
+// 1 / int G = C^-1 R, with C^-1 the approximate constant and R = 2 / (1 + Psi):
+//   Psi = 2 Lam e^{-Lam} S(sig) / (1 - e^{-2 Lam}),  Lam = lam (1 + a),  sig = Lam^2 - k^2,
+//   S(sig) = sinh(sqrt sig)/sqrt sig, continued to sin(t)/t for sig = -t^2 (S is entire in sig).
+// e^{-Lam} S and e^{-Lam} S' (S' = dS/dsig) are formed without overflow (Lam reaches 2e3):
+//   |sig| <= 1: e^{-Lam} times the Taylor series of S and S' in sig (to sig^5);
+//   sig > 1:    s = sqrt sig, A = e^{s - Lam} = e^{-k^2/(s + Lam)}, B = e^{-s - Lam},
+//               e^{-Lam} S = (A - B)/(2 s),  e^{-Lam} S' = (s (A + B) - (A - B))/(4 s^3);
+//   sig < -1:   t = sqrt(-sig) (t < k <= 40),  e^{-Lam} S = e^{-Lam} sin t / t,
+//               e^{-Lam} S' = e^{-Lam} (sin t - t cos t)/(2 t^3).
+// Psi > -0.22 everywhere (Lam e^{-Lam} / (1 - e^{-2 Lam}) <= 1/2 and sin t / t >= -0.22).
+// Derivatives: d ln R = -(R/2) dPsi with
+//   dPsi/dk   = -2 k c e^{-Lam} S',  c = 2 Lam / (1 - e^{-2 Lam}),
+//   dPsi/dLam = Psi (1/Lam - coth Lam) + 2 Lam c e^{-Lam} S',
+// where for sig > 1 the second form is rearranged so that no two large terms cancel
+// (they do when Lam >> k, where dPsi/dLam ~ k^2 / (2 Lam^2)):
+//   dPsi/dLam = -Psi (k^2 / (Lam s^2) + 2 e^{-2 Lam}/(1 - e^{-2 Lam}))
+//               + Lam (A k^2 / (s + Lam) + B (s + Lam)) / (s^2 (1 - e^{-2 Lam})),
+// and 1/Lam - coth Lam = -(Lam/3 - Lam^3/45 + 2 Lam^5/945 - Lam^7/4725 + 2 Lam^9/93555)
+// below Lam = 1/2. dLam/dlam = 1 + a, dLam/da = lam.
+template <bool GRAD>
+__device__ __forceinline__ void exact_norm1(float lam, float a, float k, float& r, float& dl, float& da,
+                                            float& dk) {
+  const float opa = 1.f + a;
+  const float L = lam * opa;
+  const float sig = (L - k) * (L + k);
+  const float om = -vexpm1n(-2.f * L);  // 1 - e^{-2 Lam}
+  const float rom = rcpa(om);
+  const float c = 2.f * L * rom;
+  float es, esp, dpsi_dl = 0.f;
+  bool rearranged = false;
+  float s = 0.f, A = 0.f, B = 0.f, rs2 = 0.f;
+  if (fabsf(sig) <= 1.f) {
+    const float el = vexp(-L);
+    float S = fmaf(sig, 1.f / 39916800.f, 1.f / 362880.f);
+    S = fmaf(S, sig, 1.f / 5040.f);
+    S = fmaf(S, sig, 1.f / 120.f);
+    S = fmaf(S, sig, 1.f / 6.f);
+    S = fmaf(S, sig, 1.f);
+    float Sp = fmaf(sig, 1.f / 1037836800.f, 1.f / 7983360.f);
+    Sp = fmaf(Sp, sig, 1.f / 90720.f);
+    Sp = fmaf(Sp, sig, 1.f / 1680.f);
+    Sp = fmaf(Sp, sig, 1.f / 60.f);
+    Sp = fmaf(Sp, sig, 1.f / 6.f);
+    es = el * S;
+    esp = el * Sp;
+  } else if (sig > 0.f) {
+    const float rs = rsqa(sig);
+    s = sig * rs;
+    rs2 = rs * rs;
+    A = vexp(-(k * k) * rcpa(s + L));
+    B = vexp(-s - L);
+    es = (A - B) * (0.5f * rs);
+    esp = fmaf(s, A + B, B - A) * (0.25f * rs2 * rs);
+    rearranged = true;
+  } else {
+    const float rt = rsqa(-sig);
+    const float t = -sig * rt;
+    float sn, cs;
+    vsincos<float>(t, sn, cs);
+    const float el = vexp(-L);
+    es = el * sn * rt;
+    esp = el * fmaf(-t, cs, sn) * (0.5f * rt * rt * rt);
+  }
+  const float psi = c * es;
+  r = 2.f * rcpa(1.f + psi);
+  if (GRAD) {
+    if (rearranged) {
+      const float e2 = vexp(-2.f * L);
+      const float kk = k * k;
+      const float pos = L * fmaf(A * kk, rcpa(s + L), B * (s + L)) * rs2 * rom;
+      dpsi_dl = fmaf(-psi, fmaf(kk * rcpa(L), rs2, 2.f * e2 * rom), pos);
+    } else {
+      float lg;  // 1/Lam - coth Lam
+      if (L < 0.5f) {
+        const float x2 = L * L;
+        float q = fmaf(x2, 2.f / 93555.f, -1.f / 4725.f);
+        q = fmaf(q, x2, 2.f / 945.f);
+        q = fmaf(q, x2, -1.f / 45.f);
+        q = fmaf(q, x2, 1.f / 3.f);
+        lg = -L * q;
+      } else {
+        lg = rcpa(L) - fmaf(2.f, rom, -1.f);
+      }
+      dpsi_dl = fmaf(psi, lg, 2.f * L * c * esp);
+    }
+    const float dpsi_dk = -2.f * k * c * esp;
+    const float h = -0.5f * r;
+    dl = h * dpsi_dl * opa;
+    da = h * dpsi_dl * lam;
+    dk = h * dpsi_dk;
+  }
+}
+
+template <bool GRAD>
+__device__ __forceinline__ void exact_norm(float lam, float a, float k, float& r, float& dl, float& da, float& dk) {
+  exact_norm1<GRAD>(lam, a, k, r, dl, da, dk);
+}
+template <bool GRAD>
+__device__ __forceinline__ void exact_norm(P2 lam, P2 a, P2 k, P2& r, P2& dl, P2& da, P2& dk) {
+  exact_norm1<GRAD>(lam.v.x, a.v.x, k.v.x, r.v.x, dl.v.x, da.v.x, dk.v.x);
+  exact_norm1<GRAD>(lam.v.y, a.v.y, k.v.y, r.v.y, dl.v.y, da.v.y, dk.v.y);
+}
+
 template <bool GRAD, class V>
-__device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a, V k, bool normalised,
+__device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a, V k, bool normalised, bool exact,
                                   LobePartials<V>* pd) {
   using M = typename VecTraits<V>::Mask;
   const V u = vfma(d[0], z[0], vfma(d[1], z[1], d[2] * z[2]));
@@ -251,7 +358,7 @@ __device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a
   const V pe = vexp(vfma(2.f * lam, em1, ln_e));                  // p E
   V h, sin_kv;  // (1 + cos(k v))/2 and sin(k v)
   vcarrier(0.5f * k * v, h, sin_kv);
-  V cinv = vconst<V>(1.f), dlnc_dlam = vconst<V>(0.f), dlnc_da = vconst<V>(0.f);
+  V cinv = vconst<V>(1.f), dlnc_dlam = vconst<V>(0.f), dlnc_da = vconst<V>(0.f), dlnc_dk = vconst<V>(0.f);
   if (normalised) {
     const V em = vexpm1n(-2.f * lam);  // e^{-2 lam} - 1 (negative)
     const V r_em = vrcp(em);
@@ -261,6 +368,16 @@ __device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a
       // d ln C^-1/d lam = 1/lam - 2 e^{-2 lam}/(1 - e^{-2 lam}); d ln C^-1/d a = 1/(2 (1+a))
       dlnc_dlam = vfma(2.f * (1.f + em), r_em, vrcp(lam));
       dlnc_da = 0.5f * vrcp(opa);
+    }
+    if (exact) {
+      V r, dr_lam, dr_a, dr_k;
+      exact_norm<GRAD>(lam, a, k, r, dr_lam, dr_a, dr_k);
+      cinv = cinv * r;
+      if (GRAD) {
+        dlnc_dlam = dlnc_dlam + dr_lam;
+        dlnc_da = dlnc_da + dr_a;
+        dlnc_dk = dr_k;
+      }
     }
   }
   // the antipode (G := 0 with zero derivatives) is applied once, through C^-1 p E;
@@ -277,7 +394,7 @@ __device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a
     const V cpe_sin = cpe * sin_kv;                     // C^-1 p E sin(k v)
     pd->G_u = G * vfma(two_lam_ek, dlne_du + inv_opu, dlne_du);
     pd->G_v = vfma(G * (two_lam_ek + 1.f), dlne_dv, -(cpe_sin * (0.5f * k)));
-    pd->G_k = -(cpe_sin * (0.5f * v));
+    pd->G_k = exact ? vfma(G, dlnc_dk, -(cpe_sin * (0.5f * v))) : -(cpe_sin * (0.5f * v));
     pd->G_lam = G * vfma(2.f, em1, dlnc_dlam);
     pd->G_a = G * vfma((two_lam_ek + 1.f) * ln_k, v * v * inv_s2, dlnc_da);
   }

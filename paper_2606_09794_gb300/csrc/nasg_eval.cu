@@ -16,7 +16,8 @@ static void fill_common(EvalArgs& a, const nasg_desc* desc, const void* params, 
   a.n = desc->n;
   a.n_lobes = desc->n_lobes;
   a.identity = desc->act_mode == NASG_ACT_IDENTITY;
-  a.normalised = desc->norm_mode == NASG_NORM_APPROX;
+  a.normalised = desc->norm_mode != NASG_NORM_NONE;
+  a.exact = desc->norm_mode == NASG_NORM_EXACT;
   a.accumulate = desc->accumulate;
 }
 

@@ -37,7 +37,7 @@ struct FitArgs {
   int64_t n;
   int32_t ls, lt, n_dirs, slice_log2;
   float b1, b2, omb1, omb2, step_size, inv_sqrt_bc2, eps;
-  int32_t quantize, identity, normalised;
+  int32_t quantize, identity, normalised, exact;
   float* partials;  // [gridDim.x] summed squared errors
 };
 
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
         const int j = min(base + tk, s.n_dirs - 1);
         const P2 d[3] = {p2(__ldg(s.dirs + 3 * j)), p2(__ldg(s.dirs + 3 * j + 1)), p2(__ldg(s.dirs + 3 * j + 2))};
         LobePartials<P2> pd;
-        const P2 Gt = lobe<false>(d, tqf.x, tqf.z, tact.lam, tact.a, tact.k, s.normalised != 0, &pd);
+        const P2 Gt = lobe<false>(d, tqf.x, tqf.z, tact.lam, tact.a, tact.k, s.normalised != 0, s.exact != 0, &pd);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const P2 wg = tact.w[c] * Gt;
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
         const float dx = __ldg(s.dirs + 3 * j), dy = __ldg(s.dirs + 3 * j + 1), dz = __ldg(s.dirs + 3 * j + 2);
         const P2 d[3] = {p2(dx), p2(dy), p2(dz)};
         LobePartials<P2> pd;
-        const P2 Gs = lobe<true>(d, qf.x, qf.z, act.lam, act.a, act.k, s.normalised != 0, &pd);
+        const P2 Gs = lobe<true>(d, qf.x, qf.z, act.lam, act.a, act.k, s.normalised != 0, s.exact != 0, &pd);
         float col[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -314,7 +314,8 @@ extern "C" nasg_status nasgabor_fit_step(const nasg_desc* desc, const nasg_train
   a.eps = hp->eps;
   a.quantize = desc->param_dtype == NASG_DTYPE_BF16;
   a.identity = desc->act_mode == NASG_ACT_IDENTITY;
-  a.normalised = desc->norm_mode == NASG_NORM_APPROX;
+  a.normalised = desc->norm_mode != NASG_NORM_NONE;
+  a.exact = desc->norm_mode == NASG_NORM_EXACT;
   a.partials = static_cast<float*>(workspace);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel, kFitBlock, 0) != cudaSuccess || per_sm < 1)

@@ -46,7 +46,8 @@ inline nasg_status check_desc(const nasg_desc* d) {
   if (d->n < 0 || d->n_lobes < 1 || d->n_lobes > NASG_MAX_LOBES) return NASG_ERR_RANGE;
   if (d->frame_mode != NASG_FRAME_QUAT && d->frame_mode != NASG_FRAME_COS) return NASG_ERR_RANGE;
   if (d->param_dtype != NASG_DTYPE_F32 && d->param_dtype != NASG_DTYPE_BF16) return NASG_ERR_RANGE;
-  if (d->norm_mode != NASG_NORM_APPROX && d->norm_mode != NASG_NORM_NONE) return NASG_ERR_RANGE;
+  if (d->norm_mode != NASG_NORM_APPROX && d->norm_mode != NASG_NORM_NONE && d->norm_mode != NASG_NORM_EXACT)
+    return NASG_ERR_RANGE;
   if (d->act_mode != NASG_ACT_RAW && d->act_mode != NASG_ACT_IDENTITY) return NASG_ERR_RANGE;
   if (d->accumulate != 0 && d->accumulate != 1) return NASG_ERR_RANGE;
   // element offsets are 64-bit; keep P*N*L well inside int64

@@ -36,6 +36,7 @@ struct EvalArgs {
   int32_t slice_log2;
   int32_t identity;
   int32_t normalised;
+  int32_t exact;        // exact normalisation (implies normalised)
   int32_t accumulate;
   const float* g_rgb;
   float* rgb;
@@ -56,7 +57,7 @@ struct FrameTraits {
 // and adds dLoss/dd into gd.
 template <int FRAME, bool FWD, bool BWD, class V>
 __device__ __forceinline__ void lobe_step(const V* pv, const V* d, const V* gc, bool identity, bool normalised,
-                                          V* rgb, V* gd, V* gp) {
+                                          bool exact, V* rgb, V* gd, V* gp) {
   constexpr int B = FrameTraits<FRAME>::B;
   Act<V> act;
   activate(pv + B, identity, act);
@@ -73,7 +74,7 @@ __device__ __forceinline__ void lobe_step(const V* pv, const V* d, const V* gc, 
     for (int c = 0; c < 3; ++c) { x[c] = cf.x[c]; z[c] = cf.z[c]; }
   }
   LobePartials<V> pd;
-  const V G = lobe<BWD>(d, x, z, act.lam, act.a, act.k, normalised, &pd);
+  const V G = lobe<BWD>(d, x, z, act.lam, act.a, act.k, normalised, exact, &pd);
   if (FWD) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) rgb[c] = vfma(act.w[c], G, rgb[c]);
@@ -191,7 +192,7 @@ __device__ __forceinline__ P2 unpack(uint32_t w) { return p2(bf16_lo(w), bf16_hi
 
 // Mode flags: FLAGS < 0 reads act_mode / norm_mode / accumulate from the
 // arguments at run time; FLAGS >= 0 fixes them at compile time (bit 0 identity
-// activations, bit 1 unnormalised, bit 2 accumulate) so that the common mode
+// activations, bit 1 unnormalised, bit 2 accumulate, bit 3 exact normalisation) so that the common mode
 // (raw activations, normalised, overwrite: kFlagsDefault) carries no untaken
 // predicated paths.
 constexpr int kFlagsRuntime = -1;
@@ -204,6 +205,9 @@ struct Flags {
   }
   __device__ __forceinline__ static bool normalised(const EvalArgs& a) {
     return FLAGS < 0 ? a.normalised != 0 : (FLAGS & 2) == 0;
+  }
+  __device__ __forceinline__ static bool exact(const EvalArgs& a) {
+    return FLAGS < 0 ? a.exact != 0 : (FLAGS & 8) != 0;
   }
   __device__ __forceinline__ static bool accumulate(const EvalArgs& a) {
     return FLAGS < 0 ? a.accumulate != 0 : (FLAGS & 4) != 0;
@@ -246,8 +250,8 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
       P2 rgbv[3] = {p2(0.f), p2(0.f), p2(0.f)};
       P2 gdv[3] = {p2(0.f), p2(0.f), p2(0.f)};
       P2 gp[P];
-      lobe_step<FRAME, FWD, BWD>(pv, dv, gcv, Flags<FLAGS>::identity(a), Flags<FLAGS>::normalised(a), rgbv, gdv,
-                                 gp);
+      lobe_step<FRAME, FWD, BWD>(pv, dv, gcv, Flags<FLAGS>::identity(a), Flags<FLAGS>::normalised(a),
+                                 Flags<FLAGS>::exact(a), rgbv, gdv, gp);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         rgb[c] = rgbv[c].v.x + (second ? rgbv[c].v.y : 0.f);
@@ -543,7 +547,7 @@ nasg_status launch_tma(const EvalArgs& a, cudaStream_t s) {
 template <int MODE, int FRAME, typename T>
 nasg_status launch_frame_dtype(const EvalArgs& a, bool even, cudaStream_t s) {
   if (tma_eligible<FRAME, T>(a, even)) {
-    const bool dflt = a.identity == 0 && a.normalised != 0 && a.accumulate == 0;
+    const bool dflt = a.identity == 0 && a.normalised != 0 && a.exact == 0 && a.accumulate == 0;
     return dflt ? launch_tma<MODE, FRAME, T, kFlagsDefault>(a, s) : launch_tma<MODE, FRAME, T, kFlagsRuntime>(a, s);
   }
   // 32-bit element offsets when every offset the kernel forms (P*N*L elements,

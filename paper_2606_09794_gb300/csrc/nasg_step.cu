@@ -90,7 +90,7 @@ __device__ __forceinline__ bool step_phase1(const StepArgs& s, const RawItem<flo
       P2 rgbv[3] = {p2(0.f), p2(0.f), p2(0.f)};
       P2 gdv[3] = {p2(0.f), p2(0.f), p2(0.f)};
       P2 gp[P];
-      lobe_step<FRAME, true, true>(pv, dv, gcv, a.identity != 0, a.normalised != 0, rgbv, gdv, gp);
+      lobe_step<FRAME, true, true>(pv, dv, gcv, a.identity != 0, a.normalised != 0, a.exact != 0, rgbv, gdv, gp);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         rgb[c] = rgbv[c].v.x + (second ? rgbv[c].v.y : 0.f);
@@ -393,7 +393,8 @@ extern "C" nasg_status nasgabor_fused_step(const nasg_desc* desc, const nasg_tra
   a.slice_log2 = slice_log2(desc->n_lobes);
   a.slice = 1 << a.slice_log2;
   a.identity = desc->act_mode == NASG_ACT_IDENTITY;
-  a.normalised = desc->norm_mode == NASG_NORM_APPROX;
+  a.normalised = desc->norm_mode != NASG_NORM_NONE;
+  a.exact = desc->norm_mode == NASG_NORM_EXACT;
   a.g_rgb = g_rgb;
   a.rgb = rgb;
   a.g_means = g_means;

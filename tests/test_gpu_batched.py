@@ -26,13 +26,13 @@ def _scenes(sizes, seed, bf16, frame="quat"):
     return out
 
 
-def _compare_with_single(lib, scenes, frame="quat"):
+def _compare_with_single(lib, scenes, frame="quat", norm="approx"):
     import torch
     for sc in scenes:
         if sc["means"].shape[0] == 0:
             continue
         ref = lib.nasgabor_fused_fwd_bwd(sc["params"], sc["c0"], sc["means"], sc["cam"], sc["g_rgb"], sc["n_lobes"],
-                                         frame_mode=frame)
+                                         frame_mode=frame, norm_mode=norm)
         torch.testing.assert_close(sc["rgb"], ref[0], rtol=1e-6, atol=1e-5)
         gp, rp = sc["g_params"].cpu().numpy(), ref[1].cpu().numpy()
         assert max(rel_l2(gp[p], rp[p]) for p in range(gp.shape[0])) < 1e-5
@@ -59,6 +59,13 @@ def test_batched_cos_frames(lib):
     b = lib.Batch(scenes, frame_mode="cos")
     b.run()
     _compare_with_single(lib, scenes, "cos")
+
+
+def test_batched_exact_normalisation(lib):
+    scenes = _scenes([(2000, 8), (333, 3), (1024, 16)], 450, True)
+    b = lib.Batch(scenes, norm_mode="exact")
+    b.run()
+    _compare_with_single(lib, scenes, norm="exact")
 
 
 def test_batched_oracle_parity(lib):

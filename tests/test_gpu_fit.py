@@ -28,8 +28,9 @@ def _setup(lib, n, ls, lt, seed, warm):
     return t, s, st, (m, v, cm, cv)
 
 
-@pytest.mark.parametrize("ls,lt,ndirs", [(16, 4, 64), (8, 4, 13), (4, 2, 7)])
-def test_fit_steps_match_oracle(lib, ls, lt, ndirs):
+@pytest.mark.parametrize("ls,lt,ndirs,norm", [(16, 4, 64, "approx"), (8, 4, 13, "approx"), (4, 2, 7, "approx"),
+                                             (8, 4, 9, "exact")])
+def test_fit_steps_match_oracle(lib, ls, lt, ndirs, norm):
     n = 96
     t, s, st, (m, v, cm, cv) = _setup(lib, n, ls, lt, 41 + ls, warm=True)
     tp, tc = _dev(t.params), _dev(t.c0)
@@ -37,9 +38,9 @@ def test_fit_steps_match_oracle(lib, ls, lt, ndirs):
              "c0": s.c0.astype(np.float64), "c0_m": cm.astype(np.float64), "c0_v": cv.astype(np.float64)}
     for step in range(1, 4):
         dirs = inputs.fit_directions(step, 7, ndirs)
-        loss = lib.nasgabor_fit_step(st, tp, tc, lt, _dev(dirs), ls, step)
+        loss = lib.nasgabor_fit_step(st, tp, tc, lt, _dev(dirs), ls, step, norm_mode=norm)
         new, mse = oad.fit_step(state["student"], state["m"], state["v"], state["c0"], state["c0_m"], state["c0_v"],
-                                t.params, t.c0, dirs, ls, lt, step)
+                                t.params, t.c0, dirs, ls, lt, step, norm_mode=norm)
         assert abs(float(loss.item()) - mse) <= 1e-4 * mse + 1e-9, (float(loss.item()), mse)
         got = st.master.cpu().numpy().astype(np.float64)
         for p in range(10):

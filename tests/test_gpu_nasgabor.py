@@ -84,7 +84,31 @@ CASES = [
     ("quat", 4096, 8, True, "approx", "raw", 15),
     ("cos", 999, 4, True, "approx", "raw", 16),
     ("quat", 333, 3, True, "approx", "raw", 17),
+    ("quat", 1037, 8, False, "exact", "raw", 18),     # Sec. 4.1 exact normalisation
+    ("cos", 555, 5, False, "exact", "raw", 19),
+    ("quat", 513, 4, False, "exact", "identity", 20),
+    ("quat", 4096, 8, True, "exact", "raw", 22),       # staged path, run-time flags
 ]
+
+
+def _exact_branch_workload():
+    """Identity-mode lobes whose (lam, a, k) cover every branch of the exact
+    normalisation: Lam = lam (1 + a) equal to k, |Lam^2 - k^2| on both sides of 1,
+    Lam << k (sin branch), Lam >> k up to 2e3 (rearranged derivative), tiny Lam."""
+    lam = [0.05, 0.3, 1.0, 2.0, 3.0, 3.0, 7.9, 8.0, 12.0, 30.0, 100.0, 1000.0, 1000.0, 0.45, 20.0, 39.0]
+    a = [0.0, 0.2, 0.5, 0.0, 0.0, 1.0, 0.01, 0.0, 0.5, 0.3, 1.0, 1.0, 0.0, 0.1, 1.0, 0.0]
+    k = [0.1, 30.0, 1.5, 2.1, 3.0, 5.9, 8.0, 8.2, 0.0, 40.0, 8.0, 40.0, 0.5, 0.4, 39.9, 39.0]
+    n, L = 3 * len(lam), 2                       # every triple appears in 6 lobes
+    w = inputs.point_cloud_workload(n, L, 23, "quat", activated=True)
+    for row, vals in ((4, lam), (5, a), (6, k)):
+        w.params[row] = np.tile(np.asarray(vals, dtype=np.float32), n * L // len(lam))
+    return w
+
+
+def test_exact_normalisation_branches(lib):
+    w = _exact_branch_workload()
+    _check_forward(lib, w, False, "exact", "identity")
+    _check_backward(lib, w, False, "exact", "identity")
 
 
 @pytest.mark.parametrize("frame,n,L,bf16,norm,act,seed", CASES)

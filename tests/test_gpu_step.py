@@ -80,8 +80,9 @@ def _state(lib, w_params, c0, seed, warm):
                 c0.astype(np.float64), cm.astype(np.float64), cv.astype(np.float64))
 
 
-@pytest.mark.parametrize("L,frame,n", [(8, "quat", 3000), (5, "quat", 1001), (4, "cos", 2000)])
-def test_fused_step_matches_oracle(lib, L, frame, n):
+@pytest.mark.parametrize("L,frame,n,norm", [(8, "quat", 3000, "approx"), (5, "quat", 1001, "approx"),
+                                            (4, "cos", 2000, "approx"), (6, "quat", 1500, "exact")])
+def test_fused_step_matches_oracle(lib, L, frame, n, norm):
     import torch
     sc = inputs.shell_scene(n, L, 90 + L, frame_mode=frame, fov_sample=n)
     cam = sc.cameras[1]
@@ -91,12 +92,12 @@ def test_fused_step_matches_oracle(lib, L, frame, n):
     rgb = torch.full((n, 3), -3.0, device="cuda")
     t = 7
     lib.nasgabor_fused_step(st, _dev(sc.means), cam.center, _dev(g), L, t, lr=1e-3, idx=idx_full,
-                            n_idx_device=nv, frame_mode=frame, rgb=rgb)
+                            n_idx_device=nv, frame_mode=frame, norm_mode=norm, rgb=rgb)
     lib.nasg_device_status()
     vis = idx_full[:int(nv.item())].cpu().numpy()
     _check_visibility(vis, sc.means, cam)
     out = oad.fused_step(p0, m0, v0, c00, cm0, cv0, sc.means, cam.center, g, vis, L, t, lr=1e-3,
-                         frame_mode=frame)
+                         frame_mode=frame, norm_mode=norm)
     master = st.master.cpu().numpy().astype(np.float64)
     P = master.shape[0]
     lobes = (vis[:, None] * L + np.arange(L)).reshape(-1)
@@ -118,7 +119,7 @@ def test_fused_step_matches_oracle(lib, L, frame, n):
     cq = inputs.quantize_bf16(sc.c0[:, vis])
 
     def fwd(p_, c_, m_, cam_):
-        return ong.forward(p_, c_, m_, cam_, L, frame)
+        return ong.forward(p_, c_, m_, cam_, L, frame, norm)
 
     ref, nu = sensitivity_floor(fwd, (pq, cq, sc.means[vis], cam.center), (0, 1, 2, 3))
     rep = colour_report(rgb.cpu().numpy()[vis], ref, nu, 4e-3)
