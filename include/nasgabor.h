@@ -3,13 +3,13 @@
  *
  * The library evaluates, for every primitive i, the view-dependent colour of
  * the appearance model of "Beyond Spherical Harmonics" (arXiv 2606.09794,
- * Sec. 3.2, eq:app_model)
+ * Sec. 4.2, eq:app_model)
  *
  *     f_C(d_i) = c0_i + sum_{l=1..L} w_il G(d_i; [x_il, y_il, z_il], lam_il, a_il, k_il)
  *
- * with G the Normalized Anisotropic Spherical Gabor lobe (Sec. 4.1 definition,
+ * with G the Normalized Anisotropic Spherical Gabor lobe (Sec. 5.1 definition,
  * normalised by the approximate constant of Supp. E/F), at the central-ray
- * direction d_i = (mu_i - cam)/|mu_i - cam| (Sec. 4.2: one evaluation per
+ * direction d_i = (mu_i - cam)/|mu_i - cam| (Sec. 5.2: one evaluation per
  * primitive per frame), plus the matching backward pass (Supp. F derivatives,
  * chained through the Supp. C activations) and the comparison real-SH model
  * (Sec. 3.2, Spherical Harmonics).
@@ -62,9 +62,9 @@ typedef int32_t nasg_status;
 #define NASG_DTYPE_F32  0   /* parameters stored as float32                         */
 #define NASG_DTYPE_BF16 1   /* parameters stored as bfloat16 (math stays float32)   */
 
-#define NASG_NORM_APPROX 0  /* C^-1 = lam sqrt(1+a) / (2 pi (1 - e^{-2 lam})) (Sec. 4.1, used for all results) */
-#define NASG_NORM_NONE   1  /* the unnormalised Sec. 4.1 kernel (G(z) = 1)          */
-#define NASG_NORM_EXACT  2  /* 1 / (Sec. 4.1 closed-form integral): the approximate C^-1 times
+#define NASG_NORM_APPROX 0  /* C^-1 = lam sqrt(1+a) / (2 pi (1 - e^{-2 lam})) (Sec. 5.1, used for all results) */
+#define NASG_NORM_NONE   1  /* the unnormalised Sec. 5.1 kernel (G(z) = 1)          */
+#define NASG_NORM_EXACT  2  /* 1 / (Sec. 5.1 closed-form integral): the approximate C^-1 times
                                2 / (1 + Psi), Psi = 2 Lam e^{-Lam} sinhc(sqrt(Lam^2 - k^2)) / (1 - e^{-2 Lam}),
                                Lam = lam (1+a); the paper's "Exact" variant. The printed integral is
                                exact for a = 0 or k = 0 and approximate otherwise.               */
@@ -106,7 +106,7 @@ nasg_status nasg_device_status(void* stream);
 int32_t nasg_abi_version(void);
 
 /*
- * Forward pass (eq:app_model with the Sec. 4.1 / Supp. F lobe):
+ * Forward pass (eq:app_model with the Sec. 5.1 / Supp. F lobe):
  *   rgb[i][c] = c0[c][i] + sum_l w_il[c] G_il(d_i),  d_i = normalize(means[i] - cam).
  *
  * params  device, [P][N*L] of desc->param_dtype (f32 or bf16)
@@ -196,7 +196,7 @@ size_t nasg_frustum_workspace_bytes(int64_t n);
 
 /*
  * Ordered list of the primitives whose centre lies in a pinhole frustum (the
- * primitives a frame sees, Sec. 4.2): with p = R (mu - center), visible iff
+ * primitives a frame sees, Sec. 5.2): with p = R (mu - center), visible iff
  * p_z > near_z, |p_x| <= t p_z and |p_y| <= t p_z, t = tan_half_fov.
  *   rot      HOST 9 f32, row-major world->camera rotation (rows right, up, forward)
  *   center   HOST 3 f32
@@ -360,6 +360,35 @@ nasg_status sh_eval_bwd(int32_t degree, int64_t n, const float* coeffs, const fl
  * x, y, y2 device [n] f32. Errors: NASG_ERR_RANGE (fn or n), NASG_ERR_NULL.
  */
 nasg_status nasg_math_probe(int32_t fn, const float* x, float* y, float* y2, int64_t n, void* stream);
+
+/* ------------------------------------------------------------------------- */
+/* Learning-rate rules (host side, no device work)                            */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Camera-spacing learning-rate heuristic (Sec. 4.2). d_knn = mean over the
+ * cameras of the mean Euclidean distance from the camera centre to its k nearest
+ * other centres (all others when n_cams - 1 < k); then
+ *   *eta_f     = eta_f_base     * (d_ref / d_knn)^beta    (spherical / feature parameters)
+ *   *eta_sigma = eta_sigma_base * (d_knn / d_ref)^gamma   (kernel opacities).
+ * The paper uses k = 3, beta = 2, gamma = 0.6 and, as d_ref, the same spacing of a
+ * reference capture (a dataset constant supplied by the caller).
+ * centres: HOST [n_cams][3] f32, read only. d_knn: nullable output.
+ * Errors: NASG_ERR_NULL; NASG_ERR_RANGE for n_cams < 2, k < 1, d_ref not a
+ * positive finite number, or all cameras at one point. O(n_cams^2) work.
+ */
+nasg_status nasg_lr_heuristic(const float* centres, int32_t n_cams, int32_t k, double d_ref, double eta_f_base,
+                              double eta_sigma_base, double beta, double gamma, double* eta_f, double* eta_sigma,
+                              double* d_knn);
+
+/*
+ * Cosine learning-rate factor (Supp. C, LR scheduling): 1 before t_start, then
+ * (1 + cos(pi s / S)) / 2 with s = t - t_start and S = t_max - t_start, and 0 from
+ * s >= S on (also when S <= 0). The factor multiplies the base rates of the
+ * appearance parameters from the start of the schedule (the paper starts it once
+ * the model has largely converged). Never fails.
+ */
+double nasg_cosine_lr_factor(int64_t t, int64_t t_start, int64_t t_max);
 
 /*
  * Diagnostic: launches one block that waits, with an iteration limit of

@@ -6,13 +6,14 @@ plain restatement of the paper's definitions in float64 numpy and shares no
 code with the CUDA library (``paper_2606_09794_gb300``), which never imports it.
 
 Modules:
-  nasgabor  -- NASGabor lobe, appearance model forward/backward (Sec. 3.2, 4.1, Supp. C/E/F)
+  nasgabor  -- NASGabor lobe, appearance model forward/backward (Sec. 4.2, 5.1, Supp. C/E/F)
   sh        -- real spherical harmonics forward/backward (Sec. 3.2)
   adam      -- Adam update, fused BF16 step and the teacher/student fitting step
   frustum   -- pinhole visibility of primitive centres
+  schedule  -- the camera k-NN learning-rate heuristic and the cosine LR schedule
 
 Parity pins: every function here is checked in ``tests/test_oracle_*.py``
 against closed forms, special cases that reduce to textbook or library
 routines, invariances and central finite differences.
 """
-from . import adam, frustum, nasgabor, sh  # noqa: F401
+from . import adam, frustum, nasgabor, schedule, sh  # noqa: F401

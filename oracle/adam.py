@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY: used by tests, the smoke check and the benchmark's
 CPU-baseline leg; never by the product path. Shares no code with the CUDA path.
 
 The paper builds on gsplat and says nothing of its optimiser beyond the
-learning-rate heuristic (Sec. 3.2) and the cosine schedule (Supp. C); the
+learning-rate heuristic (Sec. 4.2) and the cosine schedule (Supp. C); the
 fused step follows Adam (Kingma & Ba) with bias correction, in the operation
 order of torch.optim.Adam:
     m <- b1 m + (1 - b1) g ;  v <- b2 v + (1 - b2) g^2

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU-baseline leg of the benchmark).
 
 The paper renders with a pinhole camera and evaluates the appearance model for
-the primitives a frame sees (Sec. 4.2: one evaluation per primitive per frame).
+the primitives a frame sees (Sec. 5.2: one evaluation per primitive per frame).
 A primitive is visible when its centre lies in the symmetric frustum of the
 camera: with p = R (mu - c) in camera coordinates (rows of R: right, up,
 forward), p_z > near and |p_x| <= t p_z and |p_y| <= t p_z, t = tan(fov/2).

@@ -10,23 +10,23 @@ inputs the GPU sees, step by step in the paper's notation, vectorised over
 primitives and lobes with numpy (no blocking, fusion or reordering).
 
 Sources (arXiv 2606.09794, "Beyond Spherical Harmonics"):
-  * appearance model  f_C(d) = c0 + sum_l w_l G_l(d)            -- Sec. 3.2, eq:app_model
-  * NASGabor kernel G, kappa, tau                               -- Sec. 4.1 (definition)
+  * appearance model  f_C(d) = c0 + sum_l w_l G_l(d)            -- Sec. 4.2, eq:app_model
+  * NASGabor kernel G, kappa, tau                               -- Sec. 5.1 (definition)
   * approximate normalisation C^-1 = lam sqrt(1+a) / (2 pi (1-e^{-2 lam}))
                                                                 -- Supp. E/F, used by all
-                                                                   Sec. 5 results (Sec. 4.1)
-  * closed-form integral (1 + Psi) and Lambda = lam (1 + a)     -- Sec. 4.1 (integral)
+                                                                   Sec. 6 results (Sec. 5.1)
+  * closed-form integral (1 + Psi) and Lambda = lam (1 + a)     -- Sec. 5.1 (integral)
   * activations (tanh, exp, exp, 20 (tanh + 1), tanh)           -- Supp. C, activation table
   * frame from cosines (z, x; y = z x x)                        -- Supp. C, parameterisation
   * derivatives wrt a, lam, x, z, k                             -- Supp. F
   * derivatives of the frame wrt the cosines                    -- Supp. E (auxiliary)
   * central-ray evaluation: one colour per primitive, at d = normalize(mu - cam)
-                                                                -- Sec. 4.2 (impl. details)
+                                                                -- Sec. 5.2 (impl. details)
 
 Readings where the paper is silent, ambiguous or mistaken (each one is also
 listed with its reason in the design notes):
   R1  normalised kernel: G = C^-1 p E h (Supp. F); norm_mode "none" drops C^-1
-      (the Sec. 4.1 display). At d = z the normalised value is the limit C^-1.
+      (the Sec. 5.1 display). At d = z the normalised value is the limit C^-1.
   R2  poles: where 1 - u^2 == 0 (u = d.z) in working precision, u > 0 takes
       tau := 0 (and zero derivatives of tau), giving G = C^-1 h(v); u < 0 gives
       G := 0 with all derivatives 0.
@@ -64,7 +64,7 @@ def lobe_planes(frame_mode: str) -> int:
 
 
 # ---------------------------------------------------------------------------
-# View direction (Sec. 4.2: one evaluation per primitive along the central ray)
+# View direction (Sec. 5.2: one evaluation per primitive along the central ray)
 # ---------------------------------------------------------------------------
 
 def view_directions(means, cam):
@@ -195,7 +195,7 @@ def _cos_frame_partials(c):
 
 
 # ---------------------------------------------------------------------------
-# The lobe (Sec. 4.1 definition; Supp. F factorisation G = C^-1 p E h)
+# The lobe (Sec. 5.1 definition; Supp. F factorisation G = C^-1 p E h)
 # ---------------------------------------------------------------------------
 
 def norm_approx(lam, a):
@@ -230,7 +230,7 @@ def _exp_sinhc(big, k):
 
 
 def integral_closed_form(lam, a, k):
-    """Sec. 4.1: int G = pi (1 - e^{-2 lam}) / (lam sqrt(1+a)) (1 + Psi),
+    """Sec. 5.1: int G = pi (1 - e^{-2 lam}) / (lam sqrt(1+a)) (1 + Psi),
     Psi = 2 Lambda e^{-Lambda} sinhc(sqrt(Lambda^2 - k^2)) / (1 - e^{-2 Lambda}), Lambda = lam (1+a),
     sinhc(s) = sinh(s)/s, continued to sin(|s|)/|s| for imaginary s (k > Lambda) and 1 at s = 0.
     The product e^{-Lambda} sinhc is formed without overflow (_exp_sinhc)."""
@@ -323,7 +323,7 @@ def lobe(d, x, z, lam, a, k, norm_mode=NORM_APPROX, need_grad=False):
 
 
 def _exact_norm_partials(lam, a, k):
-    """Partials of 1/int G (Sec. 4.1 closed form) wrt lam, a, k by the complex-step method.
+    """Partials of 1/int G (Sec. 5.1 closed form) wrt lam, a, k by the complex-step method.
 
     The complex step evaluates the closed form at (value + i h) and reads the
     derivative from the imaginary part; it has no subtractive cancellation, so

@@ -102,6 +102,9 @@ _decl("nasgabor_batched_autotune", [_P(NasgScene), _i32, _P(NasgBatchModes), _vp
                                     _P(NasgBatchPlan), _P(NasgBatchTuning), _P(ctypes.c_float), _vp])
 _decl("nasg_frustum_compact_noalloc", [_i64, _vp, _P(ctypes.c_float), _P(ctypes.c_float), ctypes.c_float,
                                        ctypes.c_float, _vp, _vp, _vp])
+_decl("nasg_lr_heuristic", [_vp, _i32, _i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                           ctypes.c_double, _P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)])
+_decl("nasg_cosine_lr_factor", [_i64, _i64, _i64], ctypes.c_double)
 _decl("nasg_frustum_compact", [_i64, _vp, _P(ctypes.c_float), _P(ctypes.c_float), ctypes.c_float, ctypes.c_float,
                                _vp, _vp, _vp, ctypes.c_size_t, _vp])
 
@@ -166,6 +169,22 @@ def make_desc(n, n_lobes, frame_mode="quat", param_dtype=torch.float32, norm_mod
 def nasg_device_status(stream=None):
     """Synchronise the stream and raise NasgError if a kernel's bounded wait gave up."""
     _check(lib.nasg_device_status(_stream(stream)), "nasg_device_status")
+
+
+def nasg_lr_heuristic(centres, d_ref, eta_f_base, eta_sigma_base, k=3, beta=2.0, gamma=0.6):
+    """(eta_f, eta_sigma, d_knn) of the camera-spacing learning-rate heuristic; centres: host [n][3]."""
+    import numpy as np
+    c = np.ascontiguousarray(np.asarray(centres, dtype=np.float32).reshape(-1, 3))
+    ef, es, dk = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib.nasg_lr_heuristic(_vp(c.ctypes.data), int(c.shape[0]), int(k), float(d_ref), float(eta_f_base),
+                                 float(eta_sigma_base), float(beta), float(gamma), ctypes.byref(ef),
+                                 ctypes.byref(es), ctypes.byref(dk)), "nasg_lr_heuristic")
+    return ef.value, es.value, dk.value
+
+
+def nasg_cosine_lr_factor(t, t_max, t_start=0):
+    """Cosine learning-rate multiplier at iteration t (1 before t_start)."""
+    return lib.nasg_cosine_lr_factor(int(t), int(t_start), int(t_max))
 
 
 def nasg_probe_wait_timeout(limit=1024, stream=None):

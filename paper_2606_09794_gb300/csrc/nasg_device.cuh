@@ -2,11 +2,11 @@
 // NASGabor kernel of the library. FP32, generic over the value type V (one
 // lobe as float, or two lobes packed as P2, see nasg_vec.cuh).
 //
-// The lobe (Sec. 4.1 definition, Supp. F factorisation):
+// The lobe (Sec. 5.1 definition, Supp. F factorisation):
 //   u = d.z, v = d.x, kappa = (1+u)/2, tau = a v^2 / (1-u^2), E = kappa^tau,
 //   p = exp(2 lam (E kappa - 1)), h = (1 + cos(k v))/2, G = C^-1 p E h,
-//   C^-1 = lam sqrt(1+a) / (2 pi (1 - e^{-2 lam}))  (Supp. E/F; used for all Sec. 5 results),
-//   or, with exact normalisation, 1 / (the Sec. 4.1 closed-form integral).
+//   C^-1 = lam sqrt(1+a) / (2 pi (1 - e^{-2 lam}))  (Supp. E/F; used for all Sec. 6 results),
+//   or, with exact normalisation, 1 / (the Sec. 5.1 closed-form integral).
 //
 // FP32 formulation (algebraically identical, chosen for conditioning at lam
 // up to 1e3, where 2 lam (E kappa - 1) amplifies any absolute error in 1 - u
@@ -223,7 +223,7 @@ struct LobePartials {
 };
 
 // ---------------------------------------------------------------------------
-// Exact normalisation (Sec. 4.1 closed-form integral)
+// Exact normalisation (Sec. 5.1 closed-form integral)
 // ---------------------------------------------------------------------------
 // 1 / int G = C^-1 R, with C^-1 the approximate constant and R = 2 / (1 + Psi):
 //   Psi = 2 Lam e^{-Lam} S(sig) / (1 - e^{-2 Lam}),  Lam = lam (1 + a),  sig = Lam^2 - k^2,

@@ -2,7 +2,7 @@
 // (nasgabor_fit_step): for D view directions shared by all primitives, the
 // per-primitive loss is the mean over (direction, channel) of the squared
 // difference between the student's and the teacher's colour (eq:app_model,
-// both with the Sec. 4.1 / Supp. E-F lobe); its gradient, summed over the
+// both with the Sec. 5.1 / Supp. E-F lobe); its gradient, summed over the
 // directions (Supp. F derivatives), drives one Adam step of every primitive's
 // student parameters (FP32 master, BF16 copy) in the same pass. The summed
 // squared error of the step is reduced per block and then deterministically

@@ -84,7 +84,7 @@ CASES = [
     ("quat", 4096, 8, True, "approx", "raw", 15),
     ("cos", 999, 4, True, "approx", "raw", 16),
     ("quat", 333, 3, True, "approx", "raw", 17),
-    ("quat", 1037, 8, False, "exact", "raw", 18),     # Sec. 4.1 exact normalisation
+    ("quat", 1037, 8, False, "exact", "raw", 18),     # Sec. 5.1 exact normalisation
     ("cos", 555, 5, False, "exact", "raw", 19),
     ("quat", 513, 4, False, "exact", "identity", 20),
     ("quat", 4096, 8, True, "exact", "raw", 22),       # staged path, run-time flags

@@ -3,7 +3,7 @@
 Each test is chosen so that a plausible mistake in the oracle (a dropped term,
 a wrong sign or index, a transposed operand) fails at least one of them:
   * special cases that reduce to textbook / library functions (SG, von Mises-Fisher),
-  * the Sec. 4.1 closed-form integral where it is exact, by quadrature,
+  * the Sec. 5.1 closed-form integral where it is exact, by quadrature,
   * the unit mass of the approximately normalised kernel at k = 0,
   * the special values at d = +-z,
   * invariance under a joint rotation and under x -> -x (evenness in d.x),
@@ -79,7 +79,7 @@ def test_isotropic_with_carrier_is_sg_times_carrier():
 
 
 def test_special_values_at_poles():
-    """Sec. 4.1: G(z) = 1 and G(-z) = 0 for the unnormalised kernel; C^-1 at z when normalised."""
+    """Sec. 5.1: G(z) = 1 and G(-z) = 0 for the unnormalised kernel; C^-1 at z when normalised."""
     n = 50
     _, x, z = _random_frames(n, RNG)
     lam = np.exp(RNG.uniform(0, 6, n))
@@ -90,7 +90,7 @@ def test_special_values_at_poles():
     # (at -z the limit depends on the path: along d.x = 0 it is e^{-2 lam}, not the
     # convention G(-z) = 0, so only the exact antipode is checked below)
     np.testing.assert_allclose(ng.lobe(z, x, z, lam, a, k, ng.NORM_APPROX), ng.norm_approx(lam, a), rtol=1e-12)
-    # exact world-axis frame: the Sec. 4.1 special values hold exactly
+    # exact world-axis frame: the Sec. 5.1 special values hold exactly
     e = np.array([[0.0, 0.0, 1.0]])
     xe = np.array([[1.0, 0.0, 0.0]])
     one = np.ones(1)
@@ -117,7 +117,7 @@ def test_near_pole_is_continuous():
 
 
 # ---------------------------------------------------------------------------
-# Integrals (Sec. 4.1 closed form; NASG normalisation of the distributions table)
+# Integrals (Sec. 5.1 closed form; NASG normalisation of the distributions table)
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("lam,a", [(0.3, 0.0), (1.0, 0.5), (4.0, 1.5), (60.0, 0.9), (900.0, 0.3)])
@@ -132,7 +132,7 @@ def test_approx_normalised_kernel_has_unit_mass_without_carrier(lam, a):
     (1.0, 0.5, 0.0), (3.0, 1.2, 0.0), (200.0, 0.7, 0.0),
 ])
 def test_closed_form_integral_where_exact(lam, a, k):
-    """Sec. 4.1 closed form vs quadrature of the unnormalised kernel, for a = 0 or k = 0.
+    """Sec. 5.1 closed form vs quadrature of the unnormalised kernel, for a = 0 or k = 0.
 
     Covers Lambda > k, Lambda < k (sinhc continued to sin x / x) and Lambda = k."""
     quad = integrate_lobe(ng.lobe, lam, a, k, ng.NORM_NONE)
