@@ -43,6 +43,12 @@ listed with its reason in the design notes):
       dG/dz = (dG/du) d read off the Supp. F vector formulas.
   R9  QUAT frame mode (not in the paper): x and z are the first and third
       columns of the rotation matrix of the normalised quaternion (w, x, y, z).
+  R10 variants: NASG is the lobe with k = 0 (no carrier), SG the lobe with a = 0
+      and k = 0 (the isotropic normalised spherical Gaussian of the distributions
+      table), "phase" the lobe with the carrier (1 + cos(k v + phi))/2 and a
+      per-lobe phase phi stored without activation. Its integral: the envelope
+      is even in v, so the sin(k v) sin(phi) part integrates to zero and the
+      closed form becomes pi (1 - e^{-2 lam}) / (lam sqrt(1+a)) (1 + cos(phi) Psi).
 """
 from __future__ import annotations
 
@@ -59,8 +65,26 @@ ACT_RAW = "raw"
 ACT_IDENTITY = "identity"
 
 
-def lobe_planes(frame_mode: str) -> int:
-    return 10 if frame_mode == FRAME_QUAT else 9
+VAR_NASGABOR = "nasgabor"
+VAR_NASG = "nasg"
+VAR_SG = "sg"
+VAR_PHASE = "phase"
+
+# per-lobe scalars after the frame, in storage order (R10)
+_FIELDS = {
+    VAR_NASGABOR: ("lam", "a", "k", "w0", "w1", "w2"),
+    VAR_NASG: ("lam", "a", "w0", "w1", "w2"),
+    VAR_SG: ("lam", "w0", "w1", "w2"),
+    VAR_PHASE: ("lam", "a", "k", "phi", "w0", "w1", "w2"),
+}
+
+
+def variant_fields(variant: str = VAR_NASGABOR):
+    return _FIELDS[variant]
+
+
+def lobe_planes(frame_mode: str, variant: str = VAR_NASGABOR) -> int:
+    return (4 if frame_mode == FRAME_QUAT else 3) + len(_FIELDS[variant])
 
 
 # ---------------------------------------------------------------------------
@@ -78,17 +102,18 @@ def view_directions(means, cam):
 # Activations (Supp. C, activation table)
 # ---------------------------------------------------------------------------
 
-def split_planes(params, n, n_lobes, frame_mode):
+def split_planes(params, n, n_lobes, frame_mode, variant=VAR_NASGABOR):
     """params [P][N*L] -> float64 array (P, N, L)."""
     p = np.asarray(params, dtype=np.float64)
-    return p.reshape(lobe_planes(frame_mode), n, n_lobes)
+    return p.reshape(lobe_planes(frame_mode, variant), n, n_lobes)
 
 
-def activate(planes, frame_mode, act_mode=ACT_RAW):
+def activate(planes, frame_mode, act_mode=ACT_RAW, variant=VAR_NASGABOR):
     """Map raw planes (P, N, L) to the activated lobe quantities.
 
-    Returns a dict with lam, a, k (N, L), w (N, L, 3), and the frame inputs:
-    QUAT: q (N, L, 4); COS: c (N, L, 3) cosines of theta, phi, tau.
+    Returns a dict with lam, a, k, phi (N, L), w (N, L, 3), and the frame inputs:
+    QUAT: q (N, L, 4); COS: c (N, L, 3) cosines of theta, phi, tau. Quantities a
+    variant does not store are 0 (R10); the carrier phase is stored as is.
     """
     out = {}
     if frame_mode == FRAME_QUAT:
@@ -99,29 +124,35 @@ def activate(planes, frame_mode, act_mode=ACT_RAW):
         out["c_raw"] = frame_raw
         out["c"] = frame_raw if act_mode == ACT_IDENTITY else np.tanh(frame_raw)
         rest = planes[3:]
-    lam_r, a_r, k_r = rest[0], rest[1], rest[2]
-    w_r = np.moveaxis(rest[3:6], 0, -1)
+    f = {name: rest[j] for j, name in enumerate(_FIELDS[variant])}
+    lam_r = f["lam"]
+    zero = np.zeros_like(lam_r)
+    w_r = np.stack([f["w0"], f["w1"], f["w2"]], axis=-1)
     if act_mode == ACT_IDENTITY:
-        out["lam"], out["a"], out["k"], out["w"] = lam_r, a_r, k_r, w_r
+        out["lam"], out["w"] = lam_r, w_r
+        out["a"] = f.get("a", zero)
+        out["k"] = f.get("k", zero)
     else:
         out["lam"] = np.exp(lam_r)
-        out["a"] = np.exp(a_r)
-        out["k"] = 20.0 * (np.tanh(k_r) + 1.0)
+        out["a"] = np.exp(f["a"]) if "a" in f else zero
+        out["k"] = 20.0 * (np.tanh(f["k"]) + 1.0) if "k" in f else zero
         out["w"] = np.tanh(w_r)
-    out["raw"] = {"lam": lam_r, "a": a_r, "k": k_r, "w": w_r}
+    out["phi"] = f.get("phi", zero)
+    out["raw"] = {"lam": lam_r, "a": f.get("a", zero), "k": f.get("k", zero), "w": w_r}
     return out
 
 
 def activation_slopes(act, act_mode):
     """d(activated)/d(raw) for lam, a, k, w (Supp. C activations differentiated)."""
+    one = np.ones_like(act["lam"])
     if act_mode == ACT_IDENTITY:
-        one = np.ones_like(act["lam"])
-        return {"lam": one, "a": one, "k": one, "w": np.ones_like(act["w"])}
+        return {"lam": one, "a": one, "k": one, "phi": one, "w": np.ones_like(act["w"])}
     t = np.tanh(act["raw"]["k"])
     return {
         "lam": act["lam"],                 # d exp(r)/dr
         "a": act["a"],                     # d exp(r)/dr
         "k": 20.0 * (1.0 - t * t),         # d 20 (tanh r + 1)/dr
+        "phi": one,                        # stored as is
         "w": 1.0 - act["w"] ** 2,          # d tanh r/dr
     }
 
@@ -229,25 +260,29 @@ def _exp_sinhc(big, k):
     return np.where(small, br_small, np.where(pos, br_pos, br_neg))
 
 
-def integral_closed_form(lam, a, k):
+def integral_closed_form(lam, a, k, phi=0.0):
     """Sec. 5.1: int G = pi (1 - e^{-2 lam}) / (lam sqrt(1+a)) (1 + Psi),
     Psi = 2 Lambda e^{-Lambda} sinhc(sqrt(Lambda^2 - k^2)) / (1 - e^{-2 Lambda}), Lambda = lam (1+a),
     sinhc(s) = sinh(s)/s, continued to sin(|s|)/|s| for imaginary s (k > Lambda) and 1 at s = 0.
-    The product e^{-Lambda} sinhc is formed without overflow (_exp_sinhc)."""
+    The product e^{-Lambda} sinhc is formed without overflow (_exp_sinhc). With a
+    carrier phase phi (R10) Psi is multiplied by cos(phi)."""
     lam = np.asarray(lam, dtype=np.float64)
     a = np.asarray(a, dtype=np.float64)
     k = np.asarray(k, dtype=np.float64)
     big = lam * (1.0 + a)
     psi = 2.0 * big * _exp_sinhc(big, k) / (1.0 - np.exp(-2.0 * big))
-    return np.pi * (1.0 - np.exp(-2.0 * lam)) / (lam * np.sqrt(1.0 + a)) * (1.0 + psi)
+    return np.pi * (1.0 - np.exp(-2.0 * lam)) / (lam * np.sqrt(1.0 + a)) * (1.0 + np.cos(phi) * psi)
 
 
-def lobe(d, x, z, lam, a, k, norm_mode=NORM_APPROX, need_grad=False):
+def lobe(d, x, z, lam, a, k, norm_mode=NORM_APPROX, need_grad=False, phi=None):
     """G(d; [x, y, z], lam, a, k) and, optionally, its Supp. F partials.
 
-    Shapes: d, x, z (..., 3); lam, a, k (...). Returns G, or (G, partials) with
-    partials = dict(x=dG/dx, z=dG/dz, d=dG/dd (vectors), lam, a, k (scalars)).
+    Shapes: d, x, z (..., 3); lam, a, k (...); phi (...) the carrier phase (R10,
+    default 0). Returns G, or (G, partials) with partials = dict(x=dG/dx,
+    z=dG/dz, d=dG/dd (vectors), lam, a, k, phi (scalars)).
     """
+    if phi is None:
+        phi = np.zeros_like(np.asarray(lam, dtype=np.float64))
     u = np.sum(d * z, axis=-1)
     v = np.sum(d * x, axis=-1)
     one_m_u2 = 1.0 - u * u
@@ -259,13 +294,13 @@ def lobe(d, x, z, lam, a, k, norm_mode=NORM_APPROX, need_grad=False):
     ln_kappa = np.log(kappa_safe)
     E = kappa_safe ** tau
     p = np.exp(2.0 * lam * (E * kappa_safe - 1.0))
-    h = (1.0 + np.cos(k * v)) / 2.0
+    h = (1.0 + np.cos(k * v + phi)) / 2.0
     if norm_mode == NORM_NONE:
         cinv = np.ones_like(lam)
     elif norm_mode == NORM_APPROX:
         cinv = norm_approx(lam, a)
     elif norm_mode == NORM_EXACT:
-        cinv = 1.0 / integral_closed_form(lam, a, k)
+        cinv = 1.0 / integral_closed_form(lam, a, k, phi)
     else:
         raise ValueError(norm_mode)
     anti = pole & (u < 0.0)
@@ -285,12 +320,14 @@ def lobe(d, x, z, lam, a, k, norm_mode=NORM_APPROX, need_grad=False):
         dcinv_dlam = (np.sqrt(1.0 + a) * (1.0 - em) - 2.0 * lam * np.sqrt(1.0 + a) * em) / (
             2.0 * np.pi * (1.0 - em) ** 2)
         dcinv_dk = np.zeros_like(lam)
+        dcinv_dphi = np.zeros_like(lam)
     elif norm_mode == NORM_NONE:
         dcinv_da = np.zeros_like(lam)
         dcinv_dlam = np.zeros_like(lam)
         dcinv_dk = np.zeros_like(lam)
+        dcinv_dphi = np.zeros_like(lam)
     else:
-        dcinv_dlam, dcinv_da, dcinv_dk = _exact_norm_partials(lam, a, k)
+        dcinv_dlam, dcinv_da, dcinv_dk, dcinv_dphi = _exact_norm_partials(lam, a, k, phi)
     dG_da = (dp_da * E * cinv + p * dE_da * cinv + p * E * dcinv_da) * h
     # wrt lam
     dp_dlam = 2.0 * p * (E * kappa_safe - 1.0)
@@ -299,7 +336,7 @@ def lobe(d, x, z, lam, a, k, norm_mode=NORM_APPROX, need_grad=False):
     coef_tau_x = np.where(pole, 0.0, 2.0 * a * v / safe)
     coef_E_x = E * ln_kappa * coef_tau_x
     coef_p_x = 2.0 * lam * p * kappa_safe * coef_E_x
-    coef_h_x = -(k / 2.0) * np.sin(k * v)
+    coef_h_x = -(k / 2.0) * np.sin(k * v + phi)
     dG_dv = (coef_p_x * E * cinv + p * coef_E_x * cinv) * h + p * E * cinv * coef_h_x
     # wrt z: dkappa/dz = d/2 ; dtau/dz = a v^2 2u/(1-u^2)^2 d
     coef_kappa_z = 0.5
@@ -308,7 +345,9 @@ def lobe(d, x, z, lam, a, k, norm_mode=NORM_APPROX, need_grad=False):
     coef_p_z = p * 2.0 * lam * (kappa_safe * coef_E_z + E * coef_kappa_z)
     dG_du = (coef_p_z * E * cinv + p * coef_E_z * cinv) * h
     # wrt k
-    dG_dk = p * E * cinv * (-(v / 2.0) * np.sin(k * v)) + p * E * h * dcinv_dk
+    dG_dk = p * E * cinv * (-(v / 2.0) * np.sin(k * v + phi)) + p * E * h * dcinv_dk
+    # wrt the carrier phase (R10)
+    dG_dphi = p * E * cinv * (-0.5 * np.sin(k * v + phi)) + p * E * h * dcinv_dphi
     zero = lambda t: np.where(anti, 0.0, t)  # noqa: E731
     dG_du, dG_dv = zero(dG_du), zero(dG_dv)
     partials = {
@@ -318,12 +357,13 @@ def lobe(d, x, z, lam, a, k, norm_mode=NORM_APPROX, need_grad=False):
         "lam": zero(dG_dlam),
         "a": zero(dG_da),
         "k": zero(dG_dk),
+        "phi": zero(dG_dphi),
     }
     return G, partials
 
 
-def _exact_norm_partials(lam, a, k):
-    """Partials of 1/int G (Sec. 5.1 closed form) wrt lam, a, k by the complex-step method.
+def _exact_norm_partials(lam, a, k, phi=0.0):
+    """Partials of 1/int G (Sec. 5.1 closed form) wrt lam, a, k, phi by the complex-step method.
 
     The complex step evaluates the closed form at (value + i h) and reads the
     derivative from the imaginary part; it has no subtractive cancellation, so
@@ -331,19 +371,19 @@ def _exact_norm_partials(lam, a, k):
     """
     h = 1e-30
     out = []
-    for which in range(3):
+    for which in range(4):
         args = [np.asarray(lam, dtype=np.complex128), np.asarray(a, dtype=np.complex128),
-                np.asarray(k, dtype=np.complex128)]
+                np.asarray(k, dtype=np.complex128), np.asarray(phi, dtype=np.complex128)]
         args[which] = args[which] + 1j * h
         val = _integral_closed_form_complex(*args)
         out.append(np.imag(1.0 / val) / h)
-    return out[0], out[1], out[2]
+    return out[0], out[1], out[2], out[3]
 
 
-def _integral_closed_form_complex(lam, a, k):
+def _integral_closed_form_complex(lam, a, k, phi):
     big = lam * (1.0 + a)
     psi = 2.0 * big * _exp_sinhc(big, k) / (1.0 - np.exp(-2.0 * big))
-    return np.pi * (1.0 - np.exp(-2.0 * lam)) / (lam * np.sqrt(1.0 + a)) * (1.0 + psi)
+    return np.pi * (1.0 - np.exp(-2.0 * lam)) / (lam * np.sqrt(1.0 + a)) * (1.0 + np.cos(phi) * psi)
 
 
 # ---------------------------------------------------------------------------
@@ -357,21 +397,21 @@ def _frames(act, frame_mode):
 
 
 def forward(params, c0, means, cam, n_lobes, frame_mode=FRAME_QUAT, norm_mode=NORM_APPROX,
-            act_mode=ACT_RAW):
+            act_mode=ACT_RAW, variant=VAR_NASGABOR):
     """f_C(d_i) = c0_i + sum_l w_il G_il(d_i) for every primitive (eq:app_model); (N, 3) float64."""
     means = np.asarray(means)
     n = means.shape[0]
-    planes = split_planes(params, n, n_lobes, frame_mode)
-    act = activate(planes, frame_mode, act_mode)
+    planes = split_planes(params, n, n_lobes, frame_mode, variant)
+    act = activate(planes, frame_mode, act_mode, variant)
     d, _ = view_directions(means, cam)
     x, z = _frames(act, frame_mode)
-    G = lobe(d[:, None, :], x, z, act["lam"], act["a"], act["k"], norm_mode)
+    G = lobe(d[:, None, :], x, z, act["lam"], act["a"], act["k"], norm_mode, phi=act["phi"])
     c0 = np.asarray(c0, dtype=np.float64)
     return c0.T + np.sum(act["w"] * G[..., None], axis=1)
 
 
 def backward(params, c0, means, cam, g_rgb, n_lobes, frame_mode=FRAME_QUAT,
-             norm_mode=NORM_APPROX, act_mode=ACT_RAW):
+             norm_mode=NORM_APPROX, act_mode=ACT_RAW, variant=VAR_NASGABOR):
     """Gradients of <g_rgb, f_C> wrt the raw lobe planes, c0 and the means.
 
     Returns (g_params (P, N*L), g_c0 (3, N), g_means (N, 3)), float64.
@@ -379,12 +419,12 @@ def backward(params, c0, means, cam, g_rgb, n_lobes, frame_mode=FRAME_QUAT,
     means = np.asarray(means)
     n = means.shape[0]
     g_rgb = np.asarray(g_rgb, dtype=np.float64)
-    planes = split_planes(params, n, n_lobes, frame_mode)
-    act = activate(planes, frame_mode, act_mode)
+    planes = split_planes(params, n, n_lobes, frame_mode, variant)
+    act = activate(planes, frame_mode, act_mode, variant)
     slope = activation_slopes(act, act_mode)
     d, dist = view_directions(means, cam)
     x, z = _frames(act, frame_mode)
-    G, par = lobe(d[:, None, :], x, z, act["lam"], act["a"], act["k"], norm_mode, need_grad=True)
+    G, par = lobe(d[:, None, :], x, z, act["lam"], act["a"], act["k"], norm_mode, need_grad=True, phi=act["phi"])
 
     g_c = g_rgb[:, None, :]                                    # (N, 1, 3)
     g_w = g_c * G[..., None]                                   # dL/dw_l
@@ -393,6 +433,7 @@ def backward(params, c0, means, cam, g_rgb, n_lobes, frame_mode=FRAME_QUAT,
         "lam": g_G * par["lam"] * slope["lam"],
         "a": g_G * par["a"] * slope["a"],
         "k": g_G * par["k"] * slope["k"],
+        "phi": g_G * par["phi"] * slope["phi"],
         "w": g_w * slope["w"],
     }
     g_x = g_G[..., None] * par["x"]
@@ -416,8 +457,9 @@ def backward(params, c0, means, cam, g_rgb, n_lobes, frame_mode=FRAME_QUAT,
             dxr = px[cn] * np.asarray(dcdr)[..., None] + px[sn] * np.asarray(dsdr)[..., None]
             dzr = pz[cn] * np.asarray(dcdr)[..., None] + pz[sn] * np.asarray(dsdr)[..., None]
             frame_planes.append(np.sum(g_x * dxr, axis=-1) + np.sum(g_z * dzr, axis=-1))
-    out_planes = frame_planes + [grads["lam"], grads["a"], grads["k"],
-                                 grads["w"][..., 0], grads["w"][..., 1], grads["w"][..., 2]]
+    per_field = {"lam": grads["lam"], "a": grads["a"], "k": grads["k"], "phi": grads["phi"],
+                 "w0": grads["w"][..., 0], "w1": grads["w"][..., 1], "w2": grads["w"][..., 2]}
+    out_planes = frame_planes + [per_field[name] for name in _FIELDS[variant]]
     g_params = np.stack([pl.reshape(-1) for pl in out_planes])
     g_c0 = g_rgb.T.copy()
     g_d = np.sum(g_G[..., None] * par["d"], axis=1)            # (N, 3)

@@ -111,6 +111,38 @@ def _draw_lobes(st, count: int, frame_mode: str, k_max: float = 8.0, activated: 
     return np.stack(planes).astype(np.float32), phase.astype(np.float32)
 
 
+# Stored per-lobe scalars after the frame planes, per lobe family: the NASGabor
+# lobe, NASG (no carrier frequency), SG (no anisotropy, no carrier) and the
+# NASGabor lobe with a per-lobe carrier phase.
+VARIANT_FIELDS = {
+    "nasgabor": ("lam", "a", "k", "w0", "w1", "w2"),
+    "nasg": ("lam", "a", "w0", "w1", "w2"),
+    "sg": ("lam", "w0", "w1", "w2"),
+    "phase": ("lam", "a", "k", "phi", "w0", "w1", "w2"),
+}
+
+
+def variant_planes(params: np.ndarray, phase, frame_mode: str, variant: str) -> np.ndarray:
+    """Re-pack NASGabor planes [F + 6][N*L] for a lobe family: keep the frame planes
+    and the family's fields in VARIANT_FIELDS order; the phase plane is `phase`."""
+    f = 4 if frame_mode == FRAME_QUAT else 3
+    src = {"lam": params[f], "a": params[f + 1], "k": params[f + 2], "w0": params[f + 3], "w1": params[f + 4],
+           "w2": params[f + 5]}
+    if variant == "phase":
+        src["phi"] = np.asarray(phase, dtype=params.dtype)
+    rows = [params[j] for j in range(f)] + [src[name] for name in VARIANT_FIELDS[variant]]
+    return np.ascontiguousarray(np.stack(rows))
+
+
+def variant_workload(n: int, n_lobes: int, seed: int, variant: str, frame_mode: str = FRAME_QUAT,
+                     activated: bool = False) -> "Workload":
+    """The point-cloud workload with its lobes stored for `variant` (the phase family
+    stores the workload's phase draws, U[0, 2 pi])."""
+    w = point_cloud_workload(n, n_lobes, seed, frame_mode, activated=activated)
+    w.params = variant_planes(w.params, w.phase, frame_mode, variant)
+    return w
+
+
 def point_cloud_workload(n: int, n_lobes: int, seed: int, frame_mode: str = FRAME_QUAT,
                          with_upstream: bool = True, activated: bool = False) -> Workload:
     """Primitives uniform in the unit cube seen from one camera at (0, 0, 3).

@@ -341,18 +341,22 @@ def _assert_fd(an, fd, where, rtol=2e-6, atol_frac=1e-8):
     assert not bad.any(), (where, an[bad][:4], fd[bad][:4])
 
 
-def _per_prim_loss(params, c0, means, cam, g_rgb, n_lobes, fm, nm, am):
-    return np.sum(g_rgb * ng.forward(params, c0, means, cam, n_lobes, fm, nm, am), axis=-1)
+def _per_prim_loss(params, c0, means, cam, g_rgb, n_lobes, fm, nm, am, var=ng.VAR_NASGABOR):
+    return np.sum(g_rgb * ng.forward(params, c0, means, cam, n_lobes, fm, nm, am, var), axis=-1)
 
 
-@pytest.mark.parametrize("frame_mode", [ng.FRAME_QUAT, ng.FRAME_COS])
+@pytest.mark.parametrize("frame_mode,variant", [(ng.FRAME_QUAT, ng.VAR_NASGABOR), (ng.FRAME_COS, ng.VAR_NASGABOR),
+                                                (ng.FRAME_QUAT, ng.VAR_NASG), (ng.FRAME_QUAT, ng.VAR_SG),
+                                                (ng.FRAME_QUAT, ng.VAR_PHASE), (ng.FRAME_COS, ng.VAR_PHASE)])
 @pytest.mark.parametrize("norm_mode", [ng.NORM_APPROX, ng.NORM_NONE, ng.NORM_EXACT])
 @pytest.mark.parametrize("act_mode", [ng.ACT_RAW, ng.ACT_IDENTITY])
-def test_backward_matches_central_differences(frame_mode, norm_mode, act_mode):
+def test_backward_matches_central_differences(frame_mode, variant, norm_mode, act_mode):
     n, L = 64, 3
     params, c0, means, cam, g_rgb = _fd_case(frame_mode, act_mode, n, L, seed=11)
-    g_p, g_c0, g_mu = ng.backward(params, c0, means, cam, g_rgb, L, frame_mode, norm_mode, act_mode)
-    args = (L, frame_mode, norm_mode, act_mode)
+    phase = np.random.default_rng(5).uniform(0.0, 2.0 * np.pi, n * L)
+    params = inputs.variant_planes(params, phase, frame_mode, variant)
+    g_p, g_c0, g_mu = ng.backward(params, c0, means, cam, g_rgb, L, frame_mode, norm_mode, act_mode, variant)
+    args = (L, frame_mode, norm_mode, act_mode, variant)
     P = params.shape[0]
     for p in range(P):
         for l in range(L):
@@ -415,3 +419,80 @@ def test_sharp_lobe_derivatives():
         pm[p, idx] -= h
         fd = (_per_prim_loss(pp, c0, means, cam, g_rgb, *args) - _per_prim_loss(pm, c0, means, cam, g_rgb, *args)) / (2 * h)
         _assert_fd(g_p[p, idx], fd, p, rtol=1e-5, atol_frac=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# Lobe families (NASG, SG, phase-shifted carrier)
+# ---------------------------------------------------------------------------
+
+def test_sg_family_is_the_von_mises_fisher_density():
+    """SG (a = 0, k = 0) normalised: exactly the von Mises-Fisher density with
+    concentration lam about z (scipy), per lobe through the whole forward."""
+    w = inputs.variant_workload(200, 2, 31, "sg", activated=True)
+    rgb = ng.forward(w.params, w.c0, w.means, w.cam, 2, act_mode=ng.ACT_IDENTITY, variant=ng.VAR_SG)
+    d, _ = ng.view_directions(w.means, w.cam)
+    _, z = ng.frame_from_quat(np.moveaxis(w.params[0:4].reshape(4, 200, 2), 0, -1).astype(np.float64))
+    lam = w.params[4].reshape(200, 2).astype(np.float64)
+    ref = w.c0.T.astype(np.float64).copy()
+    for i in range(200):
+        for j in range(2):
+            dens = vonmises_fisher(z[i, j], lam[i, j]).pdf(d[i])
+            ref[i] += w.params[5:8, 2 * i + j].astype(np.float64) * dens
+    np.testing.assert_allclose(rgb, ref, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("variant", [ng.VAR_NASG, ng.VAR_SG])
+def test_families_equal_nasgabor_with_fixed_parameters(variant):
+    """NASG and SG are the NASGabor lobe at k = 0 (and a = 0): same colours and
+    the same gradients for every stored plane (identity activations)."""
+    n, L = 50, 3
+    w = inputs.point_cloud_workload(n, L, 32, activated=True)
+    full = w.params.astype(np.float64).copy()
+    full[6] = 0.0
+    if variant == ng.VAR_SG:
+        full[5] = 0.0
+    fam = inputs.variant_planes(full, None, "quat", variant)
+    for norm in (ng.NORM_APPROX, ng.NORM_EXACT):
+        a = ng.forward(full, w.c0, w.means, w.cam, L, norm_mode=norm, act_mode=ng.ACT_IDENTITY)
+        b = ng.forward(fam, w.c0, w.means, w.cam, L, norm_mode=norm, act_mode=ng.ACT_IDENTITY, variant=variant)
+        np.testing.assert_allclose(b, a, rtol=1e-13, atol=1e-13)
+        ga = ng.backward(full, w.c0, w.means, w.cam, w.g_rgb, L, norm_mode=norm, act_mode=ng.ACT_IDENTITY)[0]
+        gb = ng.backward(fam, w.c0, w.means, w.cam, w.g_rgb, L, norm_mode=norm, act_mode=ng.ACT_IDENTITY,
+                         variant=variant)[0]
+        keep = [0, 1, 2, 3, 4] + ([5] if variant == ng.VAR_NASG else []) + [7, 8, 9]
+        np.testing.assert_allclose(gb, ga[keep], rtol=1e-10, atol=1e-12)
+
+
+def test_phase_carrier_at_zero_phase_is_nasgabor():
+    n, L = 40, 2
+    w = inputs.point_cloud_workload(n, L, 33)
+    ph = inputs.variant_planes(w.params.astype(np.float64), np.zeros(n * L), "quat", "phase")
+    for norm in (ng.NORM_APPROX, ng.NORM_EXACT, ng.NORM_NONE):
+        np.testing.assert_allclose(ng.forward(ph, w.c0, w.means, w.cam, L, norm_mode=norm, variant=ng.VAR_PHASE),
+                                   ng.forward(w.params, w.c0, w.means, w.cam, L, norm_mode=norm),
+                                   rtol=1e-13, atol=1e-13)
+
+
+def test_phase_carrier_reflection_symmetry():
+    """Reflecting d across the plane normal to x flips v = d.x and leaves u: the
+    phase family obeys G(d; phi) = G(reflected d; -phi)."""
+    rng = np.random.default_rng(34)
+    n = 300
+    q = _unit(rng.standard_normal((n, 4)))
+    x, z = ng.frame_from_quat(q)
+    d = _unit(rng.standard_normal((n, 3)))
+    dr = d - 2.0 * np.sum(d * x, axis=-1, keepdims=True) * x
+    lam, a, k = rng.uniform(0.5, 30, n), rng.uniform(0, 1, n), rng.uniform(0, 40, n)
+    phi = rng.uniform(0, 2 * np.pi, n)
+    g1 = ng.lobe(d, x, z, lam, a, k, ng.NORM_APPROX, phi=phi)
+    g2 = ng.lobe(dr, x, z, lam, a, k, ng.NORM_APPROX, phi=-phi)
+    np.testing.assert_allclose(g1, g2, rtol=1e-11, atol=1e-14)
+
+
+@pytest.mark.parametrize("lam,k,phi", [(3.0, 9.0, 0.7), (40.0, 12.0, 2.0), (5.0, 5.0, math.pi), (200.0, 30.0, 4.0)])
+def test_phase_carrier_exact_normalisation_has_unit_mass(lam, k, phi):
+    """a = 0: with the cos(phi)-scaled closed form (the sin part integrates to 0)
+    the exactly normalised phase-shifted lobe integrates to 1."""
+    val = integrate_lobe(lambda *args, **kw: ng.lobe(*args, **kw, phi=np.full(np.shape(args[3]), phi)),
+                         lam, 0.0, k, ng.NORM_EXACT)
+    assert abs(val - 1.0) < 1e-9
