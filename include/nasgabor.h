@@ -69,6 +69,24 @@ typedef int32_t nasg_status;
                                Lam = lam (1+a); the paper's "Exact" variant. The printed integral is
                                exact for a = 0 or k = 0 and approximate otherwise.               */
 
+/* Lobe families: the NASGabor lobe and its specialisations. Stored per lobe, after the
+ * frame scalars (4 quaternion or 3 cosine planes), in this order:
+ *   NASG_FAMILY_NASGABOR  lam, a, k, w_r, w_g, w_b       (P = 10 QUAT / 9 COS)
+ *   NASG_FAMILY_NASG      lam, a, w_r, w_g, w_b          (k = 0: no carrier; P = 9)
+ *   NASG_FAMILY_SG        lam, w_r, w_g, w_b             (a = 0, k = 0: the normalised
+ *                                                          spherical Gaussian; P = 8)
+ *   NASG_FAMILY_PHASE     lam, a, k, phi, w_r, w_g, w_b  (carrier (1 + cos(k v + phi))/2,
+ *                                                          phi stored as is; P = 11)
+ * NASG and SG are the Sec. 5.1 lobe at k = 0 (and a = 0), the distributions of the
+ * Supp. A table; the phase carrier is not in the paper (its integral: the
+ * closed form with Psi scaled by cos(phi), since the envelope is even in d.x).
+ * The families other than NASGabor take QUAT frames and the evaluation entry
+ * points (fwd, bwd, fused fwd+bwd) only. */
+#define NASG_FAMILY_NASGABOR 0
+#define NASG_FAMILY_NASG     1
+#define NASG_FAMILY_SG       2
+#define NASG_FAMILY_PHASE    3
+
 #define NASG_ACT_RAW      0 /* stored values are raw; Supp. C activations applied   */
 #define NASG_ACT_IDENTITY 1 /* stored values are the activated quantities           */
 
@@ -83,10 +101,16 @@ typedef struct nasg_desc {
   int32_t norm_mode;    /* NASG_NORM_*                                                 */
   int32_t act_mode;     /* NASG_ACT_*                                                  */
   int32_t accumulate;   /* backward outputs: 0 overwrite, 1 add into (g += ...)        */
+  int32_t lobe_family;  /* NASG_FAMILY_* (0 = the NASGabor lobe)                       */
+  int32_t reserved;     /* must be 0                                                   */
 } nasg_desc;
 
 /* Raw scalars per lobe for a frame mode: 10 (QUAT) or 9 (COS); -1 if invalid. */
 int32_t nasg_lobe_planes(int32_t frame_mode);
+
+/* Raw scalars per lobe for a frame mode and lobe family (see NASG_FAMILY_*); -1 if
+ * the combination is invalid or not supported. */
+int32_t nasg_param_planes(int32_t frame_mode, int32_t lobe_family);
 
 /* Static description of a status code (never NULL). */
 const char* nasg_status_string(nasg_status status);
@@ -102,7 +126,7 @@ int32_t nasg_last_cuda_error(void);
 nasg_status nasg_device_status(void* stream);
 
 /* ABI version of this header (bumped on any incompatible change). */
-#define NASG_ABI_VERSION 1
+#define NASG_ABI_VERSION 2
 int32_t nasg_abi_version(void);
 
 /*

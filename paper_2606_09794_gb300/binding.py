@@ -25,6 +25,7 @@ lib = ctypes.CDLL(LIB_PATH)
 
 FRAME = {"quat": 0, "cos": 1}
 NORM = {"approx": 0, "none": 1, "exact": 2}
+FAMILY = {"nasgabor": 0, "nasg": 1, "sg": 2, "phase": 3}
 ACT = {"raw": 0, "identity": 1}
 PLANES = {"quat": 10, "cos": 9}
 
@@ -35,7 +36,8 @@ _i64 = ctypes.c_int64
 
 class NasgDesc(ctypes.Structure):
     _fields_ = [("n", _i64), ("n_lobes", _i32), ("frame_mode", _i32), ("param_dtype", _i32),
-                ("norm_mode", _i32), ("act_mode", _i32), ("accumulate", _i32)]
+                ("norm_mode", _i32), ("act_mode", _i32), ("accumulate", _i32), ("lobe_family", _i32),
+                ("reserved", _i32)]
 
 
 class NasgAdam(ctypes.Structure):
@@ -77,6 +79,7 @@ def _decl(name, argtypes, restype=_i32):
 
 _P = ctypes.POINTER
 _decl("nasg_lobe_planes", [_i32])
+_decl("nasg_param_planes", [_i32, _i32])
 _decl("nasg_status_string", [_i32], ctypes.c_char_p)
 _decl("nasg_last_cuda_error", [])
 _decl("nasg_abi_version", [])
@@ -161,9 +164,23 @@ def _param_dtype(t):
 
 
 def make_desc(n, n_lobes, frame_mode="quat", param_dtype=torch.float32, norm_mode="approx", act_mode="raw",
-              accumulate=False) -> NasgDesc:
+              accumulate=False, family="nasgabor") -> NasgDesc:
     return NasgDesc(int(n), int(n_lobes), FRAME[frame_mode], 1 if param_dtype == torch.bfloat16 else 0,
-                    NORM[norm_mode], ACT[act_mode], 1 if accumulate else 0)
+                    NORM[norm_mode], ACT[act_mode], 1 if accumulate else 0, FAMILY[family], 0)
+
+
+def param_planes(frame_mode="quat", family="nasgabor"):
+    """Stored scalars per lobe for a frame mode and lobe family."""
+    p = lib.nasg_param_planes(FRAME[frame_mode], FAMILY[family])
+    if p < 0:
+        raise ValueError(f"unsupported frame/family {frame_mode}/{family}")
+    return p
+
+
+def _check_planes(params, n, n_lobes, frame_mode, family):
+    p = param_planes(frame_mode, family)
+    if params.dim() != 2 or params.shape[0] != p or params.shape[1] != n * n_lobes:
+        raise ValueError(f"params must be [{p}, {n * n_lobes}] for {frame_mode}/{family}, got {tuple(params.shape)}")
 
 
 def nasg_device_status(stream=None):
@@ -197,7 +214,7 @@ def lobe_planes(frame_mode="quat") -> int:
 
 
 def nasgabor_eval_fwd(params, c0, means, cam, n_lobes, frame_mode="quat", norm_mode="approx",
-                      act_mode="raw", idx=None, rgb=None, stream=None):
+                      act_mode="raw", idx=None, rgb=None, stream=None, family="nasgabor"):
     """rgb [N, 3] = c0 + sum_l w_l G_l(d) at d = normalize(means - cam); see include/nasgabor.h."""
     _cuda(params, "params")
     _cuda(c0, "c0", params.dtype)
@@ -208,7 +225,8 @@ def nasgabor_eval_fwd(params, c0, means, cam, n_lobes, frame_mode="quat", norm_m
     _cuda(rgb, "rgb", torch.float32)
     if idx is not None:
         _cuda(idx, "idx", torch.int32)
-    desc = make_desc(n, n_lobes, frame_mode, params.dtype, norm_mode, act_mode)
+    _check_planes(params, n, n_lobes, frame_mode, family)
+    desc = make_desc(n, n_lobes, frame_mode, params.dtype, norm_mode, act_mode, family=family)
     _param_dtype(params)
     _check(lib.nasgabor_eval_fwd(ctypes.byref(desc), _ptr(params), _ptr(c0), _ptr(means), _cam(cam),
                                  _ptr(idx), 0 if idx is None else idx.numel(), _ptr(rgb), _stream(stream)),
@@ -218,7 +236,7 @@ def nasgabor_eval_fwd(params, c0, means, cam, n_lobes, frame_mode="quat", norm_m
 
 def nasgabor_eval_bwd(params, means, cam, g_rgb, n_lobes, frame_mode="quat", norm_mode="approx",
                       act_mode="raw", idx=None, g_params=None, g_c0=None, g_means=None, want_means=True,
-                      accumulate=False, stream=None):
+                      accumulate=False, stream=None, family="nasgabor"):
     """(g_params [P, N*L] f32, g_c0 [3, N] f32, g_means [N, 3] f32 or None); see include/nasgabor.h."""
     _cuda(params, "params")
     _cuda(means, "means", torch.float32)
@@ -237,7 +255,8 @@ def nasgabor_eval_bwd(params, means, cam, g_rgb, n_lobes, frame_mode="quat", nor
         _cuda(g_means, "g_means", torch.float32)
     if idx is not None:
         _cuda(idx, "idx", torch.int32)
-    desc = make_desc(n, n_lobes, frame_mode, params.dtype, norm_mode, act_mode, accumulate)
+    _check_planes(params, n, n_lobes, frame_mode, family)
+    desc = make_desc(n, n_lobes, frame_mode, params.dtype, norm_mode, act_mode, accumulate, family)
     _param_dtype(params)
     _check(lib.nasgabor_eval_bwd(ctypes.byref(desc), _ptr(params), _ptr(means), _cam(cam), _ptr(idx),
                                  0 if idx is None else idx.numel(), _ptr(g_rgb), _ptr(g_params), _ptr(g_c0),
@@ -246,7 +265,7 @@ def nasgabor_eval_bwd(params, means, cam, g_rgb, n_lobes, frame_mode="quat", nor
 
 
 def nasgabor_fused_fwd_bwd(params, c0, means, cam, g_rgb, n_lobes, frame_mode="quat", norm_mode="approx",
-                           act_mode="raw", out=None, want_means=True, stream=None):
+                           act_mode="raw", out=None, want_means=True, stream=None, family="nasgabor"):
     """One pass: (rgb, g_params, g_c0, g_means) for a given upstream gradient g_rgb."""
     _cuda(params, "params")
     _cuda(c0, "c0", params.dtype)
@@ -260,7 +279,8 @@ def nasgabor_fused_fwd_bwd(params, c0, means, cam, g_rgb, n_lobes, frame_mode="q
                torch.empty((3, n), device=dev, dtype=torch.float32),
                torch.empty((n, 3), device=dev, dtype=torch.float32) if want_means else None)
     rgb, g_params, g_c0, g_means = out
-    desc = make_desc(n, n_lobes, frame_mode, params.dtype, norm_mode, act_mode)
+    _check_planes(params, n, n_lobes, frame_mode, family)
+    desc = make_desc(n, n_lobes, frame_mode, params.dtype, norm_mode, act_mode, family=family)
     _param_dtype(params)
     _check(lib.nasgabor_fused_fwd_bwd(ctypes.byref(desc), _ptr(params), _ptr(c0), _ptr(means), _cam(cam),
                                       _ptr(g_rgb), _ptr(rgb), _ptr(g_params), _ptr(g_c0), _ptr(g_means),
@@ -323,7 +343,7 @@ class TrainState:
 
 def nasgabor_fused_step(state, means, cam, g_rgb, n_lobes, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
                         idx=None, n_idx_device=None, frame_mode="quat", norm_mode="approx", act_mode="raw",
-                        evaluate_bf16=True, rgb=None, g_means=None, stream=None):
+                        evaluate_bf16=True, rgb=None, g_means=None, stream=None, family="nasgabor"):
     """Forward + backward + Adam for the listed primitives; state (TrainState) updated in place."""
     _cuda(means, "means", torch.float32)
     _cuda(g_rgb, "g_rgb", torch.float32)
@@ -336,7 +356,7 @@ def nasgabor_fused_step(state, means, cam, g_rgb, n_lobes, step, lr=1e-3, beta1=
         if t is not None:
             _cuda(t, nm, torch.float32)
     desc = make_desc(n, n_lobes, frame_mode, torch.bfloat16 if evaluate_bf16 else torch.float32,
-                     norm_mode, act_mode)
+                     norm_mode, act_mode, family=family)
     hp = NasgAdam(lr, beta1, beta2, eps, int(step))
     st = state.as_c()
     _check(lib.nasgabor_fused_step(ctypes.byref(desc), ctypes.byref(st), _ptr(means), _cam(cam), _ptr(idx),

@@ -46,6 +46,18 @@ extern "C" int32_t nasg_lobe_planes(int32_t frame_mode) {
   return -1;
 }
 
+extern "C" int32_t nasg_param_planes(int32_t frame_mode, int32_t lobe_family) {
+  const int32_t frame = nasg_lobe_planes(frame_mode);
+  if (frame < 0) return -1;
+  switch (lobe_family) {
+    case NASG_FAMILY_NASGABOR: return frame;
+    case NASG_FAMILY_NASG: return frame_mode == NASG_FRAME_QUAT ? 9 : -1;
+    case NASG_FAMILY_SG: return frame_mode == NASG_FRAME_QUAT ? 8 : -1;
+    case NASG_FAMILY_PHASE: return frame_mode == NASG_FRAME_QUAT ? 11 : -1;
+    default: return -1;
+  }
+}
+
 extern "C" const char* nasg_status_string(nasg_status status) {
   switch (status) {
     case NASG_OK: return "ok";

@@ -32,6 +32,20 @@
 namespace nasg {
 
 constexpr float kInvTwoPi = 0.159154943091895336f;  // 1 / (2 pi)
+
+// Lobe families (the NASGabor lobe and its specialisations; values equal the
+// NASG_FAMILY_* codes of the C ABI):
+//   NASGabor  G = C^-1 p E h               stored: lam, a, k, w
+//   NASG      k = 0 (h = 1)                stored: lam, a, w
+//   SG        a = 0, k = 0 (tau = 0, E = 1) stored: lam, w
+//   phase     h = (1 + cos(k v + phi))/2    stored: lam, a, k, phi, w  (phi as is)
+constexpr int kFamNasGabor = 0, kFamNasg = 1, kFamSg = 2, kFamPhase = 3;
+template <int FAM>
+struct Family {
+  static constexpr bool HAS_A = FAM != kFamSg;
+  static constexpr bool HAS_K = FAM == kFamNasGabor || FAM == kFamPhase;
+  static constexpr bool HAS_PHASE = FAM == kFamPhase;
+};
 constexpr float kFltMin = 1.17549435e-38f;
 
 // ---------------------------------------------------------------------------
@@ -78,6 +92,7 @@ template <class V>
 struct Act {
   V lam, a, k, w[3];
   V s_lam, s_a, s_k, s_w[3];
+  V phi;  // carrier phase (phase family; stored as is)
 };
 
 // r: lam_r, a_r, k_r, w_r, w_g, w_b
@@ -104,6 +119,41 @@ __device__ __forceinline__ void activate(const V* r, bool identity, Act<V>& o) {
   o.s_k = 80.f * sig * one_m_sig;
 #pragma unroll
   for (int c = 0; c < 3; ++c) vtanh(r[3 + c], o.w[c], o.s_w[c]);
+}
+
+// Activations of a lobe family's stored scalars r = [lam, (a), (k), (phi), w_r, w_g, w_b];
+// the quantities a family does not store are 0.
+template <int FAM, class V>
+__device__ __forceinline__ void activate_family(const V* r, bool identity, Act<V>& o) {
+  using F = Family<FAM>;
+  constexpr int A = 1, K = 1 + F::HAS_A, PH = K + F::HAS_K, W = PH + F::HAS_PHASE;
+  const V zero = vconst<V>(0.f), one = vconst<V>(1.f);
+  o.phi = F::HAS_PHASE ? r[PH] : zero;
+  if (identity) {
+    o.lam = r[0];
+    o.a = F::HAS_A ? r[A] : zero;
+    o.k = F::HAS_K ? r[K] : zero;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { o.w[c] = r[W + c]; o.s_w[c] = one; }
+    o.s_lam = one; o.s_a = one; o.s_k = one;
+    return;
+  }
+  o.lam = vexp(r[0]);
+  o.s_lam = o.lam;
+  o.a = zero; o.s_a = zero; o.k = zero; o.s_k = zero;
+  if (F::HAS_A) {
+    o.a = vexp(r[A]);
+    o.s_a = o.a;
+  }
+  if (F::HAS_K) {
+    const V e = vexp(-2.f * r[K]);
+    const V sig = vrcp(1.f + e);
+    const V one_m_sig = vsel(vge(r[K], 0.f), e * sig, 1.f - sig);
+    o.k = 40.f * sig;
+    o.s_k = 80.f * sig * one_m_sig;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) vtanh(r[W + c], o.w[c], o.s_w[c]);
 }
 
 // ---------------------------------------------------------------------------
@@ -220,6 +270,7 @@ __device__ __forceinline__ void cos_frame_grad(const CosFrame<V>& f, const V* gx
 template <class V>
 struct LobePartials {
   V G_u, G_v, G_lam, G_a, G_k;  // dG/du, dG/dv, dG/dlam, dG/da, dG/dk
+  V G_phi;                      // dG/dphi (phase family)
 };
 
 // ---------------------------------------------------------------------------
@@ -244,9 +295,12 @@ struct LobePartials {
 //               + Lam (A k^2 / (s + Lam) + B (s + Lam)) / (s^2 (1 - e^{-2 Lam})),
 // and 1/Lam - coth Lam = -(Lam/3 - Lam^3/45 + 2 Lam^5/945 - Lam^7/4725 + 2 Lam^9/93555)
 // below Lam = 1/2. dLam/dlam = 1 + a, dLam/da = lam.
-template <bool GRAD>
+// With a carrier phase phi the sin(k v) sin(phi) part of the carrier integrates
+// to zero (the envelope is even in v), so R = 2 / (1 + cos(phi) Psi), its
+// Lam / k derivatives scale by cos(phi), and d ln R/dphi = (R/2) sin(phi) Psi.
+template <bool GRAD, bool PHASE = false>
 __device__ __forceinline__ void exact_norm1(float lam, float a, float k, float& r, float& dl, float& da,
-                                            float& dk) {
+                                            float& dk, float phi = 0.f, float* dphi = nullptr) {
   const float opa = 1.f + a;
   const float L = lam * opa;
   const float sig = (L - k) * (L + k);
@@ -289,7 +343,9 @@ __device__ __forceinline__ void exact_norm1(float lam, float a, float k, float& 
     esp = el * fmaf(-t, cs, sn) * (0.5f * rt * rt * rt);
   }
   const float psi = c * es;
-  r = 2.f * rcpa(1.f + psi);
+  float cph = 1.f, sph = 0.f;
+  if (PHASE) vsincos<float>(phi, sph, cph);
+  r = 2.f * rcpa(fmaf(cph, psi, 1.f));
   if (GRAD) {
     if (rearranged) {
       const float e2 = vexp(-2.f * L);
@@ -311,10 +367,11 @@ __device__ __forceinline__ void exact_norm1(float lam, float a, float k, float& 
       dpsi_dl = fmaf(psi, lg, 2.f * L * c * esp);
     }
     const float dpsi_dk = -2.f * k * c * esp;
-    const float h = -0.5f * r;
+    const float h = -0.5f * r * cph;
     dl = h * dpsi_dl * opa;
     da = h * dpsi_dl * lam;
     dk = h * dpsi_dk;
+    if (PHASE) *dphi = 0.5f * r * sph * psi;
   }
 }
 
@@ -327,10 +384,23 @@ __device__ __forceinline__ void exact_norm(P2 lam, P2 a, P2 k, P2& r, P2& dl, P2
   exact_norm1<GRAD>(lam.v.x, a.v.x, k.v.x, r.v.x, dl.v.x, da.v.x, dk.v.x);
   exact_norm1<GRAD>(lam.v.y, a.v.y, k.v.y, r.v.y, dl.v.y, da.v.y, dk.v.y);
 }
+template <bool GRAD>
+__device__ __forceinline__ void exact_norm_phase(float lam, float a, float k, float phi, float& r, float& dl,
+                                                 float& da, float& dk, float& dphi) {
+  exact_norm1<GRAD, true>(lam, a, k, r, dl, da, dk, phi, &dphi);
+}
+template <bool GRAD>
+__device__ __forceinline__ void exact_norm_phase(P2 lam, P2 a, P2 k, P2 phi, P2& r, P2& dl, P2& da, P2& dk,
+                                                 P2& dphi) {
+  exact_norm1<GRAD, true>(lam.v.x, a.v.x, k.v.x, r.v.x, dl.v.x, da.v.x, dk.v.x, phi.v.x, &dphi.v.x);
+  exact_norm1<GRAD, true>(lam.v.y, a.v.y, k.v.y, r.v.y, dl.v.y, da.v.y, dk.v.y, phi.v.y, &dphi.v.y);
+}
 
-template <bool GRAD, class V>
-__device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a, V k, bool normalised, bool exact,
-                                  LobePartials<V>* pd) {
+// One lobe of family FAM (a, k, phi ignored where the family has none; see Family).
+template <bool GRAD, int FAM, class V>
+__device__ __forceinline__ V lobe_family(const V* d, const V* x, const V* z, V lam, V a, V k, V phi,
+                                         bool normalised, bool exact, LobePartials<V>* pd) {
+  using F = Family<FAM>;
   using M = typename VecTraits<V>::Mask;
   const V u = vfma(d[0], z[0], vfma(d[1], z[1], d[2] * z[2]));
   const V v = vfma(d[0], x[0], vfma(d[1], x[1], d[2] * x[2]));
@@ -351,25 +421,46 @@ __device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a
   const V inv_opu = vsel(up, rd, one_m_u * inv_s2);  // 1/(1+u) = 1/(2 kappa)
   const V t = -0.5f * omu;
   const V kap = vsel(up, 1.f + t, 0.5f * opu);
-  const V ln_k = vsel(anti, 0.f, vlnkappa(t, vmax(kap, kFltMin)));  // ln kappa
-  const V tau = a * v * v * inv_s2;
+  // without anisotropy (SG): tau = 0, E = 1, E kappa - 1 = kappa - 1 = t exactly
+  const V ln_k = F::HAS_A ? vsel(anti, 0.f, vlnkappa(t, vmax(kap, kFltMin))) : vconst<V>(0.f);  // ln kappa
+  const V tau = F::HAS_A ? a * v * v * inv_s2 : vconst<V>(0.f);
   const V ln_e = tau * ln_k;                                      // ln E
-  const V em1 = vexpm1n(ln_e + ln_k);                             // E kappa - 1
-  const V pe = vexp(vfma(2.f * lam, em1, ln_e));                  // p E
-  V h, sin_kv;  // (1 + cos(k v))/2 and sin(k v)
-  vcarrier(0.5f * k * v, h, sin_kv);
+  const V em1 = F::HAS_A ? vexpm1n(ln_e + ln_k) : t;              // E kappa - 1
+  const V pe = F::HAS_A ? vexp(vfma(2.f * lam, em1, ln_e)) : vexp(2.f * lam * t);  // p E
+  V h = vconst<V>(1.f), sin_kv = vconst<V>(0.f);  // (1 + cos(k v + phi))/2 and sin(k v + phi)
+  if (F::HAS_PHASE) {
+    vcarrier(0.5f * vfma(k, v, phi), h, sin_kv);
+  } else if (F::HAS_K) {
+    vcarrier(0.5f * k * v, h, sin_kv);
+  }
   V cinv = vconst<V>(1.f), dlnc_dlam = vconst<V>(0.f), dlnc_da = vconst<V>(0.f), dlnc_dk = vconst<V>(0.f);
+  V dlnc_dphi = vconst<V>(0.f);
   if (normalised) {
     const V em = vexpm1n(-2.f * lam);  // e^{-2 lam} - 1 (negative)
     const V r_em = vrcp(em);
-    const V opa = 1.f + a;
-    cinv = -((lam * (opa * vrsqrt(opa))) * (kInvTwoPi * r_em));
+    if (F::HAS_A) {
+      const V opa = 1.f + a;
+      cinv = -((lam * (opa * vrsqrt(opa))) * (kInvTwoPi * r_em));
+    } else {
+      cinv = -(lam * (kInvTwoPi * r_em));
+    }
     if (GRAD) {
       // d ln C^-1/d lam = 1/lam - 2 e^{-2 lam}/(1 - e^{-2 lam}); d ln C^-1/d a = 1/(2 (1+a))
       dlnc_dlam = vfma(2.f * (1.f + em), r_em, vrcp(lam));
-      dlnc_da = 0.5f * vrcp(opa);
+      if (F::HAS_A) dlnc_da = 0.5f * vrcp(1.f + a);
     }
-    if (exact) {
+    // without a carrier the closed form is the NASG constant itself (Psi = 1)
+    if (exact && F::HAS_PHASE) {
+      V r, dr_lam, dr_a, dr_k, dr_phi;
+      exact_norm_phase<GRAD>(lam, a, k, phi, r, dr_lam, dr_a, dr_k, dr_phi);
+      cinv = cinv * r;
+      if (GRAD) {
+        dlnc_dlam = dlnc_dlam + dr_lam;
+        dlnc_da = dlnc_da + dr_a;
+        dlnc_dk = dr_k;
+        dlnc_dphi = dr_phi;
+      }
+    } else if (exact && F::HAS_K) {
       V r, dr_lam, dr_a, dr_k;
       exact_norm<GRAD>(lam, a, k, r, dr_lam, dr_a, dr_k);
       cinv = cinv * r;
@@ -391,14 +482,34 @@ __device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a
     const V dtau_dv = 2.f * a * v * inv_s2;
     const V dlne_du = vfma(ln_k, dtau_du, tau * inv_opu);
     const V dlne_dv = ln_k * dtau_dv;
-    const V cpe_sin = cpe * sin_kv;                     // C^-1 p E sin(k v)
-    pd->G_u = G * vfma(two_lam_ek, dlne_du + inv_opu, dlne_du);
-    pd->G_v = vfma(G * (two_lam_ek + 1.f), dlne_dv, -(cpe_sin * (0.5f * k)));
-    pd->G_k = exact ? vfma(G, dlnc_dk, -(cpe_sin * (0.5f * v))) : -(cpe_sin * (0.5f * v));
+    const V cpe_sin = cpe * sin_kv;                     // C^-1 p E sin(k v + phi)
+    if (F::HAS_A) {
+      pd->G_u = G * vfma(two_lam_ek, dlne_du + inv_opu, dlne_du);
+      const V gv_env = G * (two_lam_ek + 1.f) * dlne_dv;
+      pd->G_v = F::HAS_K ? vfma(G * (two_lam_ek + 1.f), dlne_dv, -(cpe_sin * (0.5f * k))) : gv_env;
+      pd->G_a = G * vfma((two_lam_ek + 1.f) * ln_k, v * v * inv_s2, dlnc_da);
+    } else {
+      pd->G_u = G * lam;                                // d/du 2 lam (kappa - 1) = lam
+      pd->G_v = vconst<V>(0.f);
+      pd->G_a = vconst<V>(0.f);
+    }
+    if (F::HAS_K) {
+      pd->G_k = exact ? vfma(G, dlnc_dk, -(cpe_sin * (0.5f * v))) : -(cpe_sin * (0.5f * v));
+    } else {
+      pd->G_k = vconst<V>(0.f);
+    }
+    pd->G_phi = F::HAS_PHASE ? (exact ? vfma(G, dlnc_dphi, -(0.5f * cpe_sin)) : -(0.5f * cpe_sin))
+                             : vconst<V>(0.f);
     pd->G_lam = G * vfma(2.f, em1, dlnc_dlam);
-    pd->G_a = G * vfma((two_lam_ek + 1.f) * ln_k, v * v * inv_s2, dlnc_da);
   }
   return G;
+}
+
+// The NASGabor lobe.
+template <bool GRAD, class V>
+__device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a, V k, bool normalised, bool exact,
+                                  LobePartials<V>* pd) {
+  return lobe_family<GRAD, kFamNasGabor>(d, x, z, lam, a, k, vconst<V>(0.f), normalised, exact, pd);
 }
 
 // ---------------------------------------------------------------------------

@@ -254,7 +254,7 @@ extern "C" nasg_status nasgabor_fit_step(const nasg_desc* desc, const nasg_train
                                          size_t workspace_bytes, void* stream) {
   nasg_status e = check_desc(desc);
   if (e != NASG_OK) return e;
-  if (desc->frame_mode != NASG_FRAME_QUAT) return NASG_ERR_UNSUPPORTED;
+  if (desc->frame_mode != NASG_FRAME_QUAT || desc->lobe_family != NASG_FAMILY_NASGABOR) return NASG_ERR_UNSUPPORTED;
   if (desc->accumulate != 0) return NASG_ERR_RANGE;
   if (!st || !hp || !loss) return NASG_ERR_NULL;
   const int ls = desc->n_lobes;

@@ -50,6 +50,9 @@ inline nasg_status check_desc(const nasg_desc* d) {
     return NASG_ERR_RANGE;
   if (d->act_mode != NASG_ACT_RAW && d->act_mode != NASG_ACT_IDENTITY) return NASG_ERR_RANGE;
   if (d->accumulate != 0 && d->accumulate != 1) return NASG_ERR_RANGE;
+  if (d->lobe_family < NASG_FAMILY_NASGABOR || d->lobe_family > NASG_FAMILY_PHASE || d->reserved != 0)
+    return NASG_ERR_RANGE;
+  if (d->lobe_family != NASG_FAMILY_NASGABOR && d->frame_mode != NASG_FRAME_QUAT) return NASG_ERR_UNSUPPORTED;
   // element offsets are 64-bit; keep P*N*L well inside int64
   if (d->n > (int64_t(1) << 40)) return NASG_ERR_RANGE;
   return NASG_OK;

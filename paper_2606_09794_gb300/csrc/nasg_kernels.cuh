@@ -46,10 +46,26 @@ struct EvalArgs {
   int* dev_err;         // device error word (bounded waits)
 };
 
+// Stored-lobe layout. The kernels' FRAME template parameter is a layout id,
+// 4 * lobe family + frame mode, so that the NASGabor lobe keeps ids 0 (QUAT) and
+// 1 (COS). Planes: the frame (4 quaternion or 3 cosine scalars), then lam, a, k,
+// phi and the three weights, each where the family stores it.
+static_assert(kFamNasGabor == NASG_FAMILY_NASGABOR && kFamNasg == NASG_FAMILY_NASG && kFamSg == NASG_FAMILY_SG &&
+                  kFamPhase == NASG_FAMILY_PHASE,
+              "family codes");
+constexpr int layout_id(int frame_mode, int family) { return 4 * family + frame_mode; }
+
 template <int FRAME>
 struct FrameTraits {
-  static constexpr int P = (FRAME == NASG_FRAME_QUAT) ? 10 : 9;  // raw scalars per lobe
-  static constexpr int B = (FRAME == NASG_FRAME_QUAT) ? 4 : 3;   // first non-frame plane
+  static constexpr int FAM = FRAME >> 2;
+  static constexpr bool QUAT = (FRAME & 3) == NASG_FRAME_QUAT;
+  using F = Family<FAM>;
+  static constexpr int B = QUAT ? 4 : 3;  // first non-frame plane (lam)
+  static constexpr int A = B + 1;
+  static constexpr int K = B + 1 + (F::HAS_A ? 1 : 0);
+  static constexpr int PH = K + (F::HAS_K ? 1 : 0);
+  static constexpr int W = PH + (F::HAS_PHASE ? 1 : 0);
+  static constexpr int P = W + 3;         // raw scalars per lobe
 };
 
 // Evaluates the lobes held in pv[0..P) (one lobe per component of V): adds their
@@ -58,13 +74,19 @@ struct FrameTraits {
 template <int FRAME, bool FWD, bool BWD, class V>
 __device__ __forceinline__ void lobe_step(const V* pv, const V* d, const V* gc, bool identity, bool normalised,
                                           bool exact, V* rgb, V* gd, V* gp) {
-  constexpr int B = FrameTraits<FRAME>::B;
+  using TR = FrameTraits<FRAME>;
+  using F = typename TR::F;
+  constexpr int B = TR::B;
   Act<V> act;
-  activate(pv + B, identity, act);
+  if constexpr (TR::FAM == kFamNasGabor) {
+    activate(pv + B, identity, act);
+  } else {
+    activate_family<TR::FAM>(pv + B, identity, act);
+  }
   V x[3], z[3];
   QuatFrame<V> qf;
   CosFrame<V> cf;
-  if (FRAME == NASG_FRAME_QUAT) {
+  if (TR::QUAT) {
     quat_frame(pv, qf);
 #pragma unroll
     for (int c = 0; c < 3; ++c) { x[c] = qf.x[c]; z[c] = qf.z[c]; }
@@ -74,24 +96,30 @@ __device__ __forceinline__ void lobe_step(const V* pv, const V* d, const V* gc, 
     for (int c = 0; c < 3; ++c) { x[c] = cf.x[c]; z[c] = cf.z[c]; }
   }
   LobePartials<V> pd;
-  const V G = lobe<BWD>(d, x, z, act.lam, act.a, act.k, normalised, exact, &pd);
+  V G;
+  if constexpr (TR::FAM == kFamNasGabor) {
+    G = lobe<BWD>(d, x, z, act.lam, act.a, act.k, normalised, exact, &pd);
+  } else {
+    G = lobe_family<BWD, TR::FAM>(d, x, z, act.lam, act.a, act.k, act.phi, normalised, exact, &pd);
+  }
   if (FWD) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) rgb[c] = vfma(act.w[c], G, rgb[c]);
   }
   if (BWD) {
     const V gG = vfma(gc[0], act.w[0], vfma(gc[1], act.w[1], gc[2] * act.w[2]));
-    gp[B + 0] = gG * pd.G_lam * act.s_lam;
-    gp[B + 1] = gG * pd.G_a * act.s_a;
-    gp[B + 2] = gG * pd.G_k * act.s_k;
+    gp[B] = gG * pd.G_lam * act.s_lam;
+    if constexpr (F::HAS_A) gp[TR::A] = gG * pd.G_a * act.s_a;
+    if constexpr (F::HAS_K) gp[TR::K] = gG * pd.G_k * act.s_k;
+    if constexpr (F::HAS_PHASE) gp[TR::PH] = gG * pd.G_phi;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) gp[B + 3 + c] = gc[c] * G * act.s_w[c];
+    for (int c = 0; c < 3; ++c) gp[TR::W + c] = gc[c] * G * act.s_w[c];
     const V gv = gG * pd.G_v, gu = gG * pd.G_u;
     const V gx[3] = {gv * d[0], gv * d[1], gv * d[2]};
     const V gz[3] = {gu * d[0], gu * d[1], gu * d[2]};
 #pragma unroll
     for (int c = 0; c < 3; ++c) gd[c] = vfma(gu, z[c], vfma(gv, x[c], gd[c]));
-    if (FRAME == NASG_FRAME_QUAT) {
+    if (TR::QUAT) {
       quat_frame_grad(qf, gx, gz, gp);
     } else {
       cos_frame_grad(cf, gx, gz, gp);
@@ -559,6 +587,29 @@ nasg_status launch_frame_dtype(const EvalArgs& a, bool even, cudaStream_t s) {
   return idx32 ? launch_idx<MODE, FRAME, T, uint32_t>(a, even, s) : launch_idx<MODE, FRAME, T, uint64_t>(a, even, s);
 }
 
+// Lobe families other than NASGabor (QUAT frames): the staged kernel with
+// run-time mode flags where it applies, else the register path with 64-bit
+// offsets. Instantiated per family in nasg_family_{nasg,sg,phase}.cu.
+template <int MODE, int FAM>
+nasg_status launch_family(const EvalArgs& a, bool even, bool bf16, cudaStream_t s) {
+  constexpr int LAYOUT = layout_id(NASG_FRAME_QUAT, FAM);
+  if (bf16) {
+    if (tma_eligible<LAYOUT, __nv_bfloat16>(a, even)) return launch_tma<MODE, LAYOUT, __nv_bfloat16, kFlagsRuntime>(a, s);
+    return launch_idx<MODE, LAYOUT, __nv_bfloat16, uint64_t>(a, even, s);
+  }
+  if (tma_eligible<LAYOUT, float>(a, even)) return launch_tma<MODE, LAYOUT, float, kFlagsRuntime>(a, s);
+  return launch_idx<MODE, LAYOUT, float, uint64_t>(a, even, s);
+}
+
+#define NASG_FAMILY_EXTERN(FAM)                                                                     \
+  extern template nasg_status launch_family<kFwd, FAM>(const EvalArgs&, bool, bool, cudaStream_t);   \
+  extern template nasg_status launch_family<kBwd, FAM>(const EvalArgs&, bool, bool, cudaStream_t);   \
+  extern template nasg_status launch_family<kFwdBwd, FAM>(const EvalArgs&, bool, bool, cudaStream_t);
+NASG_FAMILY_EXTERN(kFamNasg)
+NASG_FAMILY_EXTERN(kFamSg)
+NASG_FAMILY_EXTERN(kFamPhase)
+#undef NASG_FAMILY_EXTERN
+
 template <int MODE>
 nasg_status launch_eval(const nasg_desc* desc, EvalArgs a, cudaStream_t s) {
   a.dev_err = device_error_word();
@@ -569,6 +620,12 @@ nasg_status launch_eval(const nasg_desc* desc, EvalArgs a, cudaStream_t s) {
                     (a.g_params == nullptr || aligned(a.g_params, 8));
   const bool quat = desc->frame_mode == NASG_FRAME_QUAT;
   const bool bf16 = desc->param_dtype == NASG_DTYPE_BF16;
+  switch (desc->lobe_family) {
+    case NASG_FAMILY_NASG: return launch_family<MODE, kFamNasg>(a, even, bf16, s);
+    case NASG_FAMILY_SG: return launch_family<MODE, kFamSg>(a, even, bf16, s);
+    case NASG_FAMILY_PHASE: return launch_family<MODE, kFamPhase>(a, even, bf16, s);
+    default: break;
+  }
   if (quat) {
     return bf16 ? launch_frame_dtype<MODE, NASG_FRAME_QUAT, __nv_bfloat16>(a, even, s)
                 : launch_frame_dtype<MODE, NASG_FRAME_QUAT, float>(a, even, s);

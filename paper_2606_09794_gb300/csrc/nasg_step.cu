@@ -363,6 +363,7 @@ extern "C" nasg_status nasgabor_fused_step(const nasg_desc* desc, const nasg_tra
                                            const nasg_adam_hparams* hp, float* rgb, float* g_means, void* stream) {
   nasg_status e = check_desc(desc);
   if (e != NASG_OK) return e;
+  if (desc->lobe_family != NASG_FAMILY_NASGABOR) return NASG_ERR_UNSUPPORTED;
   if (desc->accumulate != 0) return NASG_ERR_RANGE;
   if (!st || !hp || !cam) return NASG_ERR_NULL;
   if (idx && n_idx < 0) return NASG_ERR_RANGE;

@@ -49,7 +49,7 @@ def test_every_declared_symbol_is_exported(so):
 class Desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_lobes", ctypes.c_int32), ("frame_mode", ctypes.c_int32),
                 ("param_dtype", ctypes.c_int32), ("norm_mode", ctypes.c_int32), ("act_mode", ctypes.c_int32),
-                ("accumulate", ctypes.c_int32)]
+                ("accumulate", ctypes.c_int32), ("lobe_family", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def _fwd(so):
@@ -74,7 +74,8 @@ def test_host_validation_rejects_before_launch(so):
     assert fwd(ctypes.byref(good), P, P, P, None, None, 0, P, None) == NASG_ERR_NULL
     for bad in (Desc(-1, 4, 0, 0, 0, 0, 0), Desc(16, 0, 0, 0, 0, 0, 0), Desc(16, 33, 0, 0, 0, 0, 0),
                 Desc(16, 4, 2, 0, 0, 0, 0), Desc(16, 4, 0, 2, 0, 0, 0), Desc(16, 4, 0, 0, 7, 0, 0),
-                Desc(16, 4, 0, 0, 0, 2, 0), Desc(16, 4, 0, 0, 0, 0, 3)):
+                Desc(16, 4, 0, 0, 0, 2, 0), Desc(16, 4, 0, 0, 0, 0, 3), Desc(16, 4, 0, 0, 0, 0, 0, 4),
+                Desc(16, 4, 0, 0, 0, 0, 0, -1), Desc(16, 4, 0, 0, 0, 0, 0, 0, 1)):
         assert fwd(ctypes.byref(bad), P, P, P, CAM, None, 0, P, None) == NASG_ERR_RANGE
     assert fwd(ctypes.byref(good), MIS, P, P, CAM, None, 0, P, None) == NASG_ERR_ALIGN
     assert fwd(ctypes.byref(good), P, P, P, CAM, P, -1, P, None) == NASG_ERR_RANGE
@@ -101,4 +102,11 @@ def test_status_strings_and_planes(so):
     for s in (0, -1, -2, -3, -4, -5, -6, -99):
         assert so.nasg_status_string(s)
     assert so.nasg_lobe_planes(0) == 10 and so.nasg_lobe_planes(1) == 9 and so.nasg_lobe_planes(5) == -1
-    assert so.nasg_abi_version() >= 1
+    assert so.nasg_abi_version() >= 2
+    assert [so.nasg_param_planes(0, f) for f in range(5)] == [10, 9, 8, 11, -1]
+    assert [so.nasg_param_planes(1, f) for f in range(4)] == [9, -1, -1, -1]
+
+
+def test_lobe_family_needs_quaternion_frames(so):
+    fwd = _fwd(so)
+    assert fwd(ctypes.byref(Desc(16, 4, 1, 0, 0, 0, 0, 2)), P, P, P, CAM, None, 0, P, None) == -4

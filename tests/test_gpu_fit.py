@@ -89,3 +89,36 @@ def test_fit_run_matches_oracle_fit_on_a_sample(lib):
                      - target) ** 2)
     assert mse_ref < 0.9 * start  # the fit makes progress
     assert abs(mse_gpu - mse_ref) <= 0.01 * mse_ref, (mse_gpu, mse_ref, start)
+
+
+def test_fit_subsample_matches_stored_oracle_fit(lib):
+    """The full fitting workload's 20,000-primitive subsample (2M primitives, 16-lobe
+    BF16 student, 4-lobe teacher, 64 directions, 200 Adam steps at lr 1e-3): the
+    GPU's per-step loss and its loss at the held-out step-201 directions against the
+    FP64 oracle's fit stored by tests/golden/make_fit_golden.py (1 %)."""
+    import importlib.util
+    import json
+    import os
+
+    import torch
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_fit_golden", os.path.join(here, "make_fit_golden.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    with open(os.path.join(here, "fit_subsample_20k.json")) as f:
+        gold = json.load(f)
+    tp, tc, sp, sc, _ = gen.subsample_workload()
+    st = lib.TrainState(_dev(sp), _dev(sc))
+    tpd, tcd = _dev(tp), _dev(tc)
+    steps = gold["workload"]["steps"]
+    losses = torch.empty(steps + 1, device="cuda")
+    for step in range(1, steps + 2):
+        lib.nasgabor_fit_step(st, tpd, tcd, gen.LT, _dev(inputs.fit_directions(step, gen.SEED_T)), gen.LS, step,
+                              loss=losses[step - 1:step])
+    got = losses.cpu().numpy().astype(np.float64)
+    ref = np.asarray(gold["bf16_storage"]["loss_per_step"])
+    rel = np.abs(got[:steps] - ref) / ref
+    assert rel.max() <= 0.01, (rel.max(), int(rel.argmax()))
+    final = gold["bf16_storage"]["final_mse"]
+    assert abs(got[steps] - final) <= 0.01 * final, (got[steps], final)
+    assert got[steps] < 0.9 * gold["bf16_storage"]["start_mse"]

@@ -35,17 +35,17 @@ def _prepare(w, bf16):
     return _dev(w.params), _dev(w.c0), w.params, w.c0
 
 
-def _check_forward(lib, w, bf16, norm="approx", act="raw", base=None):
+def _check_forward(lib, w, bf16, norm="approx", act="raw", base=None, family="nasgabor"):
     import torch
     params, c0, p_np, c0_np = _prepare(w, bf16)
     means = _dev(w.means)
-    rgb = lib.nasgabor_eval_fwd(params, c0, means, w.cam, w.n_lobes, w.frame_mode, norm, act)
+    rgb = lib.nasgabor_eval_fwd(params, c0, means, w.cam, w.n_lobes, w.frame_mode, norm, act, family=family)
     torch.cuda.synchronize()
     gpu = rgb.cpu().numpy()
     assert np.isfinite(gpu).all()
 
     def fwd(p, c, m, cam):
-        return ong.forward(p, c, m, cam, w.n_lobes, w.frame_mode, norm, act)
+        return ong.forward(p, c, m, cam, w.n_lobes, w.frame_mode, norm, act, family)
 
     ref, nu = sensitivity_floor(fwd, (p_np, c0_np, w.means, w.cam), (0, 1, 2, 3))
     rep = colour_report(gpu, ref, nu, base if base is not None else (4e-3 if bf16 else 1e-5))
@@ -53,14 +53,16 @@ def _check_forward(lib, w, bf16, norm="approx", act="raw", base=None):
     return rep
 
 
-def _check_backward(lib, w, bf16, norm="approx", act="raw"):
+def _check_backward(lib, w, bf16, norm="approx", act="raw", family="nasgabor"):
     import torch
     params, c0, p_np, c0_np = _prepare(w, bf16)
     means = _dev(w.means)
     g_rgb = _dev(w.g_rgb)
-    g_p, g_c0, g_mu = lib.nasgabor_eval_bwd(params, means, w.cam, g_rgb, w.n_lobes, w.frame_mode, norm, act)
+    g_p, g_c0, g_mu = lib.nasgabor_eval_bwd(params, means, w.cam, g_rgb, w.n_lobes, w.frame_mode, norm, act,
+                                            family=family)
     torch.cuda.synchronize()
-    r_p, r_c0, r_mu = ong.backward(p_np, c0_np, w.means, w.cam, w.g_rgb, w.n_lobes, w.frame_mode, norm, act)
+    r_p, r_c0, r_mu = ong.backward(p_np, c0_np, w.means, w.cam, w.g_rgb, w.n_lobes, w.frame_mode, norm, act,
+                                   family)
     g_p = g_p.cpu().numpy()
     assert np.isfinite(g_p).all()
     errs = [rel_l2(g_p[p], r_p[p]) for p in range(g_p.shape[0])]
@@ -103,6 +105,56 @@ def _exact_branch_workload():
     for row, vals in ((4, lam), (5, a), (6, k)):
         w.params[row] = np.tile(np.asarray(vals, dtype=np.float32), n * L // len(lam))
     return w
+
+
+FAMILY_CASES = [
+    # family, N, L, bf16, norm, act, seed
+    ("nasg", 1037, 8, False, "approx", "raw", 41),
+    ("nasg", 4096, 8, True, "approx", "raw", 42),      # staged path
+    ("sg", 777, 3, False, "approx", "raw", 43),
+    ("sg", 4096, 4, True, "approx", "raw", 44),
+    ("phase", 1029, 6, False, "approx", "raw", 45),
+    ("phase", 4096, 8, True, "exact", "raw", 46),
+    ("phase", 513, 5, False, "exact", "identity", 47),
+    ("nasg", 300, 2, False, "exact", "identity", 48),
+    ("phase", 2048, 4, False, "none", "raw", 49),
+]
+
+
+@pytest.mark.parametrize("family,n,L,bf16,norm,act,seed", FAMILY_CASES)
+def test_lobe_family_parity(lib, family, n, L, bf16, norm, act, seed):
+    """NASG, SG and the phase-shifted carrier against the oracle's families."""
+    w = inputs.variant_workload(n, L, seed, family, activated=(act == "identity"))
+    _check_forward(lib, w, bf16, norm, act, family=family)
+    _check_backward(lib, w, bf16, norm, act, family=family)
+
+
+@pytest.mark.parametrize("family", ["nasg", "sg", "phase"])
+def test_lobe_family_fused_equals_separate_passes(lib, family):
+    import torch
+    w = inputs.variant_workload(2048, 8, 50, family)
+    params, c0 = _dev(w.params).to(torch.bfloat16), _dev(w.c0).to(torch.bfloat16)
+    means, g_rgb = _dev(w.means), _dev(w.g_rgb)
+    rgb = lib.nasgabor_eval_fwd(params, c0, means, w.cam, 8, family=family)
+    g = lib.nasgabor_eval_bwd(params, means, w.cam, g_rgb, 8, family=family)
+    f = lib.nasgabor_fused_fwd_bwd(params, c0, means, w.cam, g_rgb, 8, family=family)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(f[0], rgb, rtol=1e-6, atol=1e-6)
+    fg, sg = f[1].cpu().numpy(), g[0].cpu().numpy()
+    assert max(rel_l2(fg[p], sg[p]) for p in range(fg.shape[0])) < 1e-6
+
+
+def test_lobe_family_rejections(lib):
+    import torch
+    w = inputs.variant_workload(64, 4, 51, "sg")
+    params, c0, means = _dev(w.params), _dev(w.c0), _dev(w.means)
+    with pytest.raises(ValueError):  # planes of the wrong family
+        lib.nasgabor_eval_fwd(params, c0, means, w.cam, 4, family="phase")
+    with pytest.raises(ValueError):  # families take QUAT frames
+        lib.nasgabor_eval_fwd(params, c0, means, w.cam, 4, frame_mode="cos", family="sg")
+    st = lib.TrainState(_dev(inputs.point_cloud_workload(64, 4, 52).params), c0.clone())
+    with pytest.raises(lib.NasgError):
+        lib.nasgabor_fused_step(st, means, w.cam, torch.zeros((64, 3), device="cuda"), 4, 1, family="sg")
 
 
 def test_exact_normalisation_branches(lib):
