@@ -11,9 +11,10 @@ Modules:
   adam      -- Adam update, fused BF16 step and the teacher/student fitting step
   frustum   -- pinhole visibility of primitive centres
   schedule  -- the camera k-NN learning-rate heuristic and the cosine LR schedule
+  raster    -- front-to-back alpha compositing of the primitives (the colours' consumer)
 
 Parity pins: every function here is checked in ``tests/test_oracle_*.py``
 against closed forms, special cases that reduce to textbook or library
 routines, invariances and central finite differences.
 """
-from . import adam, frustum, nasgabor, schedule, sh  # noqa: F401
+from . import adam, frustum, nasgabor, raster, schedule, sh  # noqa: F401
