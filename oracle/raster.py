@@ -95,14 +95,12 @@ def render(means, scales, quats, opacity, colours, cam, width, height, pixels=No
     margin = np.full(len(pixels), np.inf)
     for k, (i, j) in enumerate(pixels):
         alpha, _ = _alphas(i + 0.5, j + 0.5, mean2, sigma2, opacity)
+        if np.any(valid):
+            margin[k] = np.min(np.abs(alpha[valid] - ALPHA_MIN) / ALPHA_MIN)
         T = 1.0
-        for n in order_all:
-            if not valid[n]:
-                continue
+        # the primitives that pass P1 and P3 at this pixel, in the P4 order
+        for n in order_all[valid[order_all] & (alpha[order_all] >= ALPHA_MIN)]:
             a = alpha[n]
-            margin[k] = min(margin[k], abs(a - ALPHA_MIN) / ALPHA_MIN)
-            if a < ALPHA_MIN:
-                continue
             test = T * (1.0 - a)
             margin[k] = min(margin[k], abs(test - T_MIN) / T_MIN)
             if test < T_MIN:
@@ -130,9 +128,7 @@ def render_backward(means, scales, quats, opacity, colours, cam, width, height, 
         for i in range(width):
             alpha, rho = _alphas(i + 0.5, j + 0.5, mean2, sigma2, opacity)
             kept, T = [], 1.0
-            for n in order_all:
-                if not valid[n] or alpha[n] < ALPHA_MIN:
-                    continue
+            for n in order_all[valid[order_all] & (alpha[order_all] >= ALPHA_MIN)]:
                 test = T * (1.0 - alpha[n])
                 if test < T_MIN:
                     break
