@@ -386,6 +386,60 @@ nasg_status sh_eval_bwd(int32_t degree, int64_t n, const float* coeffs, const fl
 nasg_status nasg_math_probe(int32_t fn, const float* x, float* y, float* y2, int64_t n, void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Alpha compositing of the primitives (the consumer of their colours)        */
+/* ------------------------------------------------------------------------- */
+
+/* Pinhole camera of the compositing calls. */
+typedef struct nasg_raster_camera {
+  float rot[9];          /* world -> camera rotation, row-major, rows (right, up, forward)  */
+  float centre[3];       /* camera centre (world)                                            */
+  float fx, fy, cx, cy;  /* focal lengths and principal point, pixels; image y grows downward */
+  float near_z;          /* primitives with camera depth <= near_z are not drawn             */
+  int32_t width, height; /* image size, 1..16384                                             */
+} nasg_raster_camera;
+
+/* Device workspace bytes for n primitives, a width x height image and room for
+ * max_pairs (tile, primitive) pairs; 0 if out of range. */
+size_t nasg_raster_workspace_bytes(int64_t n, int32_t width, int32_t height, int64_t max_pairs);
+
+/*
+ * Front-to-back compositing of the primitives into an image (Sec. 3.1:
+ * C = sum_i T_i alpha_i c_i, alpha_i = sigma_i rho_i, T_i = prod_{j<i}(1 - alpha_j)),
+ * with the projection and rules of the Gaussian-splatting rasterizer the paper
+ * builds on: p = R (mu - centre), x = cx + fx p_x/p_z, y = cy - fy p_y/p_z, pixel
+ * (i, j) sampled at (i + 0.5, j + 0.5); rho = exp(-q/2) of the EWA-projected
+ * covariance J R Sigma R^T J^T + 0.3 I, Sigma = Rq diag(s^2) Rq^T;
+ * alpha = min(0.99, sigma rho), counted iff alpha >= 1/255; order by p_z (ties by
+ * index); a pixel stops before the contribution that would take T below 1e-4.
+ *   means [n][3], scales [n][3] (activated, > 0), quats [n][4] (w, x, y, z; any norm),
+ *   opacity [n] (sigma in (0, 1)), colours [n][3]: device f32.
+ *   image  device [height][width][3] f32 output; final_t device [height][width] f32
+ *          output (transmittance left at each pixel).
+ *   workspace: device, 256-byte aligned, >= nasg_raster_workspace_bytes(n, w, h,
+ *          max_pairs); it keeps the forward's state for nasg_raster_backward.
+ *   n_pairs: nullable host output, the number of (tile, primitive) pairs.
+ * Synchronises the stream once (to size the sort). NASG_ERR_CAPACITY when the
+ * pairs exceed max_pairs (n_pairs still reports the count); n < 2^31.
+ */
+nasg_status nasg_raster_forward(int64_t n, const float* means, const float* scales, const float* quats,
+                                const float* opacity, const float* colours, const nasg_raster_camera* camera,
+                                float* image, float* final_t, int64_t max_pairs, void* workspace,
+                                size_t workspace_bytes, int64_t* n_pairs, void* stream);
+
+/*
+ * Gradients of <g_image, image> of the last nasg_raster_forward with this
+ * workspace (same n, colours, camera, max_pairs) wrt the colours and the
+ * opacities: g_colours [n][3] and g_opacity [n] (device f32, overwritten):
+ *   dC/dc_i = alpha_i T_i,  dC/dalpha_i = c_i T_i - (sum_{later j} c_j alpha_j T_j)/(1 - alpha_i),
+ *   dalpha_i/dsigma_i = rho_i where alpha_i < 0.99.
+ * final_t: the forward's output; g_image device [height][width][3] f32. Sums over
+ * pixels use float atomics (the summation order is not fixed).
+ */
+nasg_status nasg_raster_backward(int64_t n, const float* colours, const nasg_raster_camera* camera,
+                                 const float* final_t, const float* g_image, float* g_colours, float* g_opacity,
+                                 int64_t max_pairs, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------- */
 /* Learning-rate rules (host side, no device work)                            */
 /* ------------------------------------------------------------------------- */
 

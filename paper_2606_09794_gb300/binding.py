@@ -112,6 +112,19 @@ _decl("nasg_frustum_compact", [_i64, _vp, _P(ctypes.c_float), _P(ctypes.c_float)
                                _vp, _vp, _vp, ctypes.c_size_t, _vp])
 
 
+class NasgRasterCamera(ctypes.Structure):
+    _fields_ = [("rot", ctypes.c_float * 9), ("centre", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("near_z", ctypes.c_float),
+                ("width", _i32), ("height", _i32)]
+
+
+_decl("nasg_raster_workspace_bytes", [_i64, _i32, _i32, _i64], ctypes.c_size_t)
+_decl("nasg_raster_forward", [_i64, _vp, _vp, _vp, _vp, _vp, _P(NasgRasterCamera), _vp, _vp, _i64, _vp,
+                              ctypes.c_size_t, _P(_i64), _vp])
+_decl("nasg_raster_backward", [_i64, _vp, _P(NasgRasterCamera), _vp, _vp, _vp, _vp, _i64, _vp, ctypes.c_size_t,
+                               _vp])
+
+
 class NasgError(RuntimeError):
     def __init__(self, status: int, where: str):
         msg = lib.nasg_status_string(status).decode()
@@ -538,3 +551,60 @@ class ShEval(torch.autograd.Function):
         g_coeffs, g_means = sh_eval_bwd(coeffs, means, cam_t, g_rgb.contiguous(), degree,
                                         want_means=ctx.needs_input_grad[1])
         return g_coeffs, g_means, None, None
+
+
+def raster_camera(rot, centre, width, height, fx, fy=None, cx=None, cy=None, near_z=0.2):
+    """Pinhole camera for the compositing calls (rot: world->camera rows right, up, forward)."""
+    import numpy as np
+    r = np.asarray(rot, dtype=np.float32).reshape(9)
+    c = np.asarray(centre, dtype=np.float32).reshape(3)
+    return NasgRasterCamera((ctypes.c_float * 9)(*r.tolist()), (ctypes.c_float * 3)(*c.tolist()), float(fx),
+                            float(fx if fy is None else fy), float(0.5 * width if cx is None else cx),
+                            float(0.5 * height if cy is None else cy), float(near_z), int(width), int(height))
+
+
+class Raster:
+    """Front-to-back compositing of primitives (see include/nasgabor.h) with a
+    workspace sized for `max_pairs` (tile, primitive) pairs; forward keeps the
+    state that backward reuses."""
+
+    def __init__(self, n, camera, max_pairs, device=None):
+        self.n = int(n)
+        self.camera = camera
+        self.max_pairs = int(max_pairs)
+        nbytes = lib.nasg_raster_workspace_bytes(self.n, camera.width, camera.height, self.max_pairs)
+        if nbytes == 0:
+            raise ValueError("raster workspace: arguments out of range")
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=device or "cuda")
+        self.n_pairs = None
+
+    def forward(self, means, scales, quats, opacity, colours, image=None, final_t=None, stream=None):
+        h, w = self.camera.height, self.camera.width
+        dev = means.device
+        for t, nm in ((means, "means"), (scales, "scales"), (quats, "quats"), (opacity, "opacity"),
+                      (colours, "colours")):
+            _cuda(t, nm, torch.float32)
+        if image is None:
+            image = torch.empty((h, w, 3), device=dev, dtype=torch.float32)
+        if final_t is None:
+            final_t = torch.empty((h, w), device=dev, dtype=torch.float32)
+        pairs = _i64(0)
+        _check(lib.nasg_raster_forward(self.n, _ptr(means), _ptr(scales), _ptr(quats), _ptr(opacity), _ptr(colours),
+                                       ctypes.byref(self.camera), _ptr(image), _ptr(final_t), self.max_pairs,
+                                       _ptr(self.workspace), self.workspace.numel(), ctypes.byref(pairs),
+                                       _stream(stream)), "nasg_raster_forward")
+        self.n_pairs = pairs.value
+        return image, final_t
+
+    def backward(self, colours, final_t, g_image, g_colours=None, g_opacity=None, stream=None):
+        dev = colours.device
+        _cuda(g_image, "g_image", torch.float32)
+        if g_colours is None:
+            g_colours = torch.empty((self.n, 3), device=dev, dtype=torch.float32)
+        if g_opacity is None:
+            g_opacity = torch.empty((self.n,), device=dev, dtype=torch.float32)
+        _check(lib.nasg_raster_backward(self.n, _ptr(colours), ctypes.byref(self.camera), _ptr(final_t),
+                                        _ptr(g_image), _ptr(g_colours), _ptr(g_opacity), self.max_pairs,
+                                        _ptr(self.workspace), self.workspace.numel(), _stream(stream)),
+               "nasg_raster_backward")
+        return g_colours, g_opacity

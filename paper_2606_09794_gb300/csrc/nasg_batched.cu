@@ -119,7 +119,9 @@ __device__ __forceinline__ EvalArgs scene_args(const SceneDev& sc, const BatchAr
   return a;
 }
 
-template <int FRAME, typename T>
+// FLAGS: kFlagsDefault (raw activations, approximate normalisation) or
+// kFlagsRuntime (modes read from the arguments).
+template <int FRAME, typename T, int FLAGS>
 __global__ void __launch_bounds__(256, 2) batched_kernel(const BatchArgs b) {
   constexpr int P = FrameTraits<FRAME>::P;
   __shared__ SceneDev sd[kMaxScenes];
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(256, 2) batched_kernel(const BatchArgs b) {
     for (int j = 0; j < b.sub_tiles; ++j) {
       const int64_t prim = base + int64_t(j) * tp + local;
       fetch_scene_item<T, P>(sc, prim + tp, l0, j + 1 < b.sub_tiles, nxt);
-      eval_item<FRAME, T, int64_t, kFwdBwd, false, kFlagsRuntime>(a, cur, prim, l0);
+      eval_item<FRAME, T, int64_t, kFwdBwd, false, FLAGS>(a, cur, prim, l0);
       cur = nxt;
     }
     if (b.dynamic) {
@@ -262,7 +264,8 @@ extern "C" nasg_status nasgabor_batched_prepare(const nasg_scene* scenes, int32_
 namespace nasg {
 template <int FRAME, typename T>
 static nasg_status launch_batched(const BatchArgs& b, int blocks_per_sm, cudaStream_t s) {
-  auto k = batched_kernel<FRAME, T>;
+  const bool dflt = b.identity == 0 && b.normalised != 0 && b.exact == 0;
+  auto k = dflt ? batched_kernel<FRAME, T, kFlagsDefault> : batched_kernel<FRAME, T, kFlagsRuntime>;
   int fit = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k, 256, 0) != cudaSuccess || fit < 1) fit = 1;
   const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : fit;

@@ -70,6 +70,9 @@ __device__ __forceinline__ void load_pair(const float* planes, int64_t n, int L,
   }
 }
 
+// EXACT: exact normalisation, a compile-time choice so that the approximate
+// (default) mode carries none of its code.
+template <bool EXACT>
 __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
   __shared__ float block_sum[kFitBlock / 32];
   const int S = 1 << s.slice_log2;
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
         const int j = min(base + tk, s.n_dirs - 1);
         const P2 d[3] = {p2(__ldg(s.dirs + 3 * j)), p2(__ldg(s.dirs + 3 * j + 1)), p2(__ldg(s.dirs + 3 * j + 2))};
         LobePartials<P2> pd;
-        const P2 Gt = lobe<false>(d, tqf.x, tqf.z, tact.lam, tact.a, tact.k, s.normalised != 0, s.exact != 0, &pd);
+        const P2 Gt = lobe<false>(d, tqf.x, tqf.z, tact.lam, tact.a, tact.k, s.normalised != 0, EXACT, &pd);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const P2 wg = tact.w[c] * Gt;
@@ -144,7 +147,7 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
         const float dx = __ldg(s.dirs + 3 * j), dy = __ldg(s.dirs + 3 * j + 1), dz = __ldg(s.dirs + 3 * j + 2);
         const P2 d[3] = {p2(dx), p2(dy), p2(dz)};
         LobePartials<P2> pd;
-        const P2 Gs = lobe<true>(d, qf.x, qf.z, act.lam, act.a, act.k, s.normalised != 0, s.exact != 0, &pd);
+        const P2 Gs = lobe<true>(d, qf.x, qf.z, act.lam, act.a, act.k, s.normalised != 0, EXACT, &pd);
         float col[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -317,14 +320,15 @@ extern "C" nasg_status nasgabor_fit_step(const nasg_desc* desc, const nasg_train
   a.normalised = desc->norm_mode != NASG_NORM_NONE;
   a.exact = desc->norm_mode == NASG_NORM_EXACT;
   a.partials = static_cast<float*>(workspace);
+  auto k = a.exact ? fit_kernel<true> : fit_kernel<false>;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fit_kernel, kFitBlock, 0) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kFitBlock, 0) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   int64_t grid = int64_t(sm_count()) * per_sm;
   const int64_t need = ((desc->n << sl) + kFitBlock - 1) / kFitBlock;
   if (grid > need) grid = need;
   if (grid > kFitMaxGrid) grid = kFitMaxGrid;
-  fit_kernel<<<unsigned(grid), kFitBlock, 0, cs>>>(a);
+  k<<<unsigned(grid), kFitBlock, 0, cs>>>(a);
   fit_loss_kernel<<<1, 256, 0, cs>>>(a.partials, int(grid), double(desc->n) * double(n_dirs) * 3.0, loss);
   return check_launch();
 }
