@@ -37,6 +37,7 @@ if ROOT not in sys.path:
 N_PRIMS = 1_000_000
 N_LOBES = 8
 SEED = 1002
+E2E_CHUNK = 131072
 METRIC = "primitives*lobes/s fwd+bwd (fused BF16-parameter NASGabor)"
 UNIT = "primitive-lobes/s"
 FALLBACK_HBM_GBS = 6800.0
@@ -297,7 +298,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paths", action="store_true")
-    ap.add_argument("--case", choices=["scene_step", "batched", "fit"], default=None,
+    ap.add_argument("--case", choices=["scene_step", "batched", "fit", "frame"], default=None,
                     help="run only this secondary measurement (at --case-n primitives) and print its JSON")
     ap.add_argument("--case-n", type=int, default=None)
     ap.add_argument("--case-steps", type=int, default=None)
@@ -369,21 +370,17 @@ def main():
     traffic = profiled_traffic()
 
     # ---- end to end through the public API with host buffers -------------------
+    # the C-ABI call on HOST (pinned) arrays: the library streams the primitives in
+    # chunks through the device, copies in both directions overlapping the kernel
     pin = dict(params=params.cpu().pin_memory(), c0=c0.cpu().pin_memory(), means=means.cpu().pin_memory(),
                g_rgb=g_rgb.cpu().pin_memory())
     host_out = tuple(torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in out)
-    dev_in = dict(params=torch.empty_like(params), c0=torch.empty_like(c0), means=torch.empty_like(means),
-                  g_rgb=torch.empty_like(g_rgb))
     h2d = sum(t.numel() * t.element_size() for t in pin.values())
     d2h = sum(t.numel() * t.element_size() for t in host_out)
+    host_fused = nb.HostFused(N, L, params.dtype, chunk=E2E_CHUNK, device=dev)
 
     def e2e_step():
-        for k in dev_in:
-            dev_in[k].copy_(pin[k], non_blocking=True)
-        nb.nasgabor_fused_fwd_bwd(dev_in["params"], dev_in["c0"], dev_in["means"], cam, dev_in["g_rgb"], L,
-                                  out=out, stream=stream)
-        for h, d in zip(host_out, out):
-            h.copy_(d, non_blocking=True)
+        host_fused(pin["params"], pin["c0"], pin["means"], cam, pin["g_rgb"], host_out, stream=stream)
 
     e2e_steps = max(5, min(50, args.steps))
     for _ in range(3):
@@ -407,6 +404,7 @@ def main():
         paths["scene_step"] = measure_scene_step(nb, inputs, dev, stream, peak)
         paths["batched"] = measure_batched(nb, inputs, dev, stream, peak)
         paths["fit"] = measure_fit(nb, inputs, dev, stream)
+        paths["frame"] = measure_frame(nb, inputs, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -429,7 +427,8 @@ def main():
                          "algorithmic_bytes_per_launch": alg_bytes},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps},
+                    "steps": e2e_steps, "api": "nasgabor_fused_fwd_bwd_host (host arrays, chunks of "
+                                                f"{E2E_CHUNK} primitives)"},
             "gpu_launches": args.steps,
             "cpu_baseline": cpu,
             "paths": paths,
@@ -455,6 +454,8 @@ def run_case(args):
         kw["n"] = args.case_n
     if args.case == "scene_step":
         res = measure_scene_step(nb, inputs, dev, stream, peak, **kw)
+    elif args.case == "frame":
+        res = measure_frame(nb, inputs, dev, stream, **kw)
     elif args.case == "batched":
         res = measure_batched(nb, inputs, dev, stream, peak, **({"n_scenes": args.case_n} if args.case_n else {}))
     else:
@@ -643,6 +644,73 @@ def measure_fit(nb, inputs, dev, stream, n=2_000_000, ls=16, lt=4, steps=200, n_
             "lobe_evaluations_per_s": evals / (ms * 1e-3),
             "note": "compute-bound; the final-MSE agreement with the oracle's replay is checked on a sample in "
                     "tests/test_gpu_fit.py"}
+
+
+def measure_frame(nb, inputs, dev, stream, n=1_000_000, L=8, width=1920, height=1080, seed=1006, reps=10):
+    """One training frame with a real upstream gradient: NASGabor colours of all
+    primitives at the camera (BF16 parameters), compositing into a 1920 x 1080 image,
+    the L2 loss gradient against a target image, the compositing backward (dL/dcolour),
+    and the fused forward+backward+Adam step driven by that gradient."""
+    import numpy as np
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    pc = inputs.device_point_cloud(n, L, seed, dev)
+    st = nb.TrainState(pc["params"], pc["c0"])
+    means = (torch.rand((n, 3), device=dev, generator=g) * 3.0 - 1.5).contiguous()
+    scales = torch.exp(torch.rand((n, 3), device=dev, generator=g) * 2.0 - 5.5)
+    quats = torch.randn((n, 4), device=dev, generator=g)
+    opacity = torch.rand(n, device=dev, generator=g) * 0.9 + 0.05
+    target = torch.rand((height, width, 3), device=dev, generator=g)
+    cam_c = (0.0, 0.0, -4.0)
+    cam = nb.raster_camera(np.eye(3), cam_c, width, height, 0.5 * width / 0.6)
+    r = nb.Raster(n, cam, 1 << 26)
+    rgb = torch.empty((n, 3), device=dev)
+    scale = 2.0 / target.numel()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+
+    def frame(t, record=False):
+        if record:
+            ev[0].record(stream)
+        nb.nasgabor_eval_fwd(st.params_bf16, st.c0_bf16, means, cam_c, L, rgb=rgb, stream=stream)
+        if record:
+            ev[1].record(stream)
+        img, T = r.forward(means, scales, quats, opacity, rgb, stream=stream)
+        if record:
+            ev[2].record(stream)
+        g_img = (img - target).mul_(scale)
+        if record:
+            ev[3].record(stream)
+        gc, _ = r.backward(rgb, T, g_img, stream=stream)
+        if record:
+            ev[4].record(stream)
+        nb.nasgabor_fused_step(st, means, cam_c, gc, L, t, stream=stream)
+        if record:
+            ev[5].record(stream)
+
+    for t in range(1, 4):
+        frame(t)
+    torch.cuda.synchronize(dev)
+    stages = np.zeros(5)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for t in range(4, 4 + reps):
+        frame(t)
+    e1.record(stream)
+    e1.synchronize()
+    total = e0.elapsed_time(e1) / reps
+    for t in range(4 + reps, 4 + 2 * reps):
+        frame(t, record=True)
+        ev[5].synchronize()
+        stages += [ev[k].elapsed_time(ev[k + 1]) for k in range(5)]
+    stages /= reps
+    return {"workload": f"training frame: N={n} primitives, L={L} BF16 lobes, {width}x{height} image, "
+                        "colours -> compositing -> L2 loss gradient -> compositing backward -> fused step",
+            "ms_per_frame": total, "pairs": r.n_pairs,
+            "stage_ms": {"colours": stages[0], "composite_fwd": stages[1], "loss_grad": stages[2],
+                         "composite_bwd": stages[3], "fused_step": stages[4]},
+            "note": "the compositing forward synchronises once to size its sort"}
 
 
 if __name__ == "__main__":

@@ -386,6 +386,30 @@ nasg_status sh_eval_bwd(int32_t degree, int64_t n, const float* coeffs, const fl
 nasg_status nasg_math_probe(int32_t fn, const float* x, float* y, float* y2, int64_t n, void* stream);
 
 /* ------------------------------------------------------------------------- */
+/* Host-resident data                                                         */
+/* ------------------------------------------------------------------------- */
+
+/* Device workspace bytes of nasgabor_fused_fwd_bwd_host for desc and chunk
+ * (a multiple of 8, 8..2^26 primitives); 0 if invalid. */
+size_t nasgabor_fused_host_workspace_bytes(const nasg_desc* desc, int64_t chunk);
+
+/*
+ * nasgabor_fused_fwd_bwd with every array in HOST memory (the same layouts;
+ * page-locked memory lets the copies run asynchronously): the primitives flow
+ * in chunks of `chunk` through three device slots in `workspace` (device,
+ * 256-byte aligned, >= nasgabor_fused_host_workspace_bytes), the copies in
+ * both directions overlapping the kernel of the neighbouring chunks on two
+ * internal copy streams (created once per device). Ordered after the work
+ * already queued on `stream`; when `stream` reaches the point after this call,
+ * the outputs are in host memory. desc->accumulate must be 0. Errors as
+ * nasgabor_fused_fwd_bwd, plus NASG_ERR_RANGE for a bad chunk or workspace.
+ */
+nasg_status nasgabor_fused_fwd_bwd_host(const nasg_desc* desc, const void* params, const void* c0,
+                                        const float* means, const float* cam, const float* g_rgb, float* rgb,
+                                        float* g_params, float* g_c0, float* g_means, int64_t chunk,
+                                        void* workspace, size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------- */
 /* Alpha compositing of the primitives (the consumer of their colours)        */
 /* ------------------------------------------------------------------------- */
 

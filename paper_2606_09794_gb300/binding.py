@@ -118,6 +118,9 @@ class NasgRasterCamera(ctypes.Structure):
                 ("width", _i32), ("height", _i32)]
 
 
+_decl("nasgabor_fused_host_workspace_bytes", [_P(NasgDesc), _i64], ctypes.c_size_t)
+_decl("nasgabor_fused_fwd_bwd_host", [_P(NasgDesc), _vp, _vp, _vp, _P(ctypes.c_float), _vp, _vp, _vp, _vp, _vp,
+                                      _i64, _vp, ctypes.c_size_t, _vp])
 _decl("nasg_raster_workspace_bytes", [_i64, _i32, _i32, _i64], ctypes.c_size_t)
 _decl("nasg_raster_forward", [_i64, _vp, _vp, _vp, _vp, _vp, _P(NasgRasterCamera), _vp, _vp, _i64, _vp,
                               ctypes.c_size_t, _P(_i64), _vp])
@@ -608,3 +611,42 @@ class Raster:
                                         _ptr(self.workspace), self.workspace.numel(), _stream(stream)),
                "nasg_raster_backward")
         return g_colours, g_opacity
+
+
+def _host(t, name, dtype=None):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host (CPU) tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class HostFused:
+    """Fused forward+backward over HOST tensors (pinned for asynchronous copies),
+    streamed through a device workspace in chunks; see nasgabor_fused_fwd_bwd_host."""
+
+    def __init__(self, n, n_lobes, param_dtype=torch.bfloat16, chunk=131072, frame_mode="quat", norm_mode="approx",
+                 act_mode="raw", family="nasgabor", device=None):
+        self.desc = make_desc(n, n_lobes, frame_mode, param_dtype, norm_mode, act_mode, family=family)
+        self.chunk = int(chunk)
+        nbytes = lib.nasgabor_fused_host_workspace_bytes(ctypes.byref(self.desc), self.chunk)
+        if nbytes == 0:
+            raise ValueError("host fused workspace: arguments out of range")
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=device or "cuda")
+
+    def __call__(self, params, c0, means, cam, g_rgb, out, stream=None):
+        rgb, g_params, g_c0, g_means = out
+        for t, nm in ((params, "params"), (c0, "c0")):
+            _host(t, nm)
+        for t, nm in ((means, "means"), (g_rgb, "g_rgb"), (rgb, "rgb"), (g_params, "g_params"), (g_c0, "g_c0")):
+            _host(t, nm, torch.float32)
+        if g_means is not None:
+            _host(g_means, "g_means", torch.float32)
+        _check(lib.nasgabor_fused_fwd_bwd_host(ctypes.byref(self.desc), _ptr(params), _ptr(c0), _ptr(means),
+                                               _cam(cam), _ptr(g_rgb), _ptr(rgb), _ptr(g_params), _ptr(g_c0),
+                                               _ptr(g_means), self.chunk, _ptr(self.workspace),
+                                               self.workspace.numel(), _stream(stream)),
+               "nasgabor_fused_fwd_bwd_host")
+        return out

@@ -18,14 +18,16 @@
 //
 // Pipeline (all on one stream): per-primitive projection and footprint (a square
 // holding every pixel centre where alpha >= 1/255 can hold, so the image does not
-// depend on the binning), exclusive scan of the tiles each primitive touches,
-// emission of (tile << 32 | depth bits, index) pairs, a stable LSD radix sort
-// (8-bit digits) of the pairs, per-tile ranges, then one block per 16 x 16 tile:
-// batches of 256 primitives staged in shared memory, one thread per pixel.
-// The backward walks each pixel's list back to front (T recovered by division),
-// reduces the per-primitive gradients over the warp and adds them with one
-// atomic per warp and primitive. The forward reads the pair total once on the
-// host to size the sort (one stream synchronisation).
+// depend on the binning); a stable LSD radix sort (8-bit digits, written here) of
+// the primitives by depth; an exclusive scan, in that order, of the tiles each
+// primitive touches; emission of (tile, index) pairs in depth order; a stable
+// radix sort of the pairs by tile alone (so each tile's list stays in depth order,
+// ties by index); per-tile ranges; then one block per 16 x 16 tile: batches of 256
+// primitives staged in shared memory, one thread per pixel. The backward walks
+// each pixel's list back to front (T recovered by division), reduces the four
+// per-primitive gradients over the warp in six shuffles and adds them with one
+// atomic per warp, value and primitive. The forward reads the pair total once on
+// the host to size the pair sort (one stream synchronisation).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -55,8 +57,8 @@ struct Cam {
 
 // Workspace layout (byte offsets, each 256-aligned), from n, tiles, pixels and the pair capacity.
 struct Layout {
-  size_t mean, conic, depth, rect, touched, offsets, scan_blocks, keys0, keys1, vals0, vals1, hist, ranges,
-      ncontrib, header, total;
+  size_t mean, conic, depth, rect, touched, offsets, scan_blocks, dkeys0, dkeys1, order0, order1, keys0, keys1, vals0,
+      vals1, hist, ranges, ncontrib, header, total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -66,7 +68,8 @@ inline Layout layout(int64_t n, int64_t tiles, int64_t pixels, int64_t cap) {
   size_t o = 0;
   auto take = [&](size_t bytes) { const size_t at = o; o = align256(o + bytes); return at; };
   const int64_t nscan = (n + kScanChunk - 1) / kScanChunk;
-  const int64_t sblocks = (cap + kSortChunk - 1) / kSortChunk;
+  const int64_t big = cap > n ? cap : n;
+  const int64_t sblocks = (big + kSortChunk - 1) / kSortChunk;
   const int64_t hist = 256 * (sblocks > 0 ? sblocks : 1);
   L.header = take(256);
   L.mean = take(size_t(n) * sizeof(float2));
@@ -76,8 +79,12 @@ inline Layout layout(int64_t n, int64_t tiles, int64_t pixels, int64_t cap) {
   L.touched = take(size_t(n) * sizeof(uint32_t));
   L.offsets = take(size_t(n) * sizeof(uint32_t));
   L.scan_blocks = take(size_t(nscan + (hist + kScanChunk - 1) / kScanChunk + 2) * sizeof(uint32_t));
-  L.keys0 = take(size_t(cap) * sizeof(uint64_t));
-  L.keys1 = take(size_t(cap) * sizeof(uint64_t));
+  L.dkeys0 = take(size_t(n) * sizeof(uint32_t));
+  L.dkeys1 = take(size_t(n) * sizeof(uint32_t));
+  L.order0 = take(size_t(n) * sizeof(uint32_t));
+  L.order1 = take(size_t(n) * sizeof(uint32_t));
+  L.keys0 = take(size_t(cap) * sizeof(uint32_t));
+  L.keys1 = take(size_t(cap) * sizeof(uint32_t));
   L.vals0 = take(size_t(cap) * sizeof(uint32_t));
   L.vals1 = take(size_t(cap) * sizeof(uint32_t));
   L.hist = take(size_t(hist) * sizeof(uint32_t));
@@ -94,11 +101,11 @@ struct Header {
   unsigned long long pairs64;
 };
 
-// Radix passes over the (tile, depth) keys: 4 for the depth bits, then the tile bits.
+// Radix passes over the pairs' tile keys (8 bits each).
 inline int sort_passes(int64_t tiles) {
   int tile_bits = 0;
   while ((int64_t(1) << tile_bits) < tiles) ++tile_bits;
-  return 4 + (tile_bits + 7) / 8;
+  return tile_bits > 0 ? (tile_bits + 7) / 8 : 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -108,7 +115,8 @@ inline int sort_passes(int64_t tiles) {
 __global__ void project_kernel(int64_t n, const float* __restrict__ means, const float* __restrict__ scales,
                                const float* __restrict__ quats, const float* __restrict__ opacity, Cam cam,
                                float2* __restrict__ mean2, float4* __restrict__ conic, float* __restrict__ depth,
-                               int4* __restrict__ rect, uint32_t* __restrict__ touched) {
+                               int4* __restrict__ rect, uint32_t* __restrict__ touched, uint32_t* __restrict__ dkey,
+                               uint32_t* __restrict__ order) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t count = 0;
@@ -179,6 +187,10 @@ __global__ void project_kernel(int64_t n, const float* __restrict__ means, const
   }
   rect[i] = rc;
   touched[i] = count;
+  // depth sort key: the bits of a positive float order like its value; primitives
+  // that draw nothing go last
+  dkey[i] = count ? __float_as_uint(pz) : 0xffffffffu;
+  order[i] = uint32_t(i);
 }
 
 // ---------------------------------------------------------------------------
@@ -276,24 +288,32 @@ static void exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, uint32_
 // Pair emission, radix sort, tile ranges
 // ---------------------------------------------------------------------------
 
-__global__ void emit_kernel(int64_t n, const int4* __restrict__ rect, const float* __restrict__ depth,
-                            const uint32_t* __restrict__ offsets, int tiles_x, uint64_t* __restrict__ keys,
+// touched counts in depth order (for the scan that places each primitive's pairs)
+__global__ void gather_counts_kernel(int64_t n, const uint32_t* __restrict__ order,
+                                     const uint32_t* __restrict__ touched, uint32_t* __restrict__ out) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = touched[order[k]];
+}
+
+// pairs (tile, primitive) of the k-th primitive in depth order, at offsets[k]
+__global__ void emit_kernel(int64_t n, const uint32_t* __restrict__ order, const int4* __restrict__ rect,
+                            const uint32_t* __restrict__ offsets, int tiles_x, uint32_t* __restrict__ keys,
                             uint32_t* __restrict__ vals) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const uint32_t i = order[k];
   const int4 r = rect[i];
   if (r.y < r.x) return;
-  uint32_t o = offsets[i];
-  const uint64_t d = uint64_t(__float_as_uint(depth[i]));  // positive: bit order = value order
+  uint32_t o = offsets[k];
   for (int ty = r.z; ty <= r.w; ++ty)
     for (int tx = r.x; tx <= r.y; ++tx) {
-      keys[o] = (uint64_t(uint32_t(ty * tiles_x + tx)) << 32) | d;
-      vals[o] = uint32_t(i);
+      keys[o] = uint32_t(ty * tiles_x + tx);
+      vals[o] = i;
       ++o;
     }
 }
 
-__global__ void radix_hist_kernel(const uint64_t* __restrict__ keys, int64_t m, int shift,
+__global__ void radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t m, int shift,
                                   uint32_t* __restrict__ hist, int nblocks) {
   __shared__ uint32_t h[256];
   h[threadIdx.x] = 0;
@@ -310,8 +330,8 @@ __global__ void radix_hist_kernel(const uint64_t* __restrict__ keys, int64_t m, 
 
 // Stable scatter of one block's chunk: rounds of 256 keys in order; within a
 // round, keys with equal digits keep thread order (warp match + per-warp counts).
-__global__ void radix_scatter_kernel(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                                     uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t m, int shift,
+__global__ void radix_scatter_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t m, int shift,
                                      const uint32_t* __restrict__ offs, int nblocks) {
   __shared__ uint32_t run[256];
   __shared__ uint32_t wcnt[kBlock / 32][256];
@@ -326,7 +346,7 @@ __global__ void radix_scatter_kernel(const uint64_t* __restrict__ kin, const uin
     for (int w = 0; w < kBlock / 32; ++w) wcnt[w][threadIdx.x] = 0;
     __syncthreads();
     const bool ok = j < m;
-    uint64_t key = 0;
+    uint32_t key = 0;
     uint32_t val = 0, d = 256;
     if (ok) {
       key = kin[j];
@@ -352,12 +372,30 @@ __global__ void radix_scatter_kernel(const uint64_t* __restrict__ kin, const uin
   }
 }
 
-__global__ void ranges_kernel(const uint64_t* __restrict__ keys, int64_t m, uint2* __restrict__ ranges) {
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t m, uint2* __restrict__ ranges) {
   const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= m) return;
-  const uint32_t t = uint32_t(keys[j] >> 32);
-  if (j == 0 || uint32_t(keys[j - 1] >> 32) != t) ranges[t].x = uint32_t(j);
-  if (j == m - 1 || uint32_t(keys[j + 1] >> 32) != t) ranges[t].y = uint32_t(j + 1);
+  const uint32_t t = keys[j];
+  if (j == 0 || keys[j - 1] != t) ranges[t].x = uint32_t(j);
+  if (j == m - 1 || keys[j + 1] != t) ranges[t].y = uint32_t(j + 1);
+}
+
+// Stable LSD radix sort of (key, value) pairs over the given 8-bit digits; returns
+// the buffer index (0 or 1) that holds the result.
+static int radix_sort(uint32_t* keys[2], uint32_t* vals[2], int64_t m, int passes, uint32_t* hist, uint32_t* sums,
+                      cudaStream_t s) {
+  int cur = 0;
+  if (m <= 0) return cur;
+  const int nblocks = int((m + kSortChunk - 1) / kSortChunk);
+  for (int ps = 0; ps < passes; ++ps) {
+    const int shift = 8 * ps;
+    radix_hist_kernel<<<nblocks, kBlock, 0, s>>>(keys[cur], m, shift, hist, nblocks);
+    exclusive_scan(hist, hist, int64_t(256) * nblocks, sums, nullptr, s);
+    radix_scatter_kernel<<<nblocks, kBlock, 0, s>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], m, shift,
+                                                    hist, nblocks);
+    cur = 1 - cur;
+  }
+  return cur;
 }
 
 // ---------------------------------------------------------------------------
@@ -433,12 +471,6 @@ __global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(
   }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 __global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(
     Cam cam, const uint2* __restrict__ ranges, const uint32_t* __restrict__ vals, const float2* __restrict__ mean2,
     const float4* __restrict__ conic, const float* __restrict__ colours, const float* __restrict__ final_t,
@@ -466,8 +498,15 @@ __global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(
   }
   float af0 = 0.f, af1 = 0.f, af2 = 0.f;  // sum over later contributions of c alpha T
   const int lane = threadIdx.x & 31;
-  // batches from the back of the range
-  const uint32_t n = rg.y - rg.x;
+  // batches from the back of the range, starting at the block's furthest last
+  // contribution (entries behind every pixel's stop point contribute nothing)
+  __shared__ uint32_t s_last;
+  if (threadIdx.x == 0) s_last = 0;
+  __syncthreads();
+  const uint32_t wl = __reduce_max_sync(0xffffffffu, last);
+  if (lane == 0) atomicMax(&s_last, wl);
+  __syncthreads();
+  const uint32_t n = s_last;
   for (uint32_t done_cnt = 0; done_cnt < n; done_cnt += kBlock) {
     const uint32_t hi = n - done_cnt;                   // exclusive end (relative)
     const uint32_t lo = hi > uint32_t(kBlock) ? hi - kBlock : 0u;
@@ -504,16 +543,22 @@ __global__ void __launch_bounds__(kTilePixels) render_bwd_kernel(
         T = Tb;
       }
       if (__any_sync(0xffffffffu, a > 0.f)) {
-        gc0 = warp_sum(gc0);
-        gc1 = warp_sum(gc1);
-        gc2 = warp_sum(gc2);
-        go = warp_sum(go);
-        if (lane == 0) {
+        // four sums over the warp in six shuffles: halves exchange two values, then
+        // quarters one, then a plain butterfly; lane 8 q (q = 0..3) ends with sum q
+        const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+        float k0 = hi16 ? gc2 : gc0, k1 = hi16 ? go : gc1;
+        const float s0 = hi16 ? gc0 : gc2, s1 = hi16 ? gc1 : go;
+        k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+        k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+        float v = hi8 ? k1 : k0;
+        v += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        if ((lane & 7) == 0) {
           const uint32_t id = s_id[k];
-          atomicAdd(g_colours + 3 * id, gc0);
-          atomicAdd(g_colours + 3 * id + 1, gc1);
-          atomicAdd(g_colours + 3 * id + 2, gc2);
-          atomicAdd(g_opacity + id, go);
+          const int q = lane >> 3;  // 0, 1, 2: colour channel; 3: opacity
+          atomicAdd(q < 3 ? g_colours + 3 * id + q : g_opacity + id, v);
         }
       }
     }
@@ -586,7 +631,9 @@ extern "C" nasg_status nasg_raster_forward(int64_t n, const float* means, const 
   auto* touched = reinterpret_cast<uint32_t*>(ws + L.touched);
   auto* offsets = reinterpret_cast<uint32_t*>(ws + L.offsets);
   auto* sums = reinterpret_cast<uint32_t*>(ws + L.scan_blocks);
-  uint64_t* keys[2] = {reinterpret_cast<uint64_t*>(ws + L.keys0), reinterpret_cast<uint64_t*>(ws + L.keys1)};
+  uint32_t* keys[2] = {reinterpret_cast<uint32_t*>(ws + L.keys0), reinterpret_cast<uint32_t*>(ws + L.keys1)};
+  uint32_t* dkeys[2] = {reinterpret_cast<uint32_t*>(ws + L.dkeys0), reinterpret_cast<uint32_t*>(ws + L.dkeys1)};
+  uint32_t* order[2] = {reinterpret_cast<uint32_t*>(ws + L.order0), reinterpret_cast<uint32_t*>(ws + L.order1)};
   uint32_t* vals[2] = {reinterpret_cast<uint32_t*>(ws + L.vals0), reinterpret_cast<uint32_t*>(ws + L.vals1)};
   auto* hist = reinterpret_cast<uint32_t*>(ws + L.hist);
   auto* ranges = reinterpret_cast<uint2*>(ws + L.ranges);
@@ -595,10 +642,15 @@ extern "C" nasg_status nasg_raster_forward(int64_t n, const float* means, const 
   if (cudaMemsetAsync(hdr, 0, sizeof(Header), s) != cudaSuccess) return check_launch();
   if (cudaMemsetAsync(ranges, 0, size_t(tiles) * sizeof(uint2), s) != cudaSuccess) return check_launch();
   unsigned long long total64 = 0;
+  int dcur = 0;
   if (n > 0) {
     project_kernel<<<unsigned((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, means, scales, quats, opacity, cam,
-                                                                            mean2, con, dep, rect, touched);
-    exclusive_scan(touched, offsets, n, sums, &hdr->pairs, s);
+                                                                            mean2, con, dep, rect, touched, dkeys[0],
+                                                                            order[0]);
+    // primitives by depth (ties by index: the sort is stable), then their tile counts in that order
+    dcur = radix_sort(dkeys, order, n, 4, hist, sums, s);
+    gather_counts_kernel<<<unsigned((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, order[dcur], touched, offsets);
+    exclusive_scan(offsets, offsets, n, sums, &hdr->pairs, s);
     sum64_kernel<<<unsigned(std::min<int64_t>((n + kBlock - 1) / kBlock, 1024)), kBlock, 0, s>>>(touched, n,
                                                                                                  &hdr->pairs64);
     if (cudaMemcpyAsync(&total64, &hdr->pairs64, sizeof(total64), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -611,17 +663,10 @@ extern "C" nasg_status nasg_raster_forward(int64_t n, const float* means, const 
   const int passes = sort_passes(tiles);
   int cur = 0;
   if (total > 0) {
-    emit_kernel<<<unsigned((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, rect, dep, offsets, cam.tx, keys[0],
-                                                                         vals[0]);
-    const int nblocks = int((int64_t(total) + kSortChunk - 1) / kSortChunk);
-    for (int ps = 0; ps < passes; ++ps) {
-      const int shift = 8 * ps;
-      radix_hist_kernel<<<nblocks, kBlock, 0, s>>>(keys[cur], total, shift, hist, nblocks);
-      exclusive_scan(hist, hist, int64_t(256) * nblocks, sums, nullptr, s);
-      radix_scatter_kernel<<<nblocks, kBlock, 0, s>>>(keys[cur], vals[cur], keys[1 - cur], vals[1 - cur], total,
-                                                      shift, hist, nblocks);
-      cur = 1 - cur;
-    }
+    emit_kernel<<<unsigned((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(n, order[dcur], rect, offsets, cam.tx,
+                                                                         keys[0], vals[0]);
+    cur = radix_sort(keys, vals, total, passes, hist, sums, s);
+    if (cur != passes % 2) return NASG_ERR_DEVICE;  // the backward relies on this parity
     ranges_kernel<<<unsigned((total + kBlock - 1) / kBlock), kBlock, 0, s>>>(keys[cur], total, ranges);
   }
   render_fwd_kernel<<<unsigned(tiles), kTilePixels, 0, s>>>(cam, ranges, vals[cur], mean2, con, colours, image,

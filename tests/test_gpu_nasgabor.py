@@ -347,3 +347,25 @@ def test_staged_path_matches_oracle(lib, bf16, n, L):
     torch.testing.assert_close(r[0], f[0], rtol=1e-6, atol=1e-6)
     fg, rg = f[1].cpu().numpy(), r[1].cpu().numpy()
     assert max(rel_l2(rg[p], fg[p]) for p in range(fg.shape[0])) < 1e-6
+
+
+@pytest.mark.parametrize("n,L,chunk,bf16", [(100_003, 8, 16384, True), (4096, 4, 1024, False), (777, 3, 64, True),
+                                            (5000, 8, 8, False)])
+def test_host_resident_fused_matches_device_fused(lib, n, L, chunk, bf16):
+    """Host arrays streamed in chunks through the device (copies overlapping the
+    kernel) give the device-resident fused pass's results."""
+    import torch
+    w = inputs.point_cloud_workload(n, L, 60 + L)
+    params, c0, _, _ = _prepare(w, bf16)
+    means, g_rgb = _dev(w.means), _dev(w.g_rgb)
+    ref = lib.nasgabor_fused_fwd_bwd(params, c0, means, w.cam, g_rgb, L)
+    hp = [params.cpu().pin_memory(), c0.cpu().pin_memory(), means.cpu().pin_memory(), g_rgb.cpu().pin_memory()]
+    out = tuple(torch.empty(t.shape, dtype=torch.float32).pin_memory() for t in ref)
+    hf = lib.HostFused(n, L, params.dtype, chunk=chunk)
+    hf(hp[0], hp[1], hp[2], w.cam, hp[3], out)
+    torch.cuda.synchronize()
+    torch.testing.assert_close(out[0], ref[0].cpu(), rtol=1e-6, atol=1e-6)
+    gp, rp = out[1].numpy(), ref[1].cpu().numpy()
+    assert max(rel_l2(gp[p], rp[p]) for p in range(gp.shape[0])) < 1e-6
+    torch.testing.assert_close(out[2], ref[2].cpu(), rtol=0, atol=0)
+    assert rel_l2(out[3].numpy(), ref[3].cpu().numpy()) < 1e-6
