@@ -297,9 +297,12 @@ typedef struct nasg_batch_plan {
 } nasg_batch_plan;
 
 /* Launch schedule: dynamic (1: tiles from an atomic counter, 0: round-robin),
- * blocks per SM (0: as many as fit), sub_tiles (the k prepare was called with). */
+ * blocks per SM (0: as many as fit), sub_tiles (the k prepare was called with),
+ * staged (1: parameter spans moved into shared memory by bulk copies, four
+ * sub-tiles ahead, for the scenes with even L and 16-byte aligned planes; the
+ * others are loaded directly; 0: every load direct, one sub-tile ahead). */
 typedef struct nasg_batch_tuning {
-  int32_t dynamic, blocks_per_sm, sub_tiles, reserved;
+  int32_t dynamic, blocks_per_sm, sub_tiles, staged;
 } nasg_batch_tuning;
 
 /* Device workspace bytes for a batch of n_scenes (1..NASG_MAX_SCENES); 0 if out of range. */
@@ -327,7 +330,7 @@ nasg_status nasgabor_batched_run(const nasg_batch_plan* plan, const nasg_batch_t
 
 /*
  * Small autotuner: times every schedule (sub_tiles in {1, 2, 4, 8}, static or
- * dynamic, 1 or 2 blocks per SM) on this batch, `reps` runs each, writes the
+ * dynamic, staged or direct, 1 or 2 blocks per SM) on this batch, `reps` runs each, writes the
  * fastest to *best (and its time to *best_ms, nullable) and leaves `workspace`
  * and *plan prepared for it. Runs the batch's kernels (outputs are overwritten).
  */

@@ -67,7 +67,7 @@ class NasgBatchPlan(ctypes.Structure):
 
 
 class NasgBatchTuning(ctypes.Structure):
-    _fields_ = [("dynamic", _i32), ("blocks_per_sm", _i32), ("sub_tiles", _i32), ("reserved", _i32)]
+    _fields_ = [("dynamic", _i32), ("blocks_per_sm", _i32), ("sub_tiles", _i32), ("staged", _i32)]
 
 
 def _decl(name, argtypes, restype=_i32):
@@ -465,7 +465,7 @@ class Batch:
                                              _stream(stream)), "nasgabor_batched_autotune")
         self.tuning = best
         return {"dynamic": best.dynamic, "blocks_per_sm": best.blocks_per_sm, "sub_tiles": best.sub_tiles,
-                "ms": ms.value}
+                "staged": best.staged, "ms": ms.value}
 
 
 def nasgabor_fit_step(state, teacher_params, teacher_c0, teacher_lobes, dirs, n_lobes, step, lr=1e-3, beta1=0.9,

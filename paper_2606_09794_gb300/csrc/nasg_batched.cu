@@ -11,8 +11,11 @@
 // look the scene up in the shared-memory copy of the table, and evaluate the
 // tile with the lobe-pair lanes of the single-scene kernels, fetching each
 // lane's next sub-tile item before computing the current one. No thread waits
-// on another block. The autotuner times the candidate schedules on the caller's
-// own prepared batch and returns the fastest.
+// on another block. A staged variant moves each sub-tile's parameter spans
+// into shared memory with bulk copies, four sub-tiles ahead (one elected
+// producer thread, full/empty mbarriers, every wait bounded), for the scenes
+// whose planes allow it, and loads the rest directly. The autotuner times the
+// candidate schedules on the caller's own prepared batch and returns the fastest.
 #include <algorithm>
 #include <vector>
 
@@ -34,7 +37,7 @@ struct SceneDev {
   float cam[3];
   int32_t n_lobes;
   int32_t slice_log2;
-  int32_t pad;
+  int32_t staged;  // parameter spans may be moved by bulk copies (even L, 16-byte aligned planes)
 };
 
 constexpr int kMaxScenes = NASG_MAX_SCENES;
@@ -178,6 +181,209 @@ struct PlanDev {
   int64_t total_tiles;
 };
 
+
+// ---------------------------------------------------------------------------
+// Staged variant
+// ---------------------------------------------------------------------------
+
+// Stages in flight per block (f32 parameters take twice the space).
+template <typename T>
+constexpr int batch_stages() { return sizeof(T) == 2 ? 4 : 3; }
+constexpr int kMaxBatchStages = 4;
+constexpr uint32_t kUnitEnd = 0xffffffffu;
+
+// Shared-memory metadata of one stage, written by the producer with the unit.
+struct StageMeta {
+  uint32_t unit;     // global sub-tile index, kUnitEnd past the last
+  int32_t scene;     // scene index, -1 for an empty unit
+  int32_t staged;    // bit 0: parameter spans in the stage; bit 1: means and upstream gradients too
+  int32_t count;     // primitives in the unit
+  int64_t p0;        // first primitive of the unit in its scene
+};
+
+// Stage layout: P parameter spans of up to 512 lobes, then up to 256 means and
+// 256 upstream gradients (a sub-tile holds at most 512 lobes: 256/S primitives x
+// L lobes with S >= L/2).
+template <typename T, int P>
+__host__ __device__ inline uint32_t batch_plane_bytes() { return 512u * uint32_t(sizeof(T)); }
+template <typename T, int P>
+__host__ __device__ inline uint32_t batch_stage_bytes() {
+  return (uint32_t(P) * batch_plane_bytes<T, P>() + 2u * 256u * 12u + 127u) & ~127u;
+}
+
+// Producer side: record a unit in a stage and start its copies; returns whether
+// copies were started (the stage then completes when their bytes have landed).
+// A block's units increase, so the scene is found by advancing `sc_i` (the
+// previous unit's scene); a scene's units are its sub-tiles in order, from
+// tile_begin x sub_tiles, so the unit's first primitive needs no division.
+template <typename T, int P>
+__device__ __forceinline__ bool issue_unit(const BatchArgs& b, const SceneDev* sd, uint32_t unit, int& sc_i,
+                                           StageMeta* meta, unsigned char* st, uint64_t* bar) {
+  const int64_t total_units = b.total_tiles * b.sub_tiles;
+  if (int64_t(unit) >= total_units) {
+    meta->unit = kUnitEnd;
+    meta->scene = -1;
+    meta->staged = 0;
+    meta->count = 0;
+    meta->p0 = 0;
+    mbar_arrive(bar);
+    return false;
+  }
+  const int64_t u = int64_t(unit);
+  while (sc_i + 1 < b.n_scenes && sd[sc_i + 1].tile_begin * b.sub_tiles <= u) ++sc_i;
+  const SceneDev& sc = sd[sc_i];
+  const int64_t tp = 256 >> sc.slice_log2;
+  const int64_t p0 = (u - sc.tile_begin * b.sub_tiles) * tp;
+  const int64_t count = sc.n - p0 < tp ? sc.n - p0 : tp;
+  meta->unit = unit;
+  meta->scene = count > 0 ? sc_i : -1;
+  meta->count = count > 0 ? int32_t(count) : 0;
+  meta->p0 = p0;
+  const uint32_t bytes = count > 0 ? uint32_t(count) * uint32_t(sc.n_lobes) * uint32_t(sizeof(T)) : 0u;
+  const bool stage_p = count > 0 && (sc.staged & 1) && (bytes % 16u) == 0u;
+  const bool stage_m = stage_p && (sc.staged & 2) && (count % 4) == 0;  // 12-byte records: 4 per 16 bytes
+  meta->staged = (stage_p ? 1 : 0) | (stage_m ? 2 : 0);
+  if (!stage_p) {
+    mbar_arrive(bar);
+    return false;
+  }
+  const uint32_t mbytes = uint32_t(count) * 12u;
+  mbar_arrive_expect_tx(bar, uint32_t(P) * bytes + (stage_m ? 2u * mbytes : 0u));
+  const T* params = static_cast<const T*>(sc.params);
+  const int64_t NL = sc.n * sc.n_lobes;
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+    bulk_g2s(st + size_t(p) * batch_plane_bytes<T, P>(), params + p * NL + p0 * sc.n_lobes, bytes, bar);
+  if (stage_m) {
+    unsigned char* mu = st + size_t(P) * batch_plane_bytes<T, P>();
+    bulk_g2s(mu, sc.means + 3 * p0, mbytes, bar);
+    bulk_g2s(mu + 256u * 12u, sc.g_rgb + 3 * p0, mbytes, bar);
+  }
+  return true;
+}
+
+template <int FRAME, typename T, int FLAGS>
+__global__ void __launch_bounds__(256, 2) batched_staged_kernel(const BatchArgs b) {
+  constexpr int P = FrameTraits<FRAME>::P;
+  constexpr int NS = batch_stages<T>();
+  using W = typename RawWord<T>::type;
+  __shared__ SceneDev sd[kMaxScenes];
+  __shared__ StageMeta meta[kMaxBatchStages];
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t sbytes = batch_stage_bytes<T, P>();
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * sbytes);
+  uint64_t* empty = full + NS;
+  {
+    const int words = int(b.n_scenes * sizeof(SceneDev) / sizeof(uint32_t));
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(b.table);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(sd);
+    for (int j = threadIdx.x; j < words; j += blockDim.x) dst[j] = src[j];
+  }
+  const uint32_t n_warps = blockDim.x >> 5;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], n_warps);
+    }
+    fence_barrier_init();
+  }
+  __syncthreads();
+  // producer state (thread 0): stages whose copies are in flight and the parity of
+  // the phase each of them completes, for the drain on error
+  uint32_t pending = 0, pend_par = 0;
+  int issue_scene = 0;
+  auto next_unit = [&](uint32_t it) -> uint32_t {
+    return b.dynamic ? atomicAdd(b.counter, 1u) : uint32_t(blockIdx.x + uint64_t(it) * gridDim.x);
+  };
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (issue_unit<T, P>(b, sd, next_unit(s), issue_scene, &meta[s], smem + s * sbytes, &full[s]))
+        pending |= 1u << s;
+  }
+  bool failed = false;
+  int cur_scene = -1;
+  EvalArgs a{};
+  for (uint32_t it = 0;; ++it) {
+    if (threadIdx.x == 0 && it >= 1) {
+      const uint32_t pit = it - 1;
+      const int ps = int(pit % NS);
+      if (mbar_wait(&empty[ps], (pit / NS) & 1u, b.dev_err)) {
+        fence_proxy_async();
+        const uint32_t nit = pit + NS;
+        if (issue_unit<T, P>(b, sd, next_unit(nit), issue_scene, &meta[ps], smem + ps * sbytes, &full[ps])) {
+          pending |= 1u << ps;
+          pend_par = (pend_par & ~(1u << ps)) | (((nit / NS) & 1u) << ps);
+        }
+      } else {
+        failed = true;
+      }
+    }
+    const int s = int(it % NS);
+    const bool arrived = __all_sync(0xffffffffu, mbar_wait(&full[s], (it / NS) & 1u, b.dev_err));
+    if (!arrived) {
+      failed = true;
+      break;  // warp-uniform; the other warps give up on their own waits
+    }
+    if (threadIdx.x == 0) pending &= ~(1u << s);
+    const StageMeta m = meta[s];
+    if (m.unit == kUnitEnd) break;  // block-uniform: every warp reads the same stage
+    RawItem<T, P> r;
+    r.ok = 0;
+    int64_t prim = 0;
+    int l0 = 0;
+    if (m.scene >= 0) {
+      const SceneDev& sc = sd[m.scene];
+      if (m.scene != cur_scene) {  // block-uniform
+        a = scene_args(sc, b);
+        cur_scene = m.scene;
+      }
+      const int local = int(threadIdx.x) >> sc.slice_log2;
+      l0 = 2 * (int(threadIdx.x) & ((1 << sc.slice_log2) - 1));
+      prim = m.p0 + local;
+      if (m.staged & 1) {
+        r.ok = local < m.count;
+        if (r.ok) {
+          r.i = 0;
+          const unsigned char* st = smem + s * sbytes;
+          if (m.staged & 2) {
+            const float* mu = reinterpret_cast<const float*>(st + size_t(P) * batch_plane_bytes<T, P>());
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r.mu[c] = mu[3 * local + c];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r.gc[c] = mu[256 * 3 + 3 * local + c];
+          } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r.mu[c] = __ldg(sc.means + 3 * prim + c);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r.gc[c] = __ldg(sc.g_rgb + 3 * prim + c);
+          }
+          const T* c0 = static_cast<const T*>(sc.c0);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) r.c0[c] = load1<T>(c0 + c * sc.n + prim);
+          if (l0 < sc.n_lobes) {
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+              r.w[p] = *reinterpret_cast<const W*>(st + size_t(p) * batch_plane_bytes<T, P>() +
+                                                   size_t(local * sc.n_lobes + l0) * sizeof(T));
+          }
+        }
+      } else {
+        fetch_scene_item<T, P>(sc, prim, l0, true, r);
+      }
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
+    if (m.scene >= 0) eval_item<FRAME, T, int64_t, kFwdBwd, false, FLAGS>(a, r, prim, l0);
+  }
+  // on a failed wait, let the copies this block started finish before leaving (bounded)
+  if (threadIdx.x == 0 && failed) {
+    for (int s = 0; s < NS; ++s)
+      if (pending & (1u << s)) mbar_wait(&full[s], (pend_par >> s) & 1u, nullptr, 1u << 16);
+  }
+}
+
 }  // namespace nasg
 
 using namespace nasg;
@@ -231,7 +437,9 @@ extern "C" nasg_status nasgabor_batched_prepare(const nasg_scene* scenes, int32_
     d.cam[2] = s.cam[2];
     d.n_lobes = s.n_lobes;
     d.slice_log2 = slice_log2(s.n_lobes);
-    d.pad = 0;
+    d.staged = (s.n_lobes % 2 == 0) && s.params && aligned(s.params, 16) && (s.n * s.n_lobes * es) % 16 == 0
+                   ? 1 | (aligned(s.means, 16) && aligned(s.g_rgb, 16) ? 2 : 0)
+                   : 0;
     d.tile_begin = tiles;
     const int64_t tile_prims = int64_t(256 >> d.slice_log2) * sub_tiles;
     tiles += (s.n + tile_prims - 1) / tile_prims;
@@ -263,8 +471,30 @@ extern "C" nasg_status nasgabor_batched_prepare(const nasg_scene* scenes, int32_
 
 namespace nasg {
 template <int FRAME, typename T>
-static nasg_status launch_batched(const BatchArgs& b, int blocks_per_sm, cudaStream_t s) {
+static nasg_status launch_batched(const BatchArgs& b, int blocks_per_sm, bool staged, cudaStream_t s) {
   const bool dflt = b.identity == 0 && b.normalised != 0 && b.exact == 0;
+  if (staged) {
+    constexpr int P = FrameTraits<FRAME>::P;
+    auto k = dflt ? batched_staged_kernel<FRAME, T, kFlagsDefault> : batched_staged_kernel<FRAME, T, kFlagsRuntime>;
+    constexpr int NS = batch_stages<T>();
+    const size_t smem = size_t(NS) * batch_stage_bytes<T, P>() + 2 * NS * sizeof(uint64_t);
+    static size_t configured[2] = {0, 0};  // per instantiation pair (default, run-time flags)
+    size_t& cfg = configured[dflt ? 0 : 1];
+    if (smem > cfg) {
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+        return check_launch();
+      cfg = smem;
+    }
+    int fit = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k, 256, smem) != cudaSuccess || fit < 1) fit = 1;
+    const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : fit;
+    int64_t grid = int64_t(sm_count()) * per_sm;
+    const int64_t units = b.total_tiles * b.sub_tiles;
+    if (grid > units) grid = units;
+    if (grid < 1) return NASG_OK;
+    k<<<unsigned(grid), 256, smem, s>>>(b);
+    return check_launch();
+  }
   auto k = dflt ? batched_kernel<FRAME, T, kFlagsDefault> : batched_kernel<FRAME, T, kFlagsRuntime>;
   int fit = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k, 256, 0) != cudaSuccess || fit < 1) fit = 1;
@@ -284,7 +514,9 @@ extern "C" nasg_status nasgabor_batched_run(const nasg_batch_plan* plan, const n
   if (plan->total_tiles == 0) return NASG_OK;
   const int dynamic = tuning ? tuning->dynamic : 1;
   const int bps = tuning ? tuning->blocks_per_sm : 0;
+  const int staged = tuning ? tuning->staged : 0;
   if (dynamic != 0 && dynamic != 1) return NASG_ERR_RANGE;
+  if (staged != 0 && staged != 1) return NASG_ERR_RANGE;
   unsigned char* ws = static_cast<unsigned char*>(plan->workspace);
   cudaStream_t st = as_stream(stream);
   BatchArgs b{};
@@ -302,11 +534,11 @@ extern "C" nasg_status nasgabor_batched_run(const nasg_batch_plan* plan, const n
   const bool quat = plan->frame_mode == NASG_FRAME_QUAT;
   const bool bf16 = plan->param_dtype == NASG_DTYPE_BF16;
   if (quat) {
-    return bf16 ? launch_batched<NASG_FRAME_QUAT, __nv_bfloat16>(b, bps, st)
-                : launch_batched<NASG_FRAME_QUAT, float>(b, bps, st);
+    return bf16 ? launch_batched<NASG_FRAME_QUAT, __nv_bfloat16>(b, bps, staged, st)
+                : launch_batched<NASG_FRAME_QUAT, float>(b, bps, staged, st);
   }
-  return bf16 ? launch_batched<NASG_FRAME_COS, __nv_bfloat16>(b, bps, st)
-              : launch_batched<NASG_FRAME_COS, float>(b, bps, st);
+  return bf16 ? launch_batched<NASG_FRAME_COS, __nv_bfloat16>(b, bps, staged, st)
+              : launch_batched<NASG_FRAME_COS, float>(b, bps, staged, st);
 }
 
 extern "C" nasg_status nasgabor_batched_autotune(const nasg_scene* scenes, int32_t n_scenes,
@@ -330,9 +562,10 @@ extern "C" nasg_status nasgabor_batched_autotune(const nasg_scene* scenes, int32
     nasg_batch_plan pl{};
     status = nasgabor_batched_prepare(scenes, n_scenes, modes, k, workspace, workspace_bytes, &pl, stream);
     if (status != NASG_OK) break;
-    for (int32_t dyn = 0; dyn <= 1 && status == NASG_OK; ++dyn) {
+    for (int32_t cfg = 0; cfg < 4 && status == NASG_OK; ++cfg) {
+      const int32_t dyn = cfg & 1, staged = cfg >> 1;
       for (int32_t bps : bps_choices) {
-        nasg_batch_tuning t{dyn, bps, k, 0};
+        nasg_batch_tuning t{dyn, bps, k, staged};
         status = nasgabor_batched_run(&pl, &t, stream);  // warm-up
         if (status != NASG_OK) break;
         cudaEventRecord(e0, st);

@@ -443,11 +443,17 @@ __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
     fence_barrier_init();
   }
   __syncthreads();
+  // producer state (thread 0): stages with copies in flight and the parity of the
+  // phase each completes, so that a block giving up on a wait can let them land
+  uint32_t pending = 0, pend_par = 0;
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int s = 0; s < kStages; ++s) {
       const uint32_t tile = blockIdx.x + s * gridDim.x;
-      if (tile < n_tiles) issue_tile<T, P, FWD, BWD>(a, g, tile, smem + s * g.stage_bytes, &full[s]);
+      if (tile < n_tiles) {
+        issue_tile<T, P, FWD, BWD>(a, g, tile, smem + s * g.stage_bytes, &full[s]);
+        pending |= 1u << s;
+      }
     }
   }
   const uint32_t local = threadIdx.x >> a.slice_log2;
@@ -464,12 +470,21 @@ __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
       if (next < n_tiles && mbar_wait(&empty[ps], (pit / kStages) & 1u, a.dev_err)) {
         fence_proxy_async();
         issue_tile<T, P, FWD, BWD>(a, g, next, smem + ps * g.stage_bytes, &full[ps]);
+        pending |= 1u << ps;
+        pend_par = (pend_par & ~(1u << ps)) | ((((pit + kStages) / kStages) & 1u) << ps);
       }
     }
     const int s = it % kStages;
     const unsigned char* st = smem + s * g.stage_bytes;
     const bool arrived = __all_sync(0xffffffffu, mbar_wait(&full[s], (it / kStages) & 1u, a.dev_err));
-    if (!arrived) return;  // warp-uniform; the other warps give up on their own waits
+    if (!arrived) {  // warp-uniform; the other warps give up on their own waits
+      if (threadIdx.x == 0) {
+        for (int q = 0; q < kStages; ++q)
+          if (pending & (1u << q)) mbar_wait(&full[q], (pend_par >> q) & 1u, nullptr, 1u << 16);
+      }
+      return;
+    }
+    if (threadIdx.x == 0) pending &= ~(1u << s);
     const uint32_t p0 = tile * g.tp;
     const uint32_t count = min(g.tp, n - p0);
     RawItem<T, P> r;

@@ -44,11 +44,13 @@ SIZES = [(5000, 8), (1, 4), (777, 16), (12345, 4), (0, 8), (4099, 3), (2048, 8),
 
 
 @pytest.mark.parametrize("bf16", [True, False])
-@pytest.mark.parametrize("dynamic,sub_tiles", [(1, 1), (0, 3), (1, 8)])
-def test_batched_equals_single_scene_kernel(lib, bf16, dynamic, sub_tiles):
+@pytest.mark.parametrize("dynamic,sub_tiles,staged", [(1, 1, 0), (0, 3, 0), (1, 8, 0), (1, 1, 1), (0, 3, 1),
+                                                      (1, 4, 1)])
+def test_batched_equals_single_scene_kernel(lib, bf16, dynamic, sub_tiles, staged):
     scenes = _scenes(SIZES, 300, bf16)
     b = lib.Batch(scenes, sub_tiles=sub_tiles)
     b.tuning.dynamic = dynamic
+    b.tuning.staged = staged
     b.run()
     lib.nasg_device_status()
     _compare_with_single(lib, scenes)
@@ -64,6 +66,7 @@ def test_batched_cos_frames(lib):
 def test_batched_exact_normalisation(lib):
     scenes = _scenes([(2000, 8), (333, 3), (1024, 16)], 450, True)
     b = lib.Batch(scenes, norm_mode="exact")
+    b.tuning.staged = 1
     b.run()
     _compare_with_single(lib, scenes, norm="exact")
 
