@@ -312,6 +312,36 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
       }
     }
   }
+  if (FWD && BWD && a.slice >= 4) {  // warp-uniform
+    // Reduce-scatter over the slice: the colour and dLoss/dd partials (and the
+    // partial d . dLoss/dd, linear in them) are summed so that lane c < 3 of each
+    // group of four ends with channel c and lane 3 with the dot product: seven
+    // shuffles in place of the twelve of an all-reduce of six values.
+    const int lane = threadIdx.x & 31;
+    float v[7] = {rgb[0], gd[0], rgb[1], gd[1], rgb[2], gd[2], gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2]};
+    for (int o = a.slice >> 1; o >= 4; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    const bool b1 = (lane & 2) != 0, b0 = (lane & 1) != 0;
+    float k0 = b1 ? v[4] : v[0], k1 = b1 ? v[5] : v[1], k2 = b1 ? v[6] : v[2], k3 = b1 ? 0.f : v[3];
+    k0 += __shfl_xor_sync(0xffffffffu, b1 ? v[0] : v[4], 2);
+    k1 += __shfl_xor_sync(0xffffffffu, b1 ? v[1] : v[5], 2);
+    k2 += __shfl_xor_sync(0xffffffffu, b1 ? v[2] : v[6], 2);
+    k3 += __shfl_xor_sync(0xffffffffu, b1 ? v[3] : 0.f, 2);
+    float e0 = b0 ? k2 : k0, e1 = b0 ? k3 : k1;
+    e0 += __shfl_xor_sync(0xffffffffu, b0 ? k0 : k2, 1);
+    e1 += __shfl_xor_sync(0xffffffffu, b0 ? k1 : k3, 1);
+    const float dot = __shfl_sync(0xffffffffu, e0, lane | 3);
+    const int c = l0 >> 1;  // this lane's channel (lane index within the slice)
+    if (ok && c < 3) {
+      a.rgb[3 * i + c] = e0 + pick3(cur.c0, c);
+      store1(a.g_c0 + c * n + i, pick3(cur.gc, c), acc);
+      // dLoss/dmu = (I - d d^T) dLoss/dd / |mu - cam|
+      if (a.g_means) store1(a.g_means + 3 * i + c, (e1 - dot * pick3(d, c)) * inv_dist, acc);
+    }
+    return;
+  }
   // xor-butterfly over the slice: every lane ends with the primitive's sums
   for (int o = a.slice >> 1; o >= 1; o >>= 1) {
 #pragma unroll
@@ -377,7 +407,7 @@ __global__ void __launch_bounds__(256, 2) eval_kernel(const EvalArgs a) {
 // bounded. Requirements (checked on the host): no index list, N % 8 == 0,
 // L even, 16-byte aligned buffers, 32-bit offsets.
 // ---------------------------------------------------------------------------
-constexpr int kStages = 4;
+constexpr int kStages = 3;
 
 struct TileGeom {
   uint32_t tp;          // primitives per tile
@@ -443,21 +473,16 @@ __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
     fence_barrier_init();
   }
   __syncthreads();
-  // producer state (thread 0): stages with copies in flight and the parity of the
-  // phase each completes, so that a block giving up on a wait can let them land
-  uint32_t pending = 0, pend_par = 0;
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int s = 0; s < kStages; ++s) {
       const uint32_t tile = blockIdx.x + s * gridDim.x;
-      if (tile < n_tiles) {
-        issue_tile<T, P, FWD, BWD>(a, g, tile, smem + s * g.stage_bytes, &full[s]);
-        pending |= 1u << s;
-      }
+      if (tile < n_tiles) issue_tile<T, P, FWD, BWD>(a, g, tile, smem + s * g.stage_bytes, &full[s]);
     }
   }
   const uint32_t local = threadIdx.x >> a.slice_log2;
   const int l0 = 2 * (threadIdx.x & (a.slice - 1));
+  bool refilled = true;  // producer: whether this iteration's refill was issued
   for (uint32_t it = 0;; ++it) {
     const uint32_t tile = blockIdx.x + it * gridDim.x;
     if (tile >= n_tiles) break;  // block-uniform
@@ -467,24 +492,27 @@ __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
       const uint32_t pit = it - 1;
       const uint32_t next = blockIdx.x + (pit + kStages) * gridDim.x;
       const int ps = pit % kStages;
+      refilled = false;
       if (next < n_tiles && mbar_wait(&empty[ps], (pit / kStages) & 1u, a.dev_err)) {
         fence_proxy_async();
         issue_tile<T, P, FWD, BWD>(a, g, next, smem + ps * g.stage_bytes, &full[ps]);
-        pending |= 1u << ps;
-        pend_par = (pend_par & ~(1u << ps)) | ((((pit + kStages) / kStages) & 1u) << ps);
+        refilled = true;
       }
     }
     const int s = it % kStages;
     const unsigned char* st = smem + s * g.stage_bytes;
     const bool arrived = __all_sync(0xffffffffu, mbar_wait(&full[s], (it / kStages) & 1u, a.dev_err));
     if (!arrived) {  // warp-uniform; the other warps give up on their own waits
+      // the producer lets the copies it started land before the block leaves: the
+      // stages of iterations it .. it + kStages - 1 (the last only if refilled)
       if (threadIdx.x == 0) {
-        for (int q = 0; q < kStages; ++q)
-          if (pending & (1u << q)) mbar_wait(&full[q], (pend_par >> q) & 1u, nullptr, 1u << 16);
+        for (uint32_t j = it; j < it + kStages; ++j) {
+          if (blockIdx.x + j * gridDim.x >= n_tiles || (j == it + kStages - 1 && !refilled)) continue;
+          mbar_wait(&full[j % kStages], (j / kStages) & 1u, nullptr, 1u << 16);
+        }
       }
       return;
     }
-    if (threadIdx.x == 0) pending &= ~(1u << s);
     const uint32_t p0 = tile * g.tp;
     const uint32_t count = min(g.tp, n - p0);
     RawItem<T, P> r;

@@ -191,7 +191,9 @@ def test_fused_equals_separate_passes(lib, bf16):
     sg = g[0].cpu().numpy()
     assert max(rel_l2(fg[p], sg[p]) for p in range(fg.shape[0])) < 1e-6
     torch.testing.assert_close(f[2], g[1], rtol=0, atol=0)
-    assert rel_l2(f[3].cpu().numpy(), g[2].cpu().numpy()) < 1e-6
+    # the fused pass reduce-scatters dLoss/dd over the slice (another summation order),
+    # and dLoss/dmu projects out the radial part (cancellation): a looser bound
+    assert rel_l2(f[3].cpu().numpy(), g[2].cpu().numpy()) < 1e-5
 
 
 def test_index_list_and_accumulate(lib):
