@@ -162,8 +162,8 @@ __device__ __forceinline__ void activate_family(const V* r, bool identity, Act<V
 
 template <class V>
 struct QuatFrame {
-  V q[4];       // normalised quaternion (w, x, y, z)
-  V inv_norm;   // 1/|q_raw|
+  V q[4];       // raw quaternion (w, x, y, z)
+  V inv2;       // 1/|q|^2
   V x[3], z[3];
 };
 
@@ -177,10 +177,9 @@ __device__ __forceinline__ void quat_frame(const V* qr, QuatFrame<V>& f) {
   const V qw = qr[0], qx = qr[1], qy = qr[2], qz = qr[3];
   const V ww = qw * qw, xx = qx * qx, yy = qy * qy, zz = qz * qz;
   const V n2 = (ww + xx) + (yy + zz);
-  const V inv = vrsqrt(n2);
   const V inv2 = vrcp(n2);
-  f.inv_norm = inv;
-  f.q[0] = qw * inv; f.q[1] = qx * inv; f.q[2] = qy * inv; f.q[3] = qz * inv;
+  f.inv2 = inv2;
+  f.q[0] = qw; f.q[1] = qx; f.q[2] = qy; f.q[3] = qz;
   const V two_inv2 = 2.f * inv2;
   f.x[0] = ((ww + xx) - (yy + zz)) * inv2;
   f.x[1] = vfma(qx, qy, qw * qz) * two_inv2;
@@ -190,20 +189,46 @@ __device__ __forceinline__ void quat_frame(const V* qr, QuatFrame<V>& f) {
   f.z[2] = ((ww + zz) - (xx + yy)) * inv2;
 }
 
-// dLoss/dq_raw from dLoss/dx (L) and dLoss/dz (M), through the unit-quaternion
-// rotation columns and the normalisation q -> q/|q|.
+// dLoss/dq_raw from dLoss/dx (L) and dLoss/dz (M). With x = x~(q)/|q|^2 and
+// z = z~(q)/|q|^2 (x~, z~ quadratic in the raw quaternion q):
+//   dLoss/dq_i = (2/|q|^2) [L.(dx~/dq_i)/2 + M.(dz~/dq_i)/2 - q_i (L.x + M.z)].
 template <class V>
 __device__ __forceinline__ void quat_frame_grad(const QuatFrame<V>& f, const V* L, const V* M, V* g) {
   const V w = f.q[0], x = f.q[1], y = f.q[2], z = f.q[3];
-  const V gw = 2.f * (vfma(L[1], z, vfma(M[0], y, -(L[2] * y))) - M[1] * x);
-  const V gx = 2.f * (vfma(L[1], y, vfma(L[2], z, vfma(M[0], z, -(M[1] * w)))) - 2.f * M[2] * x);
-  const V gy = 2.f * (vfma(L[1], x, vfma(M[0], w, vfma(M[1], z, -(L[2] * w)))) - 2.f * (L[0] + M[2]) * y);
-  const V gz = 2.f * (vfma(L[1], w, vfma(L[2], x, vfma(M[0], x, M[1] * y))) - 2.f * L[0] * z);
-  const V dot = vfma(gw, w, vfma(gx, x, vfma(gy, y, gz * z)));
-  g[0] = (gw - dot * w) * f.inv_norm;
-  g[1] = (gx - dot * x) * f.inv_norm;
-  g[2] = (gy - dot * y) * f.inv_norm;
-  g[3] = (gz - dot * z) * f.inv_norm;
+  const V s = vfma(L[0], f.x[0], vfma(L[1], f.x[1], vfma(L[2], f.x[2], vfma(M[0], f.z[0],
+                  vfma(M[1], f.z[1], M[2] * f.z[2])))));
+  const V k = 2.f * f.inv2;
+  const V hw = vfma(L[0], w, vfma(L[1], z, vfma(M[0], y, vfma(M[2], w, -vfma(L[2], y, M[1] * x)))));
+  const V hx = vfma(L[0], x, vfma(L[1], y, vfma(L[2], z, vfma(M[0], z, -vfma(M[1], w, M[2] * x)))));
+  const V hy = vfma(L[1], x, vfma(M[0], w, vfma(M[1], z, -vfma(L[0], y, vfma(L[2], w, M[2] * y)))));
+  const V hz = vfma(L[1], w, vfma(L[2], x, vfma(M[0], x, vfma(M[1], y, vfma(M[2], z, -(L[0] * z))))));
+  g[0] = vfma(-w, s, hw) * k;
+  g[1] = vfma(-x, s, hx) * k;
+  g[2] = vfma(-y, s, hy) * k;
+  g[3] = vfma(-z, s, hz) * k;
+}
+
+// dLoss/dq_raw for dLoss/dx = gv d and dLoss/dz = gu d (the lobe depends on the
+// frame only through u = d.z and v = d.x). With x = x~(q)/|q|^2, z = z~(q)/|q|^2
+// (x~, z~ quadratic in q):
+//   dLoss/dq_i = (2/|q|^2) [gv d.(dx~/dq_i)/2 + gu d.(dz~/dq_i)/2 - q_i (gv v + gu u)],
+// and the halved derivatives reduce to four combinations of d and q:
+//   A1 = d0 w + d1 z - d2 y,  A2 = d0 x + d1 y + d2 z,  A3 = d0 y - d1 x + d2 w,
+//   A4 = d0 z - d1 w - d2 x;
+//   (w, x, y, z) components: gv A1 + gu A3, gv A2 + gu A4, gu A1 - gv A3, gu A2 - gv A4.
+template <class V>
+__device__ __forceinline__ void quat_frame_grad_d(const QuatFrame<V>& f, const V* d, V gv, V gu, V u, V v, V* g) {
+  const V w = f.q[0], x = f.q[1], y = f.q[2], z = f.q[3];
+  const V a1 = vfma(d[0], w, vfma(d[1], z, -(d[2] * y)));
+  const V a2 = vfma(d[0], x, vfma(d[1], y, d[2] * z));
+  const V a3 = vfma(d[0], y, vfma(d[2], w, -(d[1] * x)));
+  const V a4 = vfma(d[0], z, -vfma(d[1], w, d[2] * x));
+  const V s = vfma(gv, v, gu * u);
+  const V k = 2.f * f.inv2;
+  g[0] = vfma(-w, s, vfma(gv, a1, gu * a3)) * k;
+  g[1] = vfma(-x, s, vfma(gv, a2, gu * a4)) * k;
+  g[2] = vfma(-y, s, vfma(gu, a1, -(gv * a3))) * k;
+  g[3] = vfma(-z, s, vfma(gu, a2, -(gv * a4))) * k;
 }
 
 // Supp. C frame from three cosines. RAW mode: c = tanh(r), s = sech(r) >= 0,
@@ -271,6 +296,7 @@ template <class V>
 struct LobePartials {
   V G_u, G_v, G_lam, G_a, G_k;  // dG/du, dG/dv, dG/dlam, dG/da, dG/dk
   V G_phi;                      // dG/dphi (phase family)
+  V u, v;                       // d.z and d.x
 };
 
 // ---------------------------------------------------------------------------
@@ -476,6 +502,8 @@ __device__ __forceinline__ V lobe_family(const V* d, const V* x, const V* z, V l
   const V cpe = vsel(anti, 0.f, cinv * pe);
   const V G = cpe * h;
   if (GRAD) {
+    pd->u = u;
+    pd->v = v;
     const V ek = em1 + 1.f;                             // E kappa
     const V two_lam_ek = 2.f * lam * ek;
     const V dtau_du = 2.f * u * tau * inv_s2;

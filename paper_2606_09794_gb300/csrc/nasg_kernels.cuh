@@ -115,13 +115,13 @@ __device__ __forceinline__ void lobe_step(const V* pv, const V* d, const V* gc, 
 #pragma unroll
     for (int c = 0; c < 3; ++c) gp[TR::W + c] = gc[c] * G * act.s_w[c];
     const V gv = gG * pd.G_v, gu = gG * pd.G_u;
-    const V gx[3] = {gv * d[0], gv * d[1], gv * d[2]};
-    const V gz[3] = {gu * d[0], gu * d[1], gu * d[2]};
 #pragma unroll
     for (int c = 0; c < 3; ++c) gd[c] = vfma(gu, z[c], vfma(gv, x[c], gd[c]));
     if (TR::QUAT) {
-      quat_frame_grad(qf, gx, gz, gp);
+      quat_frame_grad_d(qf, d, gv, gu, pd.u, pd.v, gp);
     } else {
+      const V gx[3] = {gv * d[0], gv * d[1], gv * d[2]};
+      const V gz[3] = {gu * d[0], gu * d[1], gu * d[2]};
       cos_frame_grad(cf, gx, gz, gp);
     }
   }
