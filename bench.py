@@ -259,6 +259,45 @@ def cpu_oracle_rate(target_s=12.0, max_n=100_000):
                       f"forward+backward in float64 numpy, one thread, {total:.1f} s"}
 
 
+def _oracle_worker(args):
+    """One host process of the all-cores oracle timing: forward+backward passes of the
+    FP64 oracle (one thread) on its own seeded slice for about target_s seconds."""
+    n, seed, target_s = args
+    try:
+        from threadpoolctl import threadpool_limits
+        ctx = threadpool_limits(limits=1)
+    except Exception:  # pragma: no cover
+        import contextlib
+        ctx = contextlib.nullcontext()
+    from oracle import nasgabor as ong
+    from paper_2606_09794_gb300 import inputs
+    L = N_LOBES
+    w = inputs.point_cloud_workload(n, L, seed)
+    p = inputs.quantize_bf16(w.params)
+    c = inputs.quantize_bf16(w.c0)
+    reps, t0 = 0, time.perf_counter()
+    with ctx:
+        while time.perf_counter() - t0 < target_s or reps == 0:
+            ong.forward(p, c, w.means, w.cam, L)
+            ong.backward(p, c, w.means, w.cam, w.g_rgb, L)
+            reps += 1
+    return n * L * reps, time.perf_counter() - t0
+
+
+def cpu_oracle_rate_all_cores(target_s=8.0, n_per_proc=20_000):
+    """The same oracle pass on every host core at once (one process per core,
+    started with spawn), for context next to the one-thread baseline."""
+    import multiprocessing as mp
+    procs = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_oracle_worker, [(n_per_proc, SEED + 1 + k, target_s) for k in range(procs)])
+    lobes = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return {"value": lobes / wall, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} processes x {n_per_proc} primitives x {N_LOBES} lobes (seeded slices of the "
+                      f"N=1e6 workload), forward+backward in float64 numpy, one thread each, {wall:.1f} s"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -409,6 +448,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate()
+        if paths is not None:
+            paths["cpu_oracle_all_cores"] = cpu_oracle_rate_all_cores()
 
     if rank == 0:
         line = {

@@ -60,3 +60,10 @@ def test_reference_arm_prints_contract_line():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_all_cores_oracle_timing_runs_on_every_core():
+    import bench
+    r = bench.cpu_oracle_rate_all_cores(target_s=0.2, n_per_proc=200)
+    assert r["kind"] == "oracle" and r["value"] > 0
+    assert r["cores"] == (os.cpu_count() or 1)
