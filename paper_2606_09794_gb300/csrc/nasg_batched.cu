@@ -11,11 +11,12 @@
 // look the scene up in the shared-memory copy of the table, and evaluate the
 // tile with the lobe-pair lanes of the single-scene kernels, fetching each
 // lane's next sub-tile item before computing the current one. No thread waits
-// on another block. A staged variant moves each sub-tile's parameter spans
-// into shared memory with bulk copies, four sub-tiles ahead (one elected
-// producer thread, full/empty mbarriers, every wait bounded), for the scenes
-// whose planes allow it, and loads the rest directly. The autotuner times the
-// candidate schedules on the caller's own prepared batch and returns the fastest.
+// on another block. A staged variant moves each sub-tile's parameter spans,
+// means and upstream gradients into shared memory with bulk copies, four (BF16)
+// or three (FP32) sub-tiles ahead (one elected producer thread, full/empty
+// mbarriers, every wait bounded), for the scenes whose planes allow it, and
+// loads the rest directly. The autotuner times the candidate schedules on the
+// caller's own prepared batch and returns the fastest.
 #include <algorithm>
 #include <vector>
 
