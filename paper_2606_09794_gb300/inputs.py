@@ -321,6 +321,21 @@ def fit_directions(step: int, seed: int, n_dirs: int = 64) -> np.ndarray:
     return d.astype(np.float32)
 
 
+def fit_subsample(n: int = 2_000_000, n_student: int = 16, n_teacher: int = 4, seed_teacher: int = 1005,
+                  seed_student: int = 1006, sample: int = 20_000, seed_sample: int = 7):
+    """The fitting workload's seeded subsample: teacher planes/c0, student planes/c0 (raw
+    float32, both drawn over all n primitives) restricted to subsample_indices(n, sample,
+    seed_sample), and those indices. Primitives are independent in the fit, so a fit of
+    the subsample follows the same trajectories as those primitives inside the full run."""
+    t = point_cloud_workload(n, n_teacher, seed_teacher, with_upstream=False)
+    s = point_cloud_workload(n, n_student, seed_student, with_upstream=False)
+    idx = subsample_indices(n, sample, seed_sample)
+    lt = (idx[:, None] * n_teacher + np.arange(n_teacher)).reshape(-1)
+    ls = (idx[:, None] * n_student + np.arange(n_student)).reshape(-1)
+    return (np.ascontiguousarray(t.params[:, lt]), np.ascontiguousarray(t.c0[:, idx]),
+            np.ascontiguousarray(s.params[:, ls]), np.ascontiguousarray(s.c0[:, idx]), idx)
+
+
 def subsample_indices(n: int, count: int, seed: int) -> np.ndarray:
     """Sorted seeded subsample of primitive indices (int64)."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5AB]))

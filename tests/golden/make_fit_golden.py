@@ -32,13 +32,7 @@ OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "fit_subsample_20
 
 def subsample_workload():
     from paper_2606_09794_gb300 import inputs
-    t = inputs.point_cloud_workload(N, LT, SEED_T, with_upstream=False)
-    s = inputs.point_cloud_workload(N, LS, SEED_S, with_upstream=False)
-    idx = inputs.subsample_indices(N, SAMPLE, SEED_SAMPLE)
-    lt = (idx[:, None] * LT + np.arange(LT)).reshape(-1)
-    ls = (idx[:, None] * LS + np.arange(LS)).reshape(-1)
-    return (np.ascontiguousarray(t.params[:, lt]), np.ascontiguousarray(t.c0[:, idx]),
-            np.ascontiguousarray(s.params[:, ls]), np.ascontiguousarray(s.c0[:, idx]), idx)
+    return inputs.fit_subsample(N, LS, LT, SEED_T, SEED_S, SAMPLE, SEED_SAMPLE)
 
 
 def run_chunk(args):
