@@ -371,3 +371,39 @@ def test_host_resident_fused_matches_device_fused(lib, n, L, chunk, bf16):
     assert max(rel_l2(gp[p], rp[p]) for p in range(gp.shape[0])) < 1e-6
     torch.testing.assert_close(out[2], ref[2].cpu(), rtol=0, atol=0)
     assert rel_l2(out[3].numpy(), ref[3].cpu().numpy()) < 1e-6
+
+
+def test_offsets_past_2_to_31_sampled(lib):
+    """N = 27e6, L = 8 BF16: P N L = 2.16e9 elements per parameter array, past 2^31, so
+    the kernels take 64-bit offsets; the last 300 primitives and 300 random ones
+    against the oracle (about 25 GB on the device)."""
+    import torch
+    n, L = 27_000_000, 8
+    d = inputs.device_point_cloud(n, L, 77, "cuda")
+    params = d["params"].to(torch.bfloat16)
+    del d["params"]
+    c0 = d["c0"].to(torch.bfloat16)
+    means, g_rgb, cam = d["means"], d["g_rgb"], d["cam"]
+    rgb, g_p, g_c0, g_mu = lib.nasgabor_fused_fwd_bwd(params, c0, means, cam, g_rgb, L)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(78)
+    sample = np.unique(np.concatenate([np.arange(n - 300, n), rng.choice(n, 300, replace=False)]))
+    s_t = torch.from_numpy(sample).cuda()
+    lobes = (s_t[:, None] * L + torch.arange(L, device="cuda")).reshape(-1)
+    ps = params[:, lobes].float().cpu().numpy()
+    cs = c0[:, s_t].float().cpu().numpy()
+    ms = means[s_t].cpu().numpy()
+    gs = g_rgb[s_t].cpu().numpy()
+    cam_np = np.asarray(cam, dtype=np.float32)
+
+    def fwd(p, c, m, cm):
+        return ong.forward(p, c, m, cm, L)
+
+    ref, nu = sensitivity_floor(fwd, (ps, cs, ms, cam_np), (0, 1, 2, 3))
+    rep = colour_report(rgb[s_t].cpu().numpy(), ref, nu, 4e-3)
+    assert rep["violations"] == 0, rep
+    r_p, _, r_mu = ong.backward(ps, cs, ms, cam_np, gs, L)
+    gp = g_p[:, lobes].cpu().numpy()
+    assert max(rel_l2(gp[p], r_p[p]) for p in range(10)) <= GRAD_TOL
+    assert rel_l2(g_mu[s_t].cpu().numpy(), r_mu) <= GRAD_TOL
+    np.testing.assert_array_equal(g_c0[:, s_t].cpu().numpy(), gs.T)
