@@ -337,7 +337,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paths", action="store_true")
-    ap.add_argument("--case", choices=["scene_step", "batched", "fit", "frame"], default=None,
+    ap.add_argument("--case", choices=["paths", "scene_step", "batched", "fit", "frame"], default=None,
                     help="run only this secondary measurement (at --case-n primitives) and print its JSON")
     ap.add_argument("--case-n", type=int, default=None)
     ap.add_argument("--case-steps", type=int, default=None)
@@ -493,7 +493,12 @@ def run_case(args):
     kw = {}
     if args.case_n:
         kw["n"] = args.case_n
-    if args.case == "scene_step":
+    if args.case == "paths":
+        n = args.case_n or N_PRIMS
+        w = inputs.point_cloud_workload(n, N_LOBES, SEED)
+        params = torch.from_numpy(w.params).to(dev).to(torch.bfloat16)
+        res = measure_paths(nb, inputs, w, params, dev, stream, peak, reps=args.case_steps or 200)
+    elif args.case == "scene_step":
         res = measure_scene_step(nb, inputs, dev, stream, peak, **kw)
     elif args.case == "frame":
         res = measure_frame(nb, inputs, dev, stream, **kw)

@@ -126,7 +126,7 @@ int32_t nasg_last_cuda_error(void);
 nasg_status nasg_device_status(void* stream);
 
 /* ABI version of this header (bumped on any incompatible change). */
-#define NASG_ABI_VERSION 2
+#define NASG_ABI_VERSION 3
 int32_t nasg_abi_version(void);
 
 /*
@@ -292,6 +292,10 @@ typedef struct nasg_batch_modes {
 /* Filled by nasgabor_batched_prepare; pass it to nasgabor_batched_run. */
 typedef struct nasg_batch_plan {
   int32_t n_scenes, frame_mode, param_dtype, norm_mode, act_mode, sub_tiles;
+  int32_t pair_path;  /* 1: every scene has even L, 2-element aligned parameter planes, 8-byte aligned
+                         gradient planes and P N L < 2^31, so the launch runs the pair-load/store
+                         kernel with 32-bit offsets; 0: the general kernel */
+  int32_t reserved;
   int64_t total_tiles, total_prims, total_lobes;
   void* workspace;
 } nasg_batch_plan;

@@ -62,7 +62,8 @@ class NasgBatchModes(ctypes.Structure):
 
 class NasgBatchPlan(ctypes.Structure):
     _fields_ = [("n_scenes", _i32), ("frame_mode", _i32), ("param_dtype", _i32), ("norm_mode", _i32),
-                ("act_mode", _i32), ("sub_tiles", _i32), ("total_tiles", _i64), ("total_prims", _i64),
+                ("act_mode", _i32), ("sub_tiles", _i32), ("pair_path", _i32), ("reserved", _i32),
+                ("total_tiles", _i64), ("total_prims", _i64),
                 ("total_lobes", _i64), ("workspace", _vp)]
 
 

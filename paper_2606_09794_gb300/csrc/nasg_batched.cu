@@ -12,10 +12,11 @@
 // tile with the lobe-pair lanes of the single-scene kernels, fetching each
 // lane's next sub-tile item before computing the current one. No thread waits
 // on another block. A staged variant moves each sub-tile's parameter spans,
-// means and upstream gradients into shared memory with bulk copies, four (BF16)
-// or three (FP32) sub-tiles ahead (one elected producer thread, full/empty
-// mbarriers, every wait bounded), for the scenes whose planes allow it, and
-// loads the rest directly. The autotuner times the candidate schedules on the
+// means, upstream gradients and diffuse colours into shared memory with bulk
+// copies (span plans for any N), four (BF16) or three (FP32) sub-tiles ahead
+// (one elected producer thread, full/empty mbarriers, every wait bounded), for
+// the scenes whose planes allow it, and loads the rest directly; its copy of the
+// scene table sits in dynamic shared memory, sized for the batch. The autotuner times the candidate schedules on the
 // caller's own prepared batch and returns the fastest.
 #include <algorithm>
 #include <vector>
@@ -25,20 +26,14 @@
 namespace nasg {
 
 struct SceneDev {
-  const void* params;
-  const void* c0;
-  const float* means;
-  const float* g_rgb;
-  float* rgb;
-  float* g_params;
-  float* g_c0;
-  float* g_means;
-  int64_t n;
+  EvalArgs args;       // the scene as the single-scene argument block, read in place from shared
+                       // memory by the item arithmetic (no per-thread copy in registers)
   int64_t tile_begin;  // first global tile of this scene
-  float cam[3];
-  int32_t n_lobes;
-  int32_t slice_log2;
-  int32_t staged;  // parameter spans may be moved by bulk copies (even L, 16-byte aligned planes)
+  int64_t unit_begin;  // first global sub-tile (tile_begin x sub_tiles)
+  int32_t staged;  // bit 0: parameter spans may be moved by bulk copies (even L, N L sizeof(T) % 16 == 0,
+                   // 16-byte aligned planes); bit 1: the means, upstream gradients and diffuse colours
+                   // too (16-byte aligned buffers, moved by span plans)
+  int32_t pad;
 };
 
 constexpr int kMaxScenes = NASG_MAX_SCENES;
@@ -51,14 +46,11 @@ struct BatchArgs {
   int32_t sub_tiles;  // k
   int64_t total_tiles;
   int32_t dynamic;
-  int32_t identity;
-  int32_t normalised;
-  int32_t exact;
   int* dev_err;
 };
 
 template <typename T, int P>
-__device__ __forceinline__ void fetch_scene_item(const SceneDev& sc, int64_t prim, int l0, bool valid,
+__device__ __forceinline__ void fetch_scene_item(const EvalArgs& sc, int64_t prim, int l0, bool valid,
                                                  RawItem<T, P>& r) {
   r.ok = 0;
   if (!valid || prim >= sc.n) return;
@@ -95,37 +87,19 @@ __device__ __forceinline__ void fetch_scene_item(const SceneDev& sc, int64_t pri
   }
 }
 
-// View of one scene as the single-scene argument block (fields eval_item reads).
-__device__ __forceinline__ EvalArgs scene_args(const SceneDev& sc, const BatchArgs& b) {
-  EvalArgs a;
-  a.params = sc.params;
-  a.c0 = sc.c0;
-  a.means = sc.means;
-  a.cam[0] = sc.cam[0];
-  a.cam[1] = sc.cam[1];
-  a.cam[2] = sc.cam[2];
-  a.idx = nullptr;
-  a.n_items = sc.n;
-  a.n = sc.n;
-  a.n_lobes = sc.n_lobes;
-  a.slice_log2 = sc.slice_log2;
-  a.slice = 1 << sc.slice_log2;
-  a.identity = b.identity;
-  a.normalised = b.normalised;
-  a.exact = b.exact;
-  a.accumulate = 0;
-  a.g_rgb = sc.g_rgb;
-  a.rgb = sc.rgb;
-  a.g_params = sc.g_params;
-  a.g_c0 = sc.g_c0;
-  a.g_means = sc.g_means;
-  a.dev_err = b.dev_err;
-  return a;
+// The item arithmetic of the single-scene kernels. PAIRS: every scene of the batch
+// has even L, pair-aligned planes and 32-bit offsets (pair loads and stores, 32-bit
+// index arithmetic); else the general form (any L, 64-bit offsets).
+template <int FRAME, typename T, int FLAGS, bool PAIRS>
+__device__ __forceinline__ void eval_scene_item(const EvalArgs& a, const RawItem<T, FrameTraits<FRAME>::P>& r,
+                                                int64_t prim, int l0) {
+  if (PAIRS) eval_item<FRAME, T, uint32_t, kFwdBwd, true, FLAGS>(a, r, uint32_t(prim), l0);
+  else eval_item<FRAME, T, int64_t, kFwdBwd, false, FLAGS>(a, r, prim, l0);
 }
 
 // FLAGS: kFlagsDefault (raw activations, approximate normalisation) or
 // kFlagsRuntime (modes read from the arguments).
-template <int FRAME, typename T, int FLAGS>
+template <int FRAME, typename T, int FLAGS, bool PAIRS>
 __global__ void __launch_bounds__(256, 2) batched_kernel(const BatchArgs b) {
   constexpr int P = FrameTraits<FRAME>::P;
   __shared__ SceneDev sd[kMaxScenes];
@@ -150,18 +124,17 @@ __global__ void __launch_bounds__(256, 2) batched_kernel(const BatchArgs b) {
       const int mid = (lo + hi + 1) >> 1;
       if (sd[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
     }
-    const SceneDev& sc = sd[lo];
-    const EvalArgs a = scene_args(sc, b);
+    const EvalArgs& sc = sd[lo].args;
     const int tp = 256 >> sc.slice_log2;
     const int local = threadIdx.x >> sc.slice_log2;
     const int l0 = 2 * (threadIdx.x & ((1 << sc.slice_log2) - 1));
-    const int64_t base = (tile - sc.tile_begin) * int64_t(tp) * b.sub_tiles;
+    const int64_t base = (tile - sd[lo].tile_begin) * int64_t(tp) * b.sub_tiles;
     RawItem<T, P> cur, nxt;
     fetch_scene_item<T, P>(sc, base + local, l0, true, cur);
     for (int j = 0; j < b.sub_tiles; ++j) {
       const int64_t prim = base + int64_t(j) * tp + local;
       fetch_scene_item<T, P>(sc, prim + tp, l0, j + 1 < b.sub_tiles, nxt);
-      eval_item<FRAME, T, int64_t, kFwdBwd, false, FLAGS>(a, cur, prim, l0);
+      eval_scene_item<FRAME, T, FLAGS, PAIRS>(sc, cur, prim, l0);
       cur = nxt;
     }
     if (b.dynamic) {
@@ -202,14 +175,13 @@ struct StageMeta {
   int64_t p0;        // first primitive of the unit in its scene
 };
 
-// Stage layout: P parameter spans of up to 512 lobes, then up to 256 means and
-// 256 upstream gradients (a sub-tile holds at most 512 lobes: 256/S primitives x
-// L lobes with S >= L/2).
-template <typename T, int P>
-__host__ __device__ inline uint32_t batch_plane_bytes() { return 512u * uint32_t(sizeof(T)); }
+// Stage layout: batch_geom<T, P>() (P parameter spans of up to 512 lobes, then
+// the means, upstream-gradient and diffuse-colour regions of up to 256
+// primitives; a sub-tile holds at most 512 lobes: 256/S primitives x L lobes
+// with S >= L/2).
 template <typename T, int P>
 __host__ __device__ inline uint32_t batch_stage_bytes() {
-  return (uint32_t(P) * batch_plane_bytes<T, P>() + 2u * 256u * 12u + 127u) & ~127u;
+  return batch_geom<T, P>().stage_bytes;
 }
 
 // Producer side: record a unit in a stage and start its copies; returns whether
@@ -231,49 +203,73 @@ __device__ __forceinline__ bool issue_unit(const BatchArgs& b, const SceneDev* s
     return false;
   }
   const int64_t u = int64_t(unit);
-  while (sc_i + 1 < b.n_scenes && sd[sc_i + 1].tile_begin * b.sub_tiles <= u) ++sc_i;
-  const SceneDev& sc = sd[sc_i];
+  while (sc_i + 1 < b.n_scenes && sd[sc_i + 1].unit_begin <= u) ++sc_i;
+  const EvalArgs& sc = sd[sc_i].args;
+  const int32_t staged = sd[sc_i].staged;
+  const int64_t n = sc.n;
+  const uint32_t L = uint32_t(sc.n_lobes);
   const int64_t tp = 256 >> sc.slice_log2;
-  const int64_t p0 = (u - sc.tile_begin * b.sub_tiles) * tp;
-  const int64_t count = sc.n - p0 < tp ? sc.n - p0 : tp;
+  const int64_t p0 = (u - sd[sc_i].unit_begin) * tp;
+  const int64_t count = n - p0 < tp ? n - p0 : tp;
   meta->unit = unit;
   meta->scene = count > 0 ? sc_i : -1;
   meta->count = count > 0 ? int32_t(count) : 0;
   meta->p0 = p0;
-  const uint32_t bytes = count > 0 ? uint32_t(count) * uint32_t(sc.n_lobes) * uint32_t(sizeof(T)) : 0u;
-  const bool stage_p = count > 0 && (sc.staged & 1) && (bytes % 16u) == 0u;
-  const bool stage_m = stage_p && (sc.staged & 2) && (count % 4) == 0;  // 12-byte records: 4 per 16 bytes
+  const uint32_t bytes = count > 0 ? uint32_t(count) * L * uint32_t(sizeof(T)) : 0u;
+  const bool stage_p = count > 0 && (staged & 1) && (bytes % 16u) == 0u;
+  const bool stage_m = stage_p && (staged & 2);
   meta->staged = (stage_p ? 1 : 0) | (stage_m ? 2 : 0);
   if (!stage_p) {
     mbar_arrive(bar);
     return false;
   }
-  const uint32_t mbytes = uint32_t(count) * 12u;
-  mbar_arrive_expect_tx(bar, uint32_t(P) * bytes + (stage_m ? 2u * mbytes : 0u));
-  const T* params = static_cast<const T*>(sc.params);
-  const int64_t NL = sc.n * sc.n_lobes;
-#pragma unroll
-  for (int p = 0; p < P; ++p)
-    bulk_g2s(st + size_t(p) * batch_plane_bytes<T, P>(), params + p * NL + p0 * sc.n_lobes, bytes, bar);
+  constexpr TileGeom g = batch_geom<T, P>();
+  uint32_t total = uint32_t(P) * bytes;
+  PrimPlans pp;
   if (stage_m) {
-    unsigned char* mu = st + size_t(P) * batch_plane_bytes<T, P>();
-    bulk_g2s(mu, sc.means + 3 * p0, mbytes, bar);
-    bulk_g2s(mu + 256u * 12u, sc.g_rgb + 3 * p0, mbytes, bar);
+    // the plain-load parts are written first; the arrive below releases them
+    pp = unit_plans<T>(uint64_t(n), uint64_t(p0), uint32_t(count));
+    span_tail(st + g.off_mu, sc.means, pp.mu);
+    span_tail(st + g.off_gc, sc.g_rgb, pp.mu);
+    total += 2u * pp.mu.bulk;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      span_tail(st + g.off_c0 + c * g.c0_cap, sc.c0, pp.c0[c]);
+      total += pp.c0[c].bulk;
+    }
+  }
+  mbar_arrive_expect_tx(bar, total);
+  // parameter plane p of the unit: plane stride N L sizeof(T) bytes, advanced by additions
+  const uint64_t stride = uint64_t(n) * L * sizeof(T);
+  const unsigned char* src = static_cast<const unsigned char*>(sc.params) + uint64_t(p0) * L * sizeof(T);
+#pragma unroll
+  for (int p = 0; p < P; ++p, src += stride) bulk_g2s(st + size_t(p) * g.plane_bytes, src, bytes, bar);
+  if (stage_m) {
+    if (pp.mu.bulk) {
+      bulk_g2s(st + g.off_mu, reinterpret_cast<const unsigned char*>(sc.means) + pp.mu.src, pp.mu.bulk, bar);
+      bulk_g2s(st + g.off_gc, reinterpret_cast<const unsigned char*>(sc.g_rgb) + pp.mu.src, pp.mu.bulk, bar);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      if (pp.c0[c].bulk)
+        bulk_g2s(st + g.off_c0 + c * g.c0_cap, static_cast<const unsigned char*>(sc.c0) + pp.c0[c].src,
+                 pp.c0[c].bulk, bar);
   }
   return true;
 }
 
-template <int FRAME, typename T, int FLAGS>
+template <int FRAME, typename T, int FLAGS, bool PAIRS>
 __global__ void __launch_bounds__(256, 2) batched_staged_kernel(const BatchArgs b) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr int NS = batch_stages<T>();
   using W = typename RawWord<T>::type;
-  __shared__ SceneDev sd[kMaxScenes];
   __shared__ StageMeta meta[kMaxBatchStages];
   extern __shared__ __align__(128) unsigned char smem[];
-  const uint32_t sbytes = batch_stage_bytes<T, P>();
+  constexpr TileGeom g = batch_geom<T, P>();
+  constexpr uint32_t sbytes = g.stage_bytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * sbytes);
   uint64_t* empty = full + NS;
+  SceneDev* sd = reinterpret_cast<SceneDev*>(empty + NS);  // the scene table (n_scenes records)
   {
     const int words = int(b.n_scenes * sizeof(SceneDev) / sizeof(uint32_t));
     const uint32_t* src = reinterpret_cast<const uint32_t*>(b.table);
@@ -290,8 +286,12 @@ __global__ void __launch_bounds__(256, 2) batched_staged_kernel(const BatchArgs 
     fence_barrier_init();
   }
   __syncthreads();
-  // producer state (thread 0): stages whose copies are in flight and the parity of
-  // the phase each of them completes, for the drain on error
+  // Producer role, rotating as in the single-scene staged kernel: the refill of
+  // the stage read in iteration j is issued in iteration j + 1 by lane 0 of warp
+  // j mod (warps per block). An issuing lane keeps the stages it filled that it
+  // has not yet seen complete (and the parity of that phase) for the drain on
+  // error, and its own scene cursor (the units it is handed increase).
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   uint32_t pending = 0, pend_par = 0;
   int issue_scene = 0;
   auto next_unit = [&](uint32_t it) -> uint32_t {
@@ -304,10 +304,8 @@ __global__ void __launch_bounds__(256, 2) batched_staged_kernel(const BatchArgs 
         pending |= 1u << s;
   }
   bool failed = false;
-  int cur_scene = -1;
-  EvalArgs a{};
   for (uint32_t it = 0;; ++it) {
-    if (threadIdx.x == 0 && it >= 1) {
+    if (it >= 1 && lane == 0 && warp == (it - 1) % n_warps) {
       const uint32_t pit = it - 1;
       const int ps = int(pit % NS);
       if (mbar_wait(&empty[ps], (pit / NS) & 1u, b.dev_err)) {
@@ -327,19 +325,15 @@ __global__ void __launch_bounds__(256, 2) batched_staged_kernel(const BatchArgs 
       failed = true;
       break;  // warp-uniform; the other warps give up on their own waits
     }
-    if (threadIdx.x == 0) pending &= ~(1u << s);
+    pending &= ~(1u << s);  // this stage's fill (whoever issued it) has landed
     const StageMeta m = meta[s];
     if (m.unit == kUnitEnd) break;  // block-uniform: every warp reads the same stage
     RawItem<T, P> r;
     r.ok = 0;
     int64_t prim = 0;
     int l0 = 0;
+    const EvalArgs& sc = sd[m.scene >= 0 ? m.scene : 0].args;
     if (m.scene >= 0) {
-      const SceneDev& sc = sd[m.scene];
-      if (m.scene != cur_scene) {  // block-uniform
-        a = scene_args(sc, b);
-        cur_scene = m.scene;
-      }
       const int local = int(threadIdx.x) >> sc.slice_log2;
       l0 = 2 * (int(threadIdx.x) & ((1 << sc.slice_log2) - 1));
       prim = m.p0 + local;
@@ -349,24 +343,31 @@ __global__ void __launch_bounds__(256, 2) batched_staged_kernel(const BatchArgs 
           r.i = 0;
           const unsigned char* st = smem + s * sbytes;
           if (m.staged & 2) {
-            const float* mu = reinterpret_cast<const float*>(st + size_t(P) * batch_plane_bytes<T, P>());
+            // a unit's first primitive is a multiple of 256/S >= 16: the means start
+            // on a 16-byte boundary, diffuse-colour plane c at c0_head(c, N)
+            const float* mu = reinterpret_cast<const float*>(st + g.off_mu);
+            const float* gc = reinterpret_cast<const float*>(st + g.off_gc);
 #pragma unroll
             for (int c = 0; c < 3; ++c) r.mu[c] = mu[3 * local + c];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) r.gc[c] = mu[256 * 3 + 3 * local + c];
+            for (int c = 0; c < 3; ++c) r.gc[c] = gc[3 * local + c];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              r.c0[c] = to_float(*reinterpret_cast<const T*>(st + g.off_c0 + c * g.c0_cap + c0_head<T>(c, sc.n) +
+                                                             local * sizeof(T)));
           } else {
 #pragma unroll
             for (int c = 0; c < 3; ++c) r.mu[c] = __ldg(sc.means + 3 * prim + c);
 #pragma unroll
             for (int c = 0; c < 3; ++c) r.gc[c] = __ldg(sc.g_rgb + 3 * prim + c);
-          }
-          const T* c0 = static_cast<const T*>(sc.c0);
+            const T* c0 = static_cast<const T*>(sc.c0);
 #pragma unroll
-          for (int c = 0; c < 3; ++c) r.c0[c] = load1<T>(c0 + c * sc.n + prim);
+            for (int c = 0; c < 3; ++c) r.c0[c] = load1<T>(c0 + c * sc.n + prim);
+          }
           if (l0 < sc.n_lobes) {
 #pragma unroll
             for (int p = 0; p < P; ++p)
-              r.w[p] = *reinterpret_cast<const W*>(st + size_t(p) * batch_plane_bytes<T, P>() +
+              r.w[p] = *reinterpret_cast<const W*>(st + size_t(p) * g.plane_bytes +
                                                    size_t(local * sc.n_lobes + l0) * sizeof(T));
           }
         }
@@ -376,10 +377,10 @@ __global__ void __launch_bounds__(256, 2) batched_staged_kernel(const BatchArgs 
     }
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
-    if (m.scene >= 0) eval_item<FRAME, T, int64_t, kFwdBwd, false, FLAGS>(a, r, prim, l0);
+    if (m.scene >= 0) eval_scene_item<FRAME, T, FLAGS, PAIRS>(sc, r, prim, l0);
   }
   // on a failed wait, let the copies this block started finish before leaving (bounded)
-  if (threadIdx.x == 0 && failed) {
+  if (lane == 0 && failed) {
     for (int s = 0; s < NS; ++s)
       if (pending & (1u << s)) mbar_wait(&full[s], (pend_par >> s) & 1u, nullptr, 1u << 16);
   }
@@ -410,8 +411,9 @@ extern "C" nasg_status nasgabor_batched_prepare(const nasg_scene* scenes, int32_
     return NASG_ERR_RANGE;
   if (modes->act_mode != NASG_ACT_RAW && modes->act_mode != NASG_ACT_IDENTITY) return NASG_ERR_RANGE;
   const int es = elem_size(modes->param_dtype);
-  std::vector<SceneDev> tab(n_scenes);
+  std::vector<SceneDev> tab(n_scenes, SceneDev{});
   int64_t tiles = 0, prims = 0, lobes = 0;
+  bool pair_path = true;
   for (int j = 0; j < n_scenes; ++j) {
     const nasg_scene& s = scenes[j];
     if (s.n < 0 || s.n > (int64_t(1) << 40) || s.n_lobes < 1 || s.n_lobes > NASG_MAX_LOBES) return NASG_ERR_RANGE;
@@ -424,25 +426,44 @@ extern "C" nasg_status nasgabor_batched_prepare(const nasg_scene* scenes, int32_
     // pair loads need 2-element alignment when L is even
     if (s.n_lobes % 2 == 0 && s.params && !aligned(s.params, uintptr_t(2 * es))) return NASG_ERR_ALIGN;
     SceneDev& d = tab[j];
-    d.params = s.params;
-    d.c0 = s.c0;
-    d.means = s.means;
-    d.g_rgb = s.g_rgb;
-    d.rgb = s.rgb;
-    d.g_params = s.g_params;
-    d.g_c0 = s.g_c0;
-    d.g_means = s.g_means;
-    d.n = s.n;
-    d.cam[0] = s.cam[0];
-    d.cam[1] = s.cam[1];
-    d.cam[2] = s.cam[2];
-    d.n_lobes = s.n_lobes;
-    d.slice_log2 = slice_log2(s.n_lobes);
+    EvalArgs& a = d.args;
+    a.params = s.params;
+    a.c0 = s.c0;
+    a.means = s.means;
+    a.cam[0] = s.cam[0];
+    a.cam[1] = s.cam[1];
+    a.cam[2] = s.cam[2];
+    a.idx = nullptr;
+    a.n_items = s.n;
+    a.n = s.n;
+    a.n_lobes = s.n_lobes;
+    a.slice_log2 = slice_log2(s.n_lobes);
+    a.slice = 1 << a.slice_log2;
+    a.identity = modes->act_mode == NASG_ACT_IDENTITY;
+    a.normalised = modes->norm_mode != NASG_NORM_NONE;
+    a.exact = modes->norm_mode == NASG_NORM_EXACT;
+    a.accumulate = 0;
+    a.g_rgb = s.g_rgb;
+    a.rgb = s.rgb;
+    a.g_params = s.g_params;
+    a.g_c0 = s.g_c0;
+    a.g_means = s.g_means;
+    a.dev_err = device_error_word();
+    {
+      const int P = nasg_param_planes(modes->frame_mode, NASG_FAMILY_NASGABOR);
+      const int64_t lim = int64_t(1) << 31;
+      const bool even = s.n_lobes % 2 == 0 && (!s.params || aligned(s.params, uintptr_t(2 * es))) &&
+                        (!s.g_params || aligned(s.g_params, 8));
+      const bool idx32 = s.n * s.n_lobes * P < lim && 3 * s.n < lim;
+      pair_path = pair_path && even && idx32;
+    }
     d.staged = (s.n_lobes % 2 == 0) && s.params && aligned(s.params, 16) && (s.n * s.n_lobes * es) % 16 == 0
-                   ? 1 | (aligned(s.means, 16) && aligned(s.g_rgb, 16) ? 2 : 0)
+                   ? 1 | (aligned(s.means, 16) && aligned(s.g_rgb, 16) && aligned(s.c0, 16) ? 2 : 0)
                    : 0;
     d.tile_begin = tiles;
-    const int64_t tile_prims = int64_t(256 >> d.slice_log2) * sub_tiles;
+    d.unit_begin = tiles * sub_tiles;
+    d.pad = 0;
+    const int64_t tile_prims = int64_t(256 >> a.slice_log2) * sub_tiles;
     tiles += (s.n + tile_prims - 1) / tile_prims;
     prims += s.n;
     lobes += s.n * s.n_lobes;
@@ -463,6 +484,8 @@ extern "C" nasg_status nasgabor_batched_prepare(const nasg_scene* scenes, int32_
   plan->norm_mode = modes->norm_mode;
   plan->act_mode = modes->act_mode;
   plan->sub_tiles = sub_tiles;
+  plan->pair_path = pair_path ? 1 : 0;
+  plan->reserved = 0;
   plan->total_tiles = tiles;
   plan->total_prims = prims;
   plan->total_lobes = lobes;
@@ -471,14 +494,16 @@ extern "C" nasg_status nasgabor_batched_prepare(const nasg_scene* scenes, int32_
 }
 
 namespace nasg {
-template <int FRAME, typename T>
-static nasg_status launch_batched(const BatchArgs& b, int blocks_per_sm, bool staged, cudaStream_t s) {
-  const bool dflt = b.identity == 0 && b.normalised != 0 && b.exact == 0;
+// dflt: raw activations and approximate normalisation (the modes compiled in).
+template <int FRAME, typename T, bool PAIRS>
+static nasg_status launch_batched_k(const BatchArgs& b, int blocks_per_sm, bool staged, bool dflt, cudaStream_t s) {
   if (staged) {
     constexpr int P = FrameTraits<FRAME>::P;
-    auto k = dflt ? batched_staged_kernel<FRAME, T, kFlagsDefault> : batched_staged_kernel<FRAME, T, kFlagsRuntime>;
+    auto k = dflt ? batched_staged_kernel<FRAME, T, kFlagsDefault, PAIRS>
+                  : batched_staged_kernel<FRAME, T, kFlagsRuntime, PAIRS>;
     constexpr int NS = batch_stages<T>();
-    const size_t smem = size_t(NS) * batch_stage_bytes<T, P>() + 2 * NS * sizeof(uint64_t);
+    const size_t smem = size_t(NS) * batch_stage_bytes<T, P>() + 2 * NS * sizeof(uint64_t) +
+                        size_t(b.n_scenes) * sizeof(SceneDev);
     static size_t configured[2] = {0, 0};  // per instantiation pair (default, run-time flags)
     size_t& cfg = configured[dflt ? 0 : 1];
     if (smem > cfg) {
@@ -496,7 +521,7 @@ static nasg_status launch_batched(const BatchArgs& b, int blocks_per_sm, bool st
     k<<<unsigned(grid), 256, smem, s>>>(b);
     return check_launch();
   }
-  auto k = dflt ? batched_kernel<FRAME, T, kFlagsDefault> : batched_kernel<FRAME, T, kFlagsRuntime>;
+  auto k = dflt ? batched_kernel<FRAME, T, kFlagsDefault, PAIRS> : batched_kernel<FRAME, T, kFlagsRuntime, PAIRS>;
   int fit = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k, 256, 0) != cudaSuccess || fit < 1) fit = 1;
   const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : fit;
@@ -505,6 +530,13 @@ static nasg_status launch_batched(const BatchArgs& b, int blocks_per_sm, bool st
   if (grid < 1) return NASG_OK;
   k<<<unsigned(grid), 256, 0, s>>>(b);
   return check_launch();
+}
+
+template <int FRAME, typename T>
+static nasg_status launch_batched(const BatchArgs& b, int blocks_per_sm, bool staged, bool pairs, bool dflt,
+                                  cudaStream_t s) {
+  return pairs ? launch_batched_k<FRAME, T, true>(b, blocks_per_sm, staged, dflt, s)
+               : launch_batched_k<FRAME, T, false>(b, blocks_per_sm, staged, dflt, s);
 }
 }  // namespace nasg
 
@@ -518,6 +550,8 @@ extern "C" nasg_status nasgabor_batched_run(const nasg_batch_plan* plan, const n
   const int staged = tuning ? tuning->staged : 0;
   if (dynamic != 0 && dynamic != 1) return NASG_ERR_RANGE;
   if (staged != 0 && staged != 1) return NASG_ERR_RANGE;
+  if (plan->pair_path != 0 && plan->pair_path != 1) return NASG_ERR_RANGE;
+  const bool pairs = plan->pair_path != 0;
   unsigned char* ws = static_cast<unsigned char*>(plan->workspace);
   cudaStream_t st = as_stream(stream);
   BatchArgs b{};
@@ -527,19 +561,17 @@ extern "C" nasg_status nasgabor_batched_run(const nasg_batch_plan* plan, const n
   b.sub_tiles = plan->sub_tiles;
   b.total_tiles = plan->total_tiles;
   b.dynamic = dynamic;
-  b.identity = plan->act_mode == NASG_ACT_IDENTITY;
-  b.normalised = plan->norm_mode != NASG_NORM_NONE;
-  b.exact = plan->norm_mode == NASG_NORM_EXACT;
   b.dev_err = device_error_word();
+  const bool dflt = plan->act_mode == NASG_ACT_RAW && plan->norm_mode == NASG_NORM_APPROX;
   if (dynamic && cudaMemsetAsync(b.counter, 0, sizeof(uint32_t), st) != cudaSuccess) return check_launch();
   const bool quat = plan->frame_mode == NASG_FRAME_QUAT;
   const bool bf16 = plan->param_dtype == NASG_DTYPE_BF16;
   if (quat) {
-    return bf16 ? launch_batched<NASG_FRAME_QUAT, __nv_bfloat16>(b, bps, staged, st)
-                : launch_batched<NASG_FRAME_QUAT, float>(b, bps, staged, st);
+    return bf16 ? launch_batched<NASG_FRAME_QUAT, __nv_bfloat16>(b, bps, staged, pairs, dflt, st)
+                : launch_batched<NASG_FRAME_QUAT, float>(b, bps, staged, pairs, dflt, st);
   }
-  return bf16 ? launch_batched<NASG_FRAME_COS, __nv_bfloat16>(b, bps, staged, st)
-              : launch_batched<NASG_FRAME_COS, float>(b, bps, staged, st);
+  return bf16 ? launch_batched<NASG_FRAME_COS, __nv_bfloat16>(b, bps, staged, pairs, dflt, st)
+              : launch_batched<NASG_FRAME_COS, float>(b, bps, staged, pairs, dflt, st);
 }
 
 extern "C" nasg_status nasgabor_batched_autotune(const nasg_scene* scenes, int32_t n_scenes,

@@ -17,6 +17,7 @@
 
 #include "nasg_device.cuh"
 #include "nasg_host.h"
+#include "nasg_span.h"
 #include "nasg_tma.cuh"
 
 namespace nasg {
@@ -404,61 +405,72 @@ __global__ void __launch_bounds__(256, 2) eval_kernel(const EvalArgs a) {
 // arrives on the stage's "empty" mbarrier; one iteration later the elected
 // thread waits for that stage to be empty and refills it with the tile kStages
 // ahead. No block-wide barrier is taken inside the loop, and every wait is
-// bounded. Requirements (checked on the host): no index list, N % 8 == 0,
-// L even, 16-byte aligned buffers, 32-bit offsets.
+// bounded. Requirements (checked on the host): no index list, L even,
+// N L sizeof(T) a multiple of 16 bytes, 16-byte aligned buffers, 32-bit
+// offsets. Any N otherwise: the spans of the means, upstream gradients and
+// diffuse colours are moved by span plans (rounded to 16-byte boundaries, the
+// last bytes of a buffer by plain loads).
 // ---------------------------------------------------------------------------
 constexpr int kStages = 3;
 
-struct TileGeom {
-  uint32_t tp;          // primitives per tile
-  uint32_t plane_bytes; // bytes of one plane's span in a stage
-  uint32_t off_mu, off_gc, off_c0, stage_bytes;
-};
-
-template <typename T, int P>
-__host__ __device__ inline TileGeom tile_geom(int slice_log2, int n_lobes) {
-  TileGeom g;
-  g.tp = 256u >> slice_log2;
-  g.plane_bytes = g.tp * uint32_t(n_lobes) * uint32_t(sizeof(T));
-  g.off_mu = P * g.plane_bytes;
-  g.off_gc = g.off_mu + g.tp * 12u;
-  g.off_c0 = g.off_gc + g.tp * 12u;
-  g.stage_bytes = (g.off_c0 + 3u * g.tp * uint32_t(sizeof(T)) + 127u) & ~127u;
-  return g;
+// Moves the plain-load part of a span plan (the last bytes of a buffer).
+__device__ __forceinline__ void span_tail(unsigned char* dst, const void* base, const SpanPlan& s) {
+  if (s.tail == 0) return;
+  const uint16_t* src = reinterpret_cast<const uint16_t*>(static_cast<const unsigned char*>(base) + s.src + s.bulk);
+  uint16_t* d = reinterpret_cast<uint16_t*>(dst + s.bulk);
+  for (uint32_t j = 0; j < s.tail / 2u; ++j) d[j] = src[j];
 }
 
-template <typename T, int P, bool FWD, bool BWD>
+// One tile's copies, issued by one elected thread (the plans of tile_span): the
+// plain-load tails first (released by the arrive), then the announcement of the
+// tile's bulk bytes, then the bulk copies. (Issuing them from the 32 lanes of a
+// warp side by side measured slower: the whole warp then waits on the stage.)
+template <typename T, int P, bool FWD, bool BWD, bool ANYN>
 __device__ __forceinline__ void issue_tile(const EvalArgs& a, const TileGeom& g, uint32_t tile, unsigned char* st,
                                            uint64_t* bar) {
   const uint32_t n = uint32_t(a.n), L = uint32_t(a.n_lobes);
   const uint32_t p0 = tile * g.tp;
-  const uint32_t count = min(g.tp, n - p0);
-  const uint32_t bp = count * L * uint32_t(sizeof(T));
-  const uint32_t bm = count * 12u;
-  const uint32_t bc = count * uint32_t(sizeof(T));
-  const uint32_t total = P * bp + bm + (BWD ? bm : 0u) + (FWD ? 3u * bc : 0u);
+  const uint32_t bp = tile_span<T, P, ANYN>(g, n, L, tile, 0).bulk;  // every parameter plane's span
+  const SpanPlan pm = tile_span<T, P, ANYN>(g, n, L, tile, P);
+  SpanPlan pc[3];
+  uint32_t total = P * bp + (BWD ? 2u : 1u) * pm.bulk;
+  if (ANYN) {
+    span_tail(st + g.off_mu, a.means, pm);
+    if (BWD) span_tail(st + g.off_gc, a.g_rgb, pm);
+  }
+  if (FWD) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      pc[c] = tile_span<T, P, ANYN>(g, n, L, tile, P + 2 + c);
+      if (ANYN) span_tail(st + g.off_c0 + c * g.c0_cap, a.c0, pc[c]);
+      total += pc[c].bulk;
+    }
+  }
   mbar_arrive_expect_tx(bar, total);
   const T* params = static_cast<const T*>(a.params);
   const uint32_t NL = n * L;
 #pragma unroll
   for (int p = 0; p < P; ++p) bulk_g2s(st + p * g.plane_bytes, params + p * NL + p0 * L, bp, bar);
-  bulk_g2s(st + g.off_mu, a.means + 3u * p0, bm, bar);
-  if (BWD) bulk_g2s(st + g.off_gc, a.g_rgb + 3u * p0, bm, bar);
+  if (pm.bulk) {
+    bulk_g2s(st + g.off_mu, reinterpret_cast<const unsigned char*>(a.means) + pm.src, pm.bulk, bar);
+    if (BWD) bulk_g2s(st + g.off_gc, reinterpret_cast<const unsigned char*>(a.g_rgb) + pm.src, pm.bulk, bar);
+  }
   if (FWD) {
-    const T* c0 = static_cast<const T*>(a.c0);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) bulk_g2s(st + g.off_c0 + c * g.tp * sizeof(T), c0 + c * n + p0, bc, bar);
+    for (int c = 0; c < 3; ++c)
+      if (pc[c].bulk)
+        bulk_g2s(st + g.off_c0 + c * g.c0_cap, static_cast<const unsigned char*>(a.c0) + pc[c].src, pc[c].bulk, bar);
   }
 }
 
-template <int FRAME, typename T, int MODE, int FLAGS>
+template <int FRAME, typename T, int MODE, int FLAGS, bool ANYN>
 __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr bool FWD = (MODE & kFwd) != 0;
   constexpr bool BWD = (MODE & kBwd) != 0;
   using W = typename RawWord<T>::type;
   extern __shared__ __align__(128) unsigned char smem[];
-  const TileGeom g = tile_geom<T, P>(a.slice_log2, a.n_lobes);
+  const TileGeom g = tile_geom<T, P, ANYN>(a.slice_log2, a.n_lobes);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * g.stage_bytes);  // tile landed
   uint64_t* empty = full + kStages;                                             // tile read by all warps
   const uint32_t n = uint32_t(a.n), L = uint32_t(a.n_lobes);
@@ -473,46 +485,54 @@ __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
     fence_barrier_init();
   }
   __syncthreads();
+  // Producer role: the refill of the stage read in iteration j is issued, in
+  // iteration j + 1, by lane 0 of warp j mod (warps per block), so the copy work
+  // rotates over the warps (and the SM's sub-partitions) instead of loading one
+  // warp. Each issuing lane remembers the stages it filled that it has not yet
+  // seen complete (and the parity of that phase), to let them land on an error.
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  uint32_t pending = 0, pend_par = 0;
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int s = 0; s < kStages; ++s) {
       const uint32_t tile = blockIdx.x + s * gridDim.x;
-      if (tile < n_tiles) issue_tile<T, P, FWD, BWD>(a, g, tile, smem + s * g.stage_bytes, &full[s]);
+      if (tile < n_tiles) {
+        issue_tile<T, P, FWD, BWD, ANYN>(a, g, tile, smem + s * g.stage_bytes, &full[s]);
+        pending |= 1u << s;
+      }
     }
   }
   const uint32_t local = threadIdx.x >> a.slice_log2;
   const int l0 = 2 * (threadIdx.x & (a.slice - 1));
-  bool refilled = true;  // producer: whether this iteration's refill was issued
   for (uint32_t it = 0;; ++it) {
     const uint32_t tile = blockIdx.x + it * gridDim.x;
     if (tile >= n_tiles) break;  // block-uniform
     // producer: refill the stage read in the previous iteration (one iteration
     // of slack, so the wait for its last reader is normally already over)
-    if (threadIdx.x == 0 && it >= 1) {
+    if (it >= 1 && lane == 0 && warp == (it - 1) % n_warps) {
       const uint32_t pit = it - 1;
-      const uint32_t next = blockIdx.x + (pit + kStages) * gridDim.x;
+      const uint32_t nit = pit + kStages;
+      const uint32_t next = blockIdx.x + nit * gridDim.x;
       const int ps = pit % kStages;
-      refilled = false;
       if (next < n_tiles && mbar_wait(&empty[ps], (pit / kStages) & 1u, a.dev_err)) {
         fence_proxy_async();
-        issue_tile<T, P, FWD, BWD>(a, g, next, smem + ps * g.stage_bytes, &full[ps]);
-        refilled = true;
+        issue_tile<T, P, FWD, BWD, ANYN>(a, g, next, smem + ps * g.stage_bytes, &full[ps]);
+        pending |= 1u << ps;
+        pend_par = (pend_par & ~(1u << ps)) | (((nit / kStages) & 1u) << ps);
       }
     }
     const int s = it % kStages;
     const unsigned char* st = smem + s * g.stage_bytes;
     const bool arrived = __all_sync(0xffffffffu, mbar_wait(&full[s], (it / kStages) & 1u, a.dev_err));
     if (!arrived) {  // warp-uniform; the other warps give up on their own waits
-      // the producer lets the copies it started land before the block leaves: the
-      // stages of iterations it .. it + kStages - 1 (the last only if refilled)
-      if (threadIdx.x == 0) {
-        for (uint32_t j = it; j < it + kStages; ++j) {
-          if (blockIdx.x + j * gridDim.x >= n_tiles || (j == it + kStages - 1 && !refilled)) continue;
-          mbar_wait(&full[j % kStages], (j / kStages) & 1u, nullptr, 1u << 16);
-        }
+      // let the copies this lane started land before the block leaves (bounded)
+      if (lane == 0) {
+        for (int q = 0; q < kStages; ++q)
+          if (pending & (1u << q)) mbar_wait(&full[q], (pend_par >> q) & 1u, nullptr, 1u << 16);
       }
       return;
     }
+    pending &= ~(1u << s);  // this stage's fill (whoever issued it) has landed
     const uint32_t p0 = tile * g.tp;
     const uint32_t count = min(g.tp, n - p0);
     RawItem<T, P> r;
@@ -529,9 +549,10 @@ __global__ void __launch_bounds__(256, 2) eval_tma_kernel(const EvalArgs a) {
       }
       if (FWD) {
         // plain shared-memory reads (load1 uses the global read-only path)
-        const T* c0 = reinterpret_cast<const T*>(st + g.off_c0);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) r.c0[c] = to_float(c0[c * g.tp + local]);
+        for (int c = 0; c < 3; ++c)
+          r.c0[c] = to_float(*reinterpret_cast<const T*>(st + g.off_c0 + c * g.c0_cap + c0_head<T, ANYN>(c, n) +
+                                                         local * sizeof(T)));
       }
       if (uint32_t(l0) < L) {
 #pragma unroll
@@ -587,7 +608,8 @@ nasg_status launch_idx(const EvalArgs& a, bool even, cudaStream_t s) {
 // The TMA-staged kernel applies (see its requirements above).
 template <int FRAME, typename T>
 bool tma_eligible(const EvalArgs& a, bool even) {
-  if (!even || a.idx != nullptr || a.n % 8 != 0 || a.n_items != a.n) return false;
+  if (!even || a.idx != nullptr || a.n_items != a.n) return false;
+  if (a.n * a.n_lobes * int64_t(sizeof(T)) % 16 != 0) return false;  // parameter planes on 16-byte boundaries
   if (a.n * a.n_lobes * FrameTraits<FRAME>::P >= (int64_t(1) << 31)) return false;
   const void* ptrs[] = {a.params, a.means, a.c0, a.g_rgb};
   for (const void* p : ptrs)
@@ -595,12 +617,12 @@ bool tma_eligible(const EvalArgs& a, bool even) {
   return true;
 }
 
-template <int MODE, int FRAME, typename T, int FLAGS>
-nasg_status launch_tma(const EvalArgs& a, cudaStream_t s) {
+template <int MODE, int FRAME, typename T, int FLAGS, bool ANYN>
+nasg_status launch_tma_geom(const EvalArgs& a, cudaStream_t s) {
   constexpr int P = FrameTraits<FRAME>::P;
-  const TileGeom g = tile_geom<T, P>(a.slice_log2, a.n_lobes);
+  const TileGeom g = tile_geom<T, P, ANYN>(a.slice_log2, a.n_lobes);
   const size_t smem = size_t(kStages) * g.stage_bytes + 2 * kStages * sizeof(uint64_t);
-  auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS>;
+  auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS, ANYN>;
   static size_t configured = 0;  // per instantiation
   if (smem > configured) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
@@ -613,6 +635,13 @@ nasg_status launch_tma(const EvalArgs& a, cudaStream_t s) {
   const uint32_t cap = uint32_t(sm_count() * per_sm);
   k<<<n_tiles < cap ? n_tiles : cap, 256, smem, s>>>(a);
   return check_launch();
+}
+
+// N % 8 == 0: packed stages and exact spans; any other N: span plans.
+template <int MODE, int FRAME, typename T, int FLAGS>
+nasg_status launch_tma(const EvalArgs& a, cudaStream_t s) {
+  return a.n % 8 == 0 ? launch_tma_geom<MODE, FRAME, T, FLAGS, false>(a, s)
+                      : launch_tma_geom<MODE, FRAME, T, FLAGS, true>(a, s);
 }
 
 template <int MODE, int FRAME, typename T>

@@ -127,19 +127,24 @@ __global__ void __launch_bounds__(256) sh_bwd_kernel(const ShArgs a) {
     float g[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) g[c] = __ldg(a.g_rgb + 3 * i + c);
+    // dLoss/dd first (coefficient loads only), then the gradient stores: the
+    // compiler may not move a load of coeffs past a store to g_coeffs (they could
+    // alias), so interleaving the two would leave one load in flight per thread.
     float gd[3] = {0.f, 0.f, 0.f};
+    if (a.g_means) {
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      float gy = 0.f;
+      for (int j = 0; j < NB; ++j) {
+        float gy = 0.f;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int64_t o = (int64_t(j) * 3 + c) * n + i;
-        a.g_coeffs[o] = g[c] * Y[j];
-        if (a.g_means) gy = fmaf(g[c], __ldg(a.coeffs + o), gy);
+        for (int c = 0; c < 3; ++c) gy = fmaf(g[c], __ldg(a.coeffs + (int64_t(j) * 3 + c) * n + i), gy);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gd[k] = fmaf(gy, dY[j][k], gd[k]);
       }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) gd[k] = fmaf(gy, dY[j][k], gd[k]);
     }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a.g_coeffs[(int64_t(j) * 3 + c) * n + i] = g[c] * Y[j];
     if (a.g_means) {
       float gm[3];
       dir_grad(d, gd, inv_dist, gm);

@@ -49,6 +49,25 @@ SIZES = [(5000, 8), (1, 4), (777, 16), (12345, 4), (0, 8), (4099, 3), (2048, 8),
 def test_batched_equals_single_scene_kernel(lib, bf16, dynamic, sub_tiles, staged):
     scenes = _scenes(SIZES, 300, bf16)
     b = lib.Batch(scenes, sub_tiles=sub_tiles)
+    assert b.plan.pair_path == 0          # odd L in the batch: the general kernel
+    b.tuning.dynamic = dynamic
+    b.tuning.staged = staged
+    b.run()
+    lib.nasg_device_status()
+    _compare_with_single(lib, scenes)
+
+
+PAIR_SIZES = [(5001, 8), (777, 16), (12346, 4), (1, 8), (2048, 8), (0, 4), (3, 2), (4093, 4)]
+
+
+@pytest.mark.parametrize("bf16", [True, False])
+@pytest.mark.parametrize("dynamic,sub_tiles,staged", [(1, 1, 0), (0, 3, 0), (1, 1, 1), (0, 2, 1), (1, 8, 1)])
+def test_batched_pair_path_equals_single_scene_kernel(lib, bf16, dynamic, sub_tiles, staged):
+    """Even L only (the pair-load/store kernel with 32-bit offsets), ragged N, staged and
+    direct schedules, scenes whose planes can and cannot be bulk-copied."""
+    scenes = _scenes(PAIR_SIZES, 350, bf16)
+    b = lib.Batch(scenes, sub_tiles=sub_tiles)
+    assert b.plan.pair_path == 1
     b.tuning.dynamic = dynamic
     b.tuning.staged = staged
     b.run()
@@ -75,6 +94,7 @@ def test_batched_oracle_parity(lib):
     import torch
     scenes = _scenes([(2000, 8), (900, 16), (1500, 4)], 500, True)
     b = lib.Batch(scenes)
+    assert b.plan.pair_path == 1          # even L only: the pair-load/store kernel
     b.run()
     torch.cuda.synchronize()
     for sc in scenes:

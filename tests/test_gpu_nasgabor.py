@@ -329,11 +329,16 @@ def test_bounded_wait_reports_device_error(lib):
 
 
 @pytest.mark.parametrize("bf16,n,L", [(True, 4096, 8), (False, 4096, 8), (True, 1000, 4), (True, 2056, 16),
-                                      (False, 1048, 2), (True, 8, 8)])
+                                      (False, 1048, 2), (True, 8, 8),
+                                      # any N: diffuse-colour planes off 16-byte boundaries, buffer ends
+                                      # inside a 16-byte unit (plain-load tails), single-tile cases
+                                      (True, 1001, 8), (True, 1003, 16), (True, 1002, 4), (False, 1037, 4),
+                                      (False, 65, 8), (True, 1, 8), (True, 7, 8), (False, 13, 2),
+                                      (False, 10, 6), (True, 129, 32)])
 def test_staged_path_matches_oracle(lib, bf16, n, L):
-    """Sizes that take the bulk-copy staged kernel (N % 8 == 0, even L), with a
-    ragged last tile, against the oracle; and the same against the register path
-    (an offset view breaks the 16-byte alignment the staged kernel needs)."""
+    """Sizes that take the bulk-copy staged kernel (even L, N L sizeof(T) a multiple
+    of 16 bytes), with ragged last tiles, against the oracle; and the same against the
+    register path (an offset view breaks the 16-byte alignment the staged kernel needs)."""
     import torch
     w = inputs.point_cloud_workload(n, L, 31 + n + L)
     _check_forward(lib, w, bf16)
