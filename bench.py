@@ -83,12 +83,12 @@ def load_peaks():
 
 
 def kernel_source_hash():
-    """Hash of every source the headline kernel is compiled from (csrc/nasg_*.cuh, nasg_eval*.cu)."""
+    """Hash of every source the headline kernel is compiled from (csrc/nasg_*.cuh, nasg_*.h, nasg_eval*.cu)."""
     csrc = os.path.join(ROOT, "paper_2606_09794_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(csrc)):
-        if (f.startswith("nasg_") and f.endswith(".cuh")) or (f.startswith("nasg_eval") and f.endswith(".cu")) \
-                or f == "nasg_host.h":
+        if (f.startswith("nasg_") and (f.endswith(".cuh") or f.endswith(".h"))) or \
+                (f.startswith("nasg_eval") and f.endswith(".cu")):
             with open(os.path.join(csrc, f), "rb") as fh:
                 h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]

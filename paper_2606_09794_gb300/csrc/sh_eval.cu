@@ -114,7 +114,11 @@ __global__ void __launch_bounds__(256) sh_fwd_kernel(const ShArgs a) {
 }
 
 template <int DEG>
-__global__ void __launch_bounds__(256) sh_bwd_kernel(const ShArgs a) {
+// 64 registers (4 blocks of 256 threads per SM): with all 48 coefficient loads of
+// a thread issued before its first use, occupancy and loads in flight together
+// keep HBM busy (at 255 registers, one block per SM, it ran at 40 % of the copy
+// bandwidth; interleaved with the stores, at 65 %).
+__global__ void __launch_bounds__(256, 4) sh_bwd_kernel(const ShArgs a) {
   constexpr int NB = (DEG + 1) * (DEG + 1);
   const int64_t n = a.n;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
