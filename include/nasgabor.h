@@ -302,9 +302,11 @@ typedef struct nasg_batch_plan {
 
 /* Launch schedule: dynamic (1: tiles from an atomic counter, 0: round-robin),
  * blocks per SM (0: as many as fit), sub_tiles (the k prepare was called with),
- * staged (1: parameter spans moved into shared memory by bulk copies, four
- * sub-tiles ahead, for the scenes with even L and 16-byte aligned planes; the
- * others are loaded directly; 0: every load direct, one sub-tile ahead). */
+ * staged (1: each sub-tile's parameter spans, means, upstream gradients and
+ * diffuse colours moved into shared memory by bulk copies, four sub-tiles
+ * ahead (three for FP32), for the scenes with even L, N L sizeof(T) a multiple
+ * of 16 bytes and 16-byte aligned buffers; the others are loaded directly;
+ * 0: every load direct, one sub-tile ahead). */
 typedef struct nasg_batch_tuning {
   int32_t dynamic, blocks_per_sm, sub_tiles, staged;
 } nasg_batch_tuning;
