@@ -43,6 +43,15 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 __device__ __forceinline__ float bf16_rne(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 
+// Per-thread 8-byte asynchronous global -> shared copy (cp.async: no register
+// staging; source and destination 8-byte aligned), and the wait for all of the
+// thread's own copies. Used for the Adam state of a lane's two lobes, issued
+// before the lobe math so that its latency overlaps the arithmetic.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // One bias-corrected Adam update: m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
 // th <- th - (lr/bc1) m / (sqrt(v)/sqrt(bc2) + eps).
 __device__ __forceinline__ void adam(const StepArgs& s, float g, float& th, float& m, float& v) {
@@ -126,11 +135,14 @@ __device__ __forceinline__ bool step_phase1(const StepArgs& s, const RawItem<flo
   return mine;
 }
 
-// Phase two: Adam on the lane's two lobes for every plane, in batches of
-// planes: all loads of a batch first (master, m, v), then the updates and stores.
+// Phase two: Adam on the lane's two lobes for every plane. EVEN: master, m and v
+// were copied into the lane's shared-memory slots (tslot, mslot, vslot: plane p
+// at [p * 256]) while phase one ran. Otherwise in batches of planes: all loads of
+// a batch first (master, m, v), then the updates and stores.
 template <int P, typename IDX, bool EVEN>
-__device__ __forceinline__ void step_phase2(const StepArgs& s, IDX i, int l0, const float2* gslot) {
-  constexpr int kBatch = (P + 1) / 2;
+__device__ __forceinline__ void step_phase2(const StepArgs& s, IDX i, int l0, const float2* gslot,
+                                            const float2* tslot, const float2* mslot, const float2* vslot) {
+  constexpr int kBatch = EVEN ? P : (P + 1) / 2;
   const EvalArgs& a = s.e;
   const IDX n = IDX(a.n);
   const IDX L = IDX(a.n_lobes);
@@ -146,9 +158,9 @@ __device__ __forceinline__ void step_phase2(const StepArgs& s, IDX i, int l0, co
       if (p0 + j >= P) break;
       const IDX off = off0 + IDX(p0 + j) * NL;
       if (EVEN) {
-        th[j] = *reinterpret_cast<const float2*>(master + off);
-        mm[j] = *reinterpret_cast<const float2*>(s.m + off);
-        vv[j] = *reinterpret_cast<const float2*>(s.v + off);
+        th[j] = tslot[(p0 + j) * 256];
+        mm[j] = mslot[(p0 + j) * 256];
+        vv[j] = vslot[(p0 + j) * 256];
       } else {
         th[j] = make_float2(master[off], second ? master[off + 1] : 0.f);
         mm[j] = make_float2(s.m[off], second ? s.m[off + 1] : 0.f);
@@ -182,10 +194,16 @@ __device__ __forceinline__ void step_phase2(const StepArgs& s, IDX i, int l0, co
   }
 }
 
+// Shared memory of the step kernel: per thread, P gradient pairs and (EVEN) the
+// P master, m and v pairs of its two lobes, each plane-major over the block's
+// 256 threads (no sharing between threads, no barrier).
+template <int P, bool EVEN>
+constexpr size_t step_smem_bytes() { return size_t(EVEN ? 4 : 1) * P * 256 * sizeof(float2); }
+
 template <int FRAME, typename IDX, bool EVEN>
 __global__ void __launch_bounds__(256, 2) step_kernel(const StepArgs s) {
   constexpr int P = FrameTraits<FRAME>::P;
-  __shared__ float2 gbuf[P * 256];  // per-thread gradient slots (no sharing, no barrier)
+  extern __shared__ __align__(16) float2 step_smem[];
   const EvalArgs& a = s.e;
   int64_t items = a.n_items;
   if (s.n_dev) {
@@ -195,27 +213,56 @@ __global__ void __launch_bounds__(256, 2) step_kernel(const StepArgs s) {
   const int l0 = 2 * (threadIdx.x & (a.slice - 1));
   const IDX total = IDX(items) << a.slice_log2;
   const IDX stride = IDX(gridDim.x) * blockDim.x;
-  float2* gslot = gbuf + threadIdx.x;
+  float2* gslot = step_smem + threadIdx.x;
+  float2* tslot = gslot + P * 256;
+  float2* mslot = tslot + P * 256;
+  float2* vslot = mslot + P * 256;
+  const IDX L = IDX(a.n_lobes);
+  const IDX NL = IDX(a.n) * L;
+  const float* master = static_cast<const float*>(a.params);
   // block-uniform loop: every lane of a warp reaches the shuffles in phase one
   for (IDX t0 = IDX(blockIdx.x) * blockDim.x; t0 < total; t0 += stride) {
     RawItem<float, P> cur;
     IDX i = 0;
     fetch_item<float, P, IDX, EVEN, true, true>(a, total, t0 + threadIdx.x, l0, cur, i);
-    if (step_phase1<FRAME, IDX, EVEN>(s, cur, i, l0, gslot)) step_phase2<P, IDX, EVEN>(s, i, l0, gslot);
+    if (EVEN && cur.ok && IDX(l0) < L) {
+      IDX off = i * L + IDX(l0);
+#pragma unroll
+      for (int p = 0; p < P; ++p, off += NL) {
+        cp_async8(tslot + p * 256, master + off);
+        cp_async8(mslot + p * 256, s.m + off);
+        cp_async8(vslot + p * 256, s.v + off);
+      }
+    }
+    const bool mine = step_phase1<FRAME, IDX, EVEN>(s, cur, i, l0, gslot);
+    if (EVEN) cp_async_wait_all();
+    if (mine) step_phase2<P, IDX, EVEN>(s, i, l0, gslot, tslot, mslot, vslot);
   }
+}
+
+template <int FRAME, typename IDX, bool EVEN>
+static nasg_status launch_step_k(const StepArgs& s, cudaStream_t st) {
+  constexpr int P = FrameTraits<FRAME>::P;
+  constexpr size_t smem = step_smem_bytes<P, EVEN>();
+  auto k = step_kernel<FRAME, IDX, EVEN>;
+  static bool configured = false;  // per instantiation
+  if (!configured) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+      return check_launch();
+    configured = true;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+  const int64_t threads = s.e.n_items << s.e.slice_log2;
+  const unsigned need = grid_for(threads, 256);
+  const unsigned cap = unsigned(sm_count() * per_sm);
+  k<<<need < cap ? need : cap, 256, smem, st>>>(s);
+  return check_launch();
 }
 
 template <int FRAME, typename IDX>
 static nasg_status launch_step_idx(const StepArgs& s, bool even, cudaStream_t st) {
-  const int64_t threads = s.e.n_items << s.e.slice_log2;
-  if (even) {
-    auto k = step_kernel<FRAME, IDX, true>;
-    k<<<persistent_grid(k, threads, 256), 256, 0, st>>>(s);
-  } else {
-    auto k = step_kernel<FRAME, IDX, false>;
-    k<<<persistent_grid(k, threads, 256), 256, 0, st>>>(s);
-  }
-  return check_launch();
+  return even ? launch_step_k<FRAME, IDX, true>(s, st) : launch_step_k<FRAME, IDX, false>(s, st);
 }
 
 // ---------------------------------------------------------------------------

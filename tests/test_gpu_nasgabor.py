@@ -356,6 +356,30 @@ def test_staged_path_matches_oracle(lib, bf16, n, L):
     assert max(rel_l2(rg[p], fg[p]) for p in range(fg.shape[0])) < 1e-6
 
 
+@pytest.mark.parametrize("bf16,n,L", [(True, 1001, 8), (False, 4096, 8), (True, 1003, 16)])
+def test_staged_path_accumulate(lib, bf16, n, L):
+    """The staged kernel (any N) with accumulate: a second backward adds its gradients to
+    the first, bit for bit twice the single pass (same summation order); the fused pass's
+    gradients equal the backward's (rgb from the forward)."""
+    import torch
+    w = inputs.point_cloud_workload(n, L, 70 + n + L)
+    params, c0, _, _ = _prepare(w, bf16)
+    means, g_rgb = _dev(w.means), _dev(w.g_rgb)
+    g1 = lib.nasgabor_eval_bwd(params, means, w.cam, g_rgb, L)
+    gp, gc, gm = torch.zeros_like(g1[0]), torch.zeros_like(g1[1]), torch.zeros_like(g1[2])
+    for _ in range(2):
+        lib.nasgabor_eval_bwd(params, means, w.cam, g_rgb, L, g_params=gp, g_c0=gc, g_means=gm, accumulate=True)
+    rgb = lib.nasgabor_eval_fwd(params, c0, means, w.cam, L)
+    f = lib.nasgabor_fused_fwd_bwd(params, c0, means, w.cam, g_rgb, L)
+    lib.nasg_device_status()  # raises if a bounded wait gave up
+    torch.testing.assert_close(gp, 2 * g1[0], rtol=0, atol=0)
+    torch.testing.assert_close(gc, 2 * g1[1], rtol=0, atol=0)
+    torch.testing.assert_close(gm, 2 * g1[2], rtol=0, atol=0)
+    torch.testing.assert_close(f[0], rgb, rtol=1e-6, atol=1e-6)
+    fg, bg = f[1].cpu().numpy(), g1[0].cpu().numpy()
+    assert max(rel_l2(fg[p], bg[p]) for p in range(fg.shape[0])) < 1e-6
+
+
 @pytest.mark.parametrize("n,L,chunk,bf16", [(100_003, 8, 16384, True), (4096, 4, 1024, False), (777, 3, 64, True),
                                             (5000, 8, 8, False)])
 def test_host_resident_fused_matches_device_fused(lib, n, L, chunk, bf16):
