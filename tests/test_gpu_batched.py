@@ -75,6 +75,24 @@ def test_batched_pair_path_equals_single_scene_kernel(lib, bf16, dynamic, sub_ti
     _compare_with_single(lib, scenes)
 
 
+@pytest.mark.parametrize("bf16", [True, False])
+@pytest.mark.parametrize("staged", [0, 1])
+def test_batched_many_small_scenes(lib, bf16, staged):
+    """256 scenes (the table limit) of 1 .. 300 primitives with L in {2, 4, 8, 16}: the
+    scene table in shared memory at its largest, units that end inside a 16-byte unit of
+    every buffer, and scenes smaller than one sub-tile."""
+    rng = np.random.default_rng(5)
+    sizes = [(int(rng.integers(1, 301)), int(rng.choice([2, 4, 8, 16]))) for _ in range(256)]
+    scenes = _scenes(sizes, 700, bf16)
+    b = lib.Batch(scenes, sub_tiles=2)
+    assert b.plan.pair_path == 1
+    b.tuning.dynamic = 1
+    b.tuning.staged = staged
+    b.run()
+    lib.nasg_device_status()
+    _compare_with_single(lib, scenes[::17])
+
+
 def test_batched_cos_frames(lib):
     scenes = _scenes([(3000, 8), (1001, 5)], 400, True, "cos")
     b = lib.Batch(scenes, frame_mode="cos")
