@@ -259,7 +259,7 @@ __device__ __forceinline__ bool issue_unit(const BatchArgs& b, const SceneDev* s
 }
 
 template <int FRAME, typename T, int FLAGS, bool PAIRS>
-__global__ void __launch_bounds__(256, 2) batched_staged_kernel(const BatchArgs b) {
+__global__ void __launch_bounds__(kStagedThreads, 2) batched_staged_kernel(const BatchArgs b) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr int NS = batch_stages<T>();
   using W = typename RawWord<T>::type;
@@ -276,12 +276,11 @@ __global__ void __launch_bounds__(256, 2) batched_staged_kernel(const BatchArgs 
     uint32_t* dst = reinterpret_cast<uint32_t*>(sd);
     for (int j = threadIdx.x; j < words; j += blockDim.x) dst[j] = src[j];
   }
-  const uint32_t n_warps = blockDim.x >> 5;
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], n_warps);
+      mbar_init(&empty[s], kStagedWarps);
     }
     fence_barrier_init();
   }
@@ -305,7 +304,7 @@ __global__ void __launch_bounds__(256, 2) batched_staged_kernel(const BatchArgs 
   }
   bool failed = false;
   for (uint32_t it = 0;; ++it) {
-    if (it >= 1 && lane == 0 && warp == (it - 1) % n_warps) {
+    if (it >= 1 && lane == 0 && warp == (it - 1) % kStagedWarps) {
       const uint32_t pit = it - 1;
       const int ps = int(pit % NS);
       if (mbar_wait(&empty[ps], (pit / NS) & 1u, b.dev_err)) {
@@ -512,13 +511,14 @@ static nasg_status launch_batched_k(const BatchArgs& b, int blocks_per_sm, bool 
       cfg = smem;
     }
     int fit = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k, 256, smem) != cudaSuccess || fit < 1) fit = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k, kStagedThreads, smem) != cudaSuccess || fit < 1)
+      fit = 1;
     const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : fit;
     int64_t grid = int64_t(sm_count()) * per_sm;
     const int64_t units = b.total_tiles * b.sub_tiles;
     if (grid > units) grid = units;
     if (grid < 1) return NASG_OK;
-    k<<<unsigned(grid), 256, smem, s>>>(b);
+    k<<<unsigned(grid), kStagedThreads, smem, s>>>(b);
     return check_launch();
   }
   auto k = dflt ? batched_kernel<FRAME, T, kFlagsDefault, PAIRS> : batched_kernel<FRAME, T, kFlagsRuntime, PAIRS>;
