@@ -247,14 +247,20 @@ __device__ __forceinline__ float pick3(const float v[3], int c) { return c == 0 
 
 // Evaluates one fetched item: the lane's two lobes, the slice reductions and the
 // per-primitive outputs, whose three channels are spread over the slice's lanes.
-template <int FRAME, typename T, typename IDX, int MODE, bool EVEN, int FLAGS>
+// Lanes per primitive for L lobes held two per lane: next power of two >= ceil(L/2).
+constexpr int slice_of_lobes(int L) { return L <= 2 ? 1 : 2 * slice_of_lobes((L + 1) / 2); }
+constexpr int log2_of(int x) { return x <= 1 ? 0 : 1 + log2_of(x >> 1); }
+
+// LC: the lobe count when fixed at compile time (0: read from the arguments).
+template <int FRAME, typename T, typename IDX, int MODE, bool EVEN, int FLAGS, int LC = 0>
 __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, FrameTraits<FRAME>::P>& cur, IDX i,
                                           int l0) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr bool FWD = (MODE & kFwd) != 0;
   constexpr bool BWD = (MODE & kBwd) != 0;
   const IDX n = IDX(a.n);
-  const IDX L = IDX(a.n_lobes);
+  const IDX L = LC ? IDX(LC) : IDX(a.n_lobes);
+  const int S = LC ? slice_of_lobes(LC) : a.slice;
   const bool acc = Flags<FLAGS>::accumulate(a);
   const bool ok = cur.ok != 0;
   float rgb[3] = {0.f, 0.f, 0.f};
@@ -313,14 +319,14 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
       }
     }
   }
-  if (FWD && BWD && a.slice >= 4) {  // warp-uniform
+  if (FWD && BWD && S >= 4) {  // warp-uniform
     // Reduce-scatter over the slice: the colour and dLoss/dd partials (and the
     // partial d . dLoss/dd, linear in them) are summed so that lane c < 3 of each
     // group of four ends with channel c and lane 3 with the dot product: seven
     // shuffles in place of the twelve of an all-reduce of six values.
     const int lane = threadIdx.x & 31;
     float v[7] = {rgb[0], gd[0], rgb[1], gd[1], rgb[2], gd[2], gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2]};
-    for (int o = a.slice >> 1; o >= 4; o >>= 1) {
+    for (int o = S >> 1; o >= 4; o >>= 1) {
 #pragma unroll
       for (int k = 0; k < 7; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     }
@@ -344,7 +350,7 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
     return;
   }
   // xor-butterfly over the slice: every lane ends with the primitive's sums
-  for (int o = a.slice >> 1; o >= 1; o >>= 1) {
+  for (int o = S >> 1; o >= 1; o >>= 1) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       if (FWD) rgb[c] += __shfl_xor_sync(0xffffffffu, rgb[c], o);
@@ -353,7 +359,7 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
   }
   if (ok) {
     const float dot = BWD ? gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2] : 0.f;
-    for (int c = l0 >> 1; c < 3; c += a.slice) {
+    for (int c = l0 >> 1; c < 3; c += S) {
       if (FWD) a.rgb[3 * i + c] = pick3(rgb, c) + pick3(cur.c0, c);
       if (BWD) {
         store1(a.g_c0 + c * n + i, pick3(cur.gc, c), acc);
@@ -431,9 +437,9 @@ __device__ __forceinline__ void span_tail(unsigned char* dst, const void* base, 
 // tile's bulk bytes, then the bulk copies. (Issuing them from the 32 lanes of a
 // warp side by side measured slower: the whole warp then waits on the stage.)
 template <typename T, int P, bool FWD, bool BWD, bool ANYN>
-__device__ __forceinline__ void issue_tile(const EvalArgs& a, const TileGeom& g, uint32_t tile, unsigned char* st,
-                                           uint64_t* bar) {
-  const uint32_t n = uint32_t(a.n), L = uint32_t(a.n_lobes);
+__device__ __forceinline__ void issue_tile(const EvalArgs& a, const TileGeom& g, uint32_t L, uint32_t tile,
+                                           unsigned char* st, uint64_t* bar) {
+  const uint32_t n = uint32_t(a.n);
   const uint32_t p0 = tile * g.tp;
   const uint32_t bp = tile_span<T, P, ANYN>(g, n, L, tile, 0).bulk;  // every parameter plane's span
   const SpanPlan pm = tile_span<T, P, ANYN>(g, n, L, tile, P);
@@ -468,17 +474,19 @@ __device__ __forceinline__ void issue_tile(const EvalArgs& a, const TileGeom& g,
   }
 }
 
-template <int FRAME, typename T, int MODE, int FLAGS, bool ANYN>
+template <int FRAME, typename T, int MODE, int FLAGS, bool ANYN, int LC>
 __global__ void __launch_bounds__(kStagedThreads, 2) eval_tma_kernel(const EvalArgs a) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr bool FWD = (MODE & kFwd) != 0;
   constexpr bool BWD = (MODE & kBwd) != 0;
   using W = typename RawWord<T>::type;
   extern __shared__ __align__(128) unsigned char smem[];
-  const TileGeom g = tile_geom<T, P, ANYN>(a.slice_log2, a.n_lobes);
+  const int slog = LC ? log2_of(slice_of_lobes(LC)) : a.slice_log2;
+  const uint32_t L = LC ? uint32_t(LC) : uint32_t(a.n_lobes);
+  const TileGeom g = tile_geom<T, P, ANYN>(slog, int(L));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * g.stage_bytes);  // tile landed
   uint64_t* empty = full + kStages;                                             // tile read by all warps
-  const uint32_t n = uint32_t(a.n), L = uint32_t(a.n_lobes);
+  const uint32_t n = uint32_t(a.n);
   const uint32_t n_tiles = (n + g.tp - 1) / g.tp;
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -501,13 +509,13 @@ __global__ void __launch_bounds__(kStagedThreads, 2) eval_tma_kernel(const EvalA
     for (int s = 0; s < kStages; ++s) {
       const uint32_t tile = blockIdx.x + s * gridDim.x;
       if (tile < n_tiles) {
-        issue_tile<T, P, FWD, BWD, ANYN>(a, g, tile, smem + s * g.stage_bytes, &full[s]);
+        issue_tile<T, P, FWD, BWD, ANYN>(a, g, L, tile, smem + s * g.stage_bytes, &full[s]);
         pending |= 1u << s;
       }
     }
   }
-  const uint32_t local = threadIdx.x >> a.slice_log2;
-  const int l0 = 2 * (threadIdx.x & (a.slice - 1));
+  const uint32_t local = threadIdx.x >> slog;
+  const int l0 = 2 * (threadIdx.x & ((1 << slog) - 1));
   for (uint32_t it = 0;; ++it) {
     const uint32_t tile = blockIdx.x + it * gridDim.x;
     if (tile >= n_tiles) break;  // block-uniform
@@ -520,7 +528,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) eval_tma_kernel(const EvalA
       const int ps = pit % kStages;
       if (next < n_tiles && mbar_wait(&empty[ps], (pit / kStages) & 1u, a.dev_err)) {
         fence_proxy_async();
-        issue_tile<T, P, FWD, BWD, ANYN>(a, g, next, smem + ps * g.stage_bytes, &full[ps]);
+        issue_tile<T, P, FWD, BWD, ANYN>(a, g, L, next, smem + ps * g.stage_bytes, &full[ps]);
         pending |= 1u << ps;
         pend_par = (pend_par & ~(1u << ps)) | (((nit / kStages) & 1u) << ps);
       }
@@ -566,7 +574,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) eval_tma_kernel(const EvalA
     }
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
-    eval_item<FRAME, T, uint32_t, MODE, true, FLAGS>(a, r, i, l0);
+    eval_item<FRAME, T, uint32_t, MODE, true, FLAGS, LC>(a, r, i, l0);
   }
 }
 
@@ -621,12 +629,12 @@ bool tma_eligible(const EvalArgs& a, bool even) {
   return true;
 }
 
-template <int MODE, int FRAME, typename T, int FLAGS, bool ANYN>
+template <int MODE, int FRAME, typename T, int FLAGS, bool ANYN, int LC>
 nasg_status launch_tma_geom(const EvalArgs& a, cudaStream_t s) {
   constexpr int P = FrameTraits<FRAME>::P;
   const TileGeom g = tile_geom<T, P, ANYN>(a.slice_log2, a.n_lobes);
   const size_t smem = size_t(kStages) * g.stage_bytes + 2 * kStages * sizeof(uint64_t);
-  auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS, ANYN>;
+  auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS, ANYN, LC>;
   static size_t configured = 0;  // per instantiation
   if (smem > configured) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
@@ -642,11 +650,24 @@ nasg_status launch_tma_geom(const EvalArgs& a, cudaStream_t s) {
   return check_launch();
 }
 
-// N % 8 == 0: packed stages and exact spans; any other N: span plans.
+// N % 8 == 0: packed stages and exact spans; any other N: span plans. With the
+// default modes, L = 4, 8 and 16 run instances with the lobe count (and so the
+// slice width and the stage geometry) fixed at compile time.
+template <int MODE, int FRAME, typename T, int FLAGS, int LC>
+nasg_status launch_tma_lc(const EvalArgs& a, cudaStream_t s) {
+  return a.n % 8 == 0 ? launch_tma_geom<MODE, FRAME, T, FLAGS, false, LC>(a, s)
+                      : launch_tma_geom<MODE, FRAME, T, FLAGS, true, LC>(a, s);
+}
+
 template <int MODE, int FRAME, typename T, int FLAGS>
 nasg_status launch_tma(const EvalArgs& a, cudaStream_t s) {
-  return a.n % 8 == 0 ? launch_tma_geom<MODE, FRAME, T, FLAGS, false>(a, s)
-                      : launch_tma_geom<MODE, FRAME, T, FLAGS, true>(a, s);
+  if constexpr (FLAGS == kFlagsDefault) {
+    if (a.n_lobes == 8) return launch_tma_lc<MODE, FRAME, T, FLAGS, 8>(a, s);
+    if (a.n_lobes == 4) return launch_tma_lc<MODE, FRAME, T, FLAGS, 4>(a, s);
+    if (a.n_lobes == 16) return launch_tma_lc<MODE, FRAME, T, FLAGS, 16>(a, s);
+  }
+  return a.n % 8 == 0 ? launch_tma_geom<MODE, FRAME, T, FLAGS, false, 0>(a, s)
+                      : launch_tma_geom<MODE, FRAME, T, FLAGS, true, 0>(a, s);
 }
 
 template <int MODE, int FRAME, typename T>
