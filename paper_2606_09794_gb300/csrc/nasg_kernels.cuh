@@ -260,7 +260,8 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
   constexpr bool BWD = (MODE & kBwd) != 0;
   const IDX n = IDX(a.n);
   const IDX L = LC ? IDX(LC) : IDX(a.n_lobes);
-  const int S = LC ? slice_of_lobes(LC) : a.slice;
+  // the slice width, read where it is used (a cached copy cost the batched kernels registers)
+  auto S = [&]() -> int { return LC ? slice_of_lobes(LC) : a.slice; };
   const bool acc = Flags<FLAGS>::accumulate(a);
   const bool ok = cur.ok != 0;
   float rgb[3] = {0.f, 0.f, 0.f};
@@ -319,14 +320,14 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
       }
     }
   }
-  if (FWD && BWD && S >= 4) {  // warp-uniform
+  if (FWD && BWD && S() >= 4) {  // warp-uniform
     // Reduce-scatter over the slice: the colour and dLoss/dd partials (and the
     // partial d . dLoss/dd, linear in them) are summed so that lane c < 3 of each
     // group of four ends with channel c and lane 3 with the dot product: seven
     // shuffles in place of the twelve of an all-reduce of six values.
     const int lane = threadIdx.x & 31;
     float v[7] = {rgb[0], gd[0], rgb[1], gd[1], rgb[2], gd[2], gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2]};
-    for (int o = S >> 1; o >= 4; o >>= 1) {
+    for (int o = S() >> 1; o >= 4; o >>= 1) {
 #pragma unroll
       for (int k = 0; k < 7; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     }
@@ -350,7 +351,7 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
     return;
   }
   // xor-butterfly over the slice: every lane ends with the primitive's sums
-  for (int o = S >> 1; o >= 1; o >>= 1) {
+  for (int o = S() >> 1; o >= 1; o >>= 1) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       if (FWD) rgb[c] += __shfl_xor_sync(0xffffffffu, rgb[c], o);
@@ -359,7 +360,7 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
   }
   if (ok) {
     const float dot = BWD ? gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2] : 0.f;
-    for (int c = l0 >> 1; c < 3; c += S) {
+    for (int c = l0 >> 1; c < 3; c += S()) {
       if (FWD) a.rgb[3 * i + c] = pick3(rgb, c) + pick3(cur.c0, c);
       if (BWD) {
         store1(a.g_c0 + c * n + i, pick3(cur.gc, c), acc);
@@ -652,7 +653,8 @@ nasg_status launch_tma_geom(const EvalArgs& a, cudaStream_t s) {
 
 // N % 8 == 0: packed stages and exact spans; any other N: span plans. With the
 // default modes, L = 4, 8 and 16 run instances with the lobe count (and so the
-// slice width and the stage geometry) fixed at compile time.
+// slice width and the stage geometry) fixed at compile time (BF16 parameters,
+// and the FP32 forward).
 template <int MODE, int FRAME, typename T, int FLAGS, int LC>
 nasg_status launch_tma_lc(const EvalArgs& a, cudaStream_t s) {
   return a.n % 8 == 0 ? launch_tma_geom<MODE, FRAME, T, FLAGS, false, LC>(a, s)
@@ -661,7 +663,8 @@ nasg_status launch_tma_lc(const EvalArgs& a, cudaStream_t s) {
 
 template <int MODE, int FRAME, typename T, int FLAGS>
 nasg_status launch_tma(const EvalArgs& a, cudaStream_t s) {
-  if constexpr (FLAGS == kFlagsDefault) {
+  // (FP32 parameters with a backward: the fixed-L instances measured slower, so not used)
+  if constexpr (FLAGS == kFlagsDefault && (sizeof(T) == 2 || MODE == kFwd)) {
     if (a.n_lobes == 8) return launch_tma_lc<MODE, FRAME, T, FLAGS, 8>(a, s);
     if (a.n_lobes == 4) return launch_tma_lc<MODE, FRAME, T, FLAGS, 4>(a, s);
     if (a.n_lobes == 16) return launch_tma_lc<MODE, FRAME, T, FLAGS, 16>(a, s);
