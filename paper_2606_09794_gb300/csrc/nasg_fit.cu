@@ -71,35 +71,39 @@ __device__ __forceinline__ void load_pair(const float* planes, int64_t n, int L,
 }
 
 // EXACT: exact normalisation, a compile-time choice so that the approximate
-// (default) mode carries none of its code.
-template <bool EXACT>
+// (default) mode carries none of its code. LSC, LTC: the student and teacher lobe
+// counts when fixed at compile time (0: read from the arguments), which makes the
+// slice width, the teacher grouping and their loops constants.
+template <bool EXACT, int LSC, int LTC>
 __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
   __shared__ float block_sum[kFitBlock / 32];
-  const int S = 1 << s.slice_log2;
+  const int ls = LSC ? LSC : s.ls, lt = LTC ? LTC : s.lt;
+  const int slog = LSC ? log2_of(slice_of_lobes(LSC)) : s.slice_log2;
+  const int S = 1 << slog;
   const int g = threadIdx.x & (S - 1);
   const int l0 = 2 * g;
-  const int tpairs = s.lt >> 1;  // teacher pairs
+  const int tpairs = lt >> 1;    // teacher pairs
   const int G = S / tpairs;      // directions per teacher group
   const int tp = g % tpairs, tk = g / tpairs;
   const int lane = threadIdx.x & 31;
   const int slice0 = lane & ~(S - 1);
-  const int64_t total = s.n << s.slice_log2;
+  const int64_t total = s.n << slog;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   const float inv3d = 2.f / (3.f * float(s.n_dirs));
   float sq_sum = 0.f;
   for (int64_t t0 = int64_t(blockIdx.x) * blockDim.x; t0 < total; t0 += stride) {  // block-uniform
     const int64_t t = t0 + threadIdx.x;
     const bool ok = t < total;
-    const int64_t i = ok ? (t >> s.slice_log2) : 0;
-    const bool mine = ok && l0 < s.ls;
+    const int64_t i = ok ? (t >> slog) : 0;
+    const bool mine = ok && l0 < ls;
     // ---- per-step constants of the lane's student and teacher pairs ----
     P2 sp[10], tpar[10];
-    if (mine) load_pair(s.master, s.n, s.ls, i, l0, s.quantize != 0, sp);
+    if (mine) load_pair(s.master, s.n, ls, i, l0, s.quantize != 0, sp);
     else {
 #pragma unroll
       for (int p = 0; p < 10; ++p) sp[p] = p2(p == 0 ? 1.f : 0.f);
     }
-    if (ok) load_pair(s.teacher, s.n, s.lt, i, 2 * tp, false, tpar);
+    if (ok) load_pair(s.teacher, s.n, lt, i, 2 * tp, false, tpar);
     else {
 #pragma unroll
       for (int p = 0; p < 10; ++p) tpar[p] = p2(p == 0 ? 1.f : 0.f);
@@ -189,8 +193,8 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
       grad[6] = acc_k * act.s_k;
 #pragma unroll
       for (int c = 0; c < 3; ++c) grad[7 + c] = acc_w[c] * act.s_w[c];
-      const int64_t NL = s.n * s.ls;
-      const int64_t off = i * s.ls + l0;
+      const int64_t NL = s.n * ls;
+      const int64_t off = i * ls + l0;
 #pragma unroll
       for (int p = 0; p < 10; ++p) {
         float2 th = *reinterpret_cast<const float2*>(s.master + p * NL + off);
@@ -320,7 +324,9 @@ extern "C" nasg_status nasgabor_fit_step(const nasg_desc* desc, const nasg_train
   a.normalised = desc->norm_mode != NASG_NORM_NONE;
   a.exact = desc->norm_mode == NASG_NORM_EXACT;
   a.partials = static_cast<float*>(workspace);
-  auto k = a.exact ? fit_kernel<true> : fit_kernel<false>;
+  // the fitting workload's shape (16 student, 4 teacher lobes) runs a fixed-count instance
+  auto k = a.exact ? fit_kernel<true, 0, 0>
+                   : (ls == 16 && teacher_lobes == 4 ? fit_kernel<false, 16, 4> : fit_kernel<false, 0, 0>);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kFitBlock, 0) != cudaSuccess || per_sm < 1)
     per_sm = 1;
