@@ -27,9 +27,14 @@ Readings where the paper is silent, ambiguous or mistaken (each one is also
 listed with its reason in the design notes):
   R1  normalised kernel: G = C^-1 p E h (Supp. F); norm_mode "none" drops C^-1
       (the Sec. 5.1 display). At d = z the normalised value is the limit C^-1.
-  R2  poles: where 1 - u^2 == 0 (u = d.z) in working precision, u > 0 takes
-      tau := 0 (and zero derivatives of tau), giving G = C^-1 h(v); u < 0 gives
-      G := 0 with all derivatives 0.
+  R2  poles: where 1 - u^2 == 0 (u = d.z), u > 0 takes tau := 0 (and zero
+      derivatives of tau), giving G = C^-1 h(v); u < 0 gives G := 0 with all
+      derivatives 0. 1 - u^2 is evaluated as |d x z|^2 (equal for unit d, z), and
+      1 - u, 1 + u from it where each is small, so that the rule applies at the
+      exact poles only and directions a little off them keep full accuracy
+      (1 - u u in FP64 rounds to 0 within ~1.5e-8 rad of the axis and loses ~1 %
+      at 1e-7 rad); likewise ln kappa by log1p near kappa = 1 and E kappa - 1 by
+      expm1.
   R3  Supp. E writes ln(tau) in dp/da; the factor is ln(kappa) (as in Supp. F).
   R4  dC^-1/dlam printed with "+ 2 lam sqrt(1+a) e^{-2 lam}" in the numerator;
       differentiating C^-1 gives "-". The minus sign is used (pinned by finite
@@ -123,6 +128,9 @@ def activate(planes, frame_mode, act_mode=ACT_RAW, variant=VAR_NASGABOR):
         frame_raw = np.moveaxis(planes[0:3], 0, -1)
         out["c_raw"] = frame_raw
         out["c"] = frame_raw if act_mode == ACT_IDENTITY else np.tanh(frame_raw)
+        # the sines s = sqrt(1 - c^2) >= 0; for c = tanh r that is sech r = 1/cosh r, which
+        # keeps its relative accuracy where tanh r is within rounding of +-1
+        out["s"] = np.sqrt(1.0 - out["c"] ** 2) if act_mode == ACT_IDENTITY else 1.0 / np.cosh(frame_raw)
         rest = planes[3:]
     f = {name: rest[j] for j, name in enumerate(_FIELDS[variant])}
     lam_r = f["lam"]
@@ -193,23 +201,28 @@ def _quat_frame_jacobians(q):
     return dx @ proj, dz @ proj
 
 
-def frame_from_cos(c):
-    """Supp. C: z = (ct sp, st sp, cp), x = (ct cp cs - st ss, st cp cs + ct ss, -sp cs); s = sqrt(1 - c^2)."""
+def frame_from_cos(c, s=None):
+    """Supp. C: z = (ct sp, st sp, cp), x = (ct cp cs - st ss, st cp cs + ct ss, -sp cs);
+    s = sqrt(1 - c^2) unless the sines are given."""
     ct, cp, cs = c[..., 0], c[..., 1], c[..., 2]
-    st, sp, ss = (np.sqrt(1.0 - ct * ct), np.sqrt(1.0 - cp * cp), np.sqrt(1.0 - cs * cs))
+    if s is None:
+        s = np.sqrt(1.0 - c * c)
+    st, sp, ss = s[..., 0], s[..., 1], s[..., 2]
     za = np.stack([ct * sp, st * sp, cp], axis=-1)
     xa = np.stack([ct * cp * cs - st * ss, st * cp * cs + ct * ss, -sp * cs], axis=-1)
     return xa, za
 
 
-def _cos_frame_partials(c):
+def _cos_frame_partials(c, s=None):
     """Partials of x and z wrt the six quantities (ct, st, cp, sp, cs, ss), each a 3-vector.
 
     The Supp. E formulas for dx/dc, dz/dc are these partials combined with
     ds/dc = -c/s; they are combined here with the chosen chain (raw or identity).
     """
     ct, cp, cs = c[..., 0], c[..., 1], c[..., 2]
-    st, sp, ss = (np.sqrt(1.0 - ct * ct), np.sqrt(1.0 - cp * cp), np.sqrt(1.0 - cs * cs))
+    if s is None:
+        s = np.sqrt(1.0 - c * c)
+    st, sp, ss = s[..., 0], s[..., 1], s[..., 2]
     zero = np.zeros_like(ct)
     vx = lambda a, b, d: np.stack([a, b, d], axis=-1)  # noqa: E731
     px = {
@@ -285,15 +298,24 @@ def lobe(d, x, z, lam, a, k, norm_mode=NORM_APPROX, need_grad=False, phi=None):
         phi = np.zeros_like(np.asarray(lam, dtype=np.float64))
     u = np.sum(d * z, axis=-1)
     v = np.sum(d * x, axis=-1)
-    one_m_u2 = 1.0 - u * u
-    pole = (one_m_u2 <= 0.0) | (u >= 1.0) | (u <= -1.0)
+    # 1 - u^2 = |d x z|^2 for unit d, z (the same number, without the cancellation of
+    # 1 - u u near the poles); 1 - u and 1 + u from it on the side where each is small
+    dz = np.cross(d, z)
+    one_m_u2 = np.sum(dz * dz, axis=-1)
+    pole = one_m_u2 <= 0.0
     safe = np.where(pole, 1.0, one_m_u2)
-    kappa = (u + 1.0) / 2.0
+    up = u >= 0.0
+    one_m_u = np.where(up, safe / np.where(up, 1.0 + u, 1.0), 1.0 - u)
+    one_p_u = np.where(up, 1.0 + u, safe / np.where(up, 1.0, 1.0 - u))
+    kappa = one_p_u / 2.0
     kappa_safe = np.where(pole, 1.0, kappa)
     tau = np.where(pole, 0.0, a * v * v / safe)
-    ln_kappa = np.log(kappa_safe)
-    E = kappa_safe ** tau
-    p = np.exp(2.0 * lam * (E * kappa_safe - 1.0))
+    # ln kappa = log1p(-(1 - u)/2) where kappa is near 1; E kappa - 1 = expm1((1 + tau) ln kappa)
+    ln_kappa = np.where(pole, 0.0, np.where(up, np.log1p(-np.minimum(one_m_u, 1.0) / 2.0),
+                                            np.log(np.where(kappa_safe > 0.0, kappa_safe, 1.0))))
+    E = np.exp(tau * ln_kappa)
+    ek_m1 = np.expm1((1.0 + tau) * ln_kappa)
+    p = np.exp(2.0 * lam * ek_m1)
     h = (1.0 + np.cos(k * v + phi)) / 2.0
     if norm_mode == NORM_NONE:
         cinv = np.ones_like(lam)
@@ -330,7 +352,7 @@ def lobe(d, x, z, lam, a, k, norm_mode=NORM_APPROX, need_grad=False, phi=None):
         dcinv_dlam, dcinv_da, dcinv_dk, dcinv_dphi = _exact_norm_partials(lam, a, k, phi)
     dG_da = (dp_da * E * cinv + p * dE_da * cinv + p * E * dcinv_da) * h
     # wrt lam
-    dp_dlam = 2.0 * p * (E * kappa_safe - 1.0)
+    dp_dlam = 2.0 * p * ek_m1
     dG_dlam = (E * cinv * dp_dlam + E * p * dcinv_dlam) * h
     # wrt x: dtau/dx = 2 a v/(1-u^2) d ; dE/dx = E ln(kappa) dtau/dx ; dp/dx = 2 lam p kappa dE/dx
     coef_tau_x = np.where(pole, 0.0, 2.0 * a * v / safe)
@@ -393,7 +415,7 @@ def _integral_closed_form_complex(lam, a, k, phi):
 def _frames(act, frame_mode):
     if frame_mode == FRAME_QUAT:
         return frame_from_quat(act["q"])
-    return frame_from_cos(act["c"])
+    return frame_from_cos(act["c"], act.get("s"))
 
 
 def forward(params, c0, means, cam, n_lobes, frame_mode=FRAME_QUAT, norm_mode=NORM_APPROX,
@@ -443,14 +465,13 @@ def backward(params, c0, means, cam, g_rgb, n_lobes, frame_mode=FRAME_QUAT,
         g_q = np.einsum("nli,nlij->nlj", g_x, jx) + np.einsum("nli,nlij->nlj", g_z, jz)
         frame_planes = [g_q[..., j] for j in range(4)]
     else:
-        px, pz, (ct, st, cp, sp, cs, ss) = _cos_frame_partials(act["c"])
+        px, pz, (ct, st, cp, sp, cs, ss) = _cos_frame_partials(act["c"], act.get("s"))
         if act_mode == ACT_IDENTITY:
             # d/dc with ds/dc = -c/s (Supp. E)
             dc = {"t": (1.0, -ct / st), "p": (1.0, -cp / sp), "s": (1.0, -cs / ss)}
         else:
-            # raw r with c = tanh r: dc/dr = 1 - c^2 and s = sech r, ds/dr = -c s
-            dc = {"t": (1.0 - ct * ct, -ct * st), "p": (1.0 - cp * cp, -cp * sp),
-                  "s": (1.0 - cs * cs, -cs * ss)}
+            # raw r with c = tanh r: dc/dr = 1 - c^2 = s^2 and s = sech r, ds/dr = -c s
+            dc = {"t": (st * st, -ct * st), "p": (sp * sp, -cp * sp), "s": (ss * ss, -cs * ss)}
         frame_planes = []
         for ang, (cn, sn) in (("t", ("ct", "st")), ("p", ("cp", "sp")), ("s", ("cs", "ss"))):
             dcdr, dsdr = dc[ang]

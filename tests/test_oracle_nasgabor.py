@@ -496,3 +496,58 @@ def test_phase_carrier_exact_normalisation_has_unit_mass(lam, k, phi):
     val = integrate_lobe(lambda *args, **kw: ng.lobe(*args, **kw, phi=np.full(np.shape(args[3]), phi)),
                          lam, 0.0, k, ng.NORM_EXACT)
     assert abs(val - 1.0) < 1e-9
+
+
+def _lobe_mp(u, v, lam, a, k, s2):
+    """The Sec. 5.1 / Supp. F lobe written out in mpmath from its definition
+    (kappa = (1+u)/2, tau = a v^2/(1-u^2), E = kappa^tau, p = e^{2 lam (E kappa - 1)},
+    h = (1 + cos(k v))/2, approximate C^-1), with 1 - u^2 = s2 supplied."""
+    import mpmath as mp
+    kappa = (1 + u) / 2
+    tau = a * v * v / s2
+    E = kappa ** tau
+    p = mp.exp(2 * lam * (E * kappa - 1))
+    h = (1 + mp.cos(k * v)) / 2
+    cinv = lam * mp.sqrt(1 + a) / (2 * mp.pi * (1 - mp.exp(-2 * lam)))
+    return cinv * p * E * h
+
+
+@pytest.mark.parametrize("theta", [1e-2, 1e-5, 1e-7, 1e-9, 1e-12])
+@pytest.mark.parametrize("side", [1.0, -1.0])
+def test_lobe_near_poles_matches_50_digit_definition(theta, side):
+    """Directions theta from +z (side +1) and -z (side -1), down to 1e-12 rad: the FP64
+    lobe value and its partials (u, v, lam, a, k) against the definition evaluated in
+    50-digit arithmetic at the normalised direction, partials by mpmath.diff. The
+    FP64 forms 1 - u u and (1 + u)/2 would lose ~1 % at 1e-7 rad and all digits below
+    ~1e-8 rad."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    for lam, a, k, psi in ((1.0, 0.5, 3.0, 0.3), (30.0, 0.8, 7.0, 1.1), (1000.0, 0.3, 2.0, 0.0)):
+        d = np.array([math.sin(theta) * math.cos(psi), math.sin(theta) * math.sin(psi), side * math.cos(theta)])
+        x = np.array([1.0, 0.0, 0.0])
+        z = np.array([0.0, 0.0, 1.0])
+        G, par = ng.lobe(d[None], x[None], z[None], np.array([lam]), np.array([a]), np.array([k]), need_grad=True)
+        dm = [mp.mpf(float(c)) for c in d]
+        nrm = mp.sqrt(sum(c * c for c in dm))
+        dm = [c / nrm for c in dm]
+        u0, v0 = dm[2], dm[0]
+        s2 = dm[0] ** 2 + dm[1] ** 2
+
+        def f(u, v, lm, aa, kk, s2_=None):
+            return _lobe_mp(u, v, lm, aa, kk, (1 - u) * (1 + u) if s2_ is None else s2_)
+
+        L_, A_, K_ = mp.mpf(lam), mp.mpf(a), mp.mpf(k)
+        ref = f(u0, v0, L_, A_, K_, s2)
+        dnorm = float(np.dot(d, d))
+        got = {"G": float(G[0]), "u": float(np.dot(par["z"][0], d)) / dnorm, "v": float(np.dot(par["x"][0], d)) / dnorm,
+               "lam": float(par["lam"][0]), "a": float(par["a"][0]), "k": float(par["k"][0])}
+        # derivative in u at fixed v: 1 - u^2 varies with u; at the base point it equals s2
+        want = {"G": ref,
+                "u": mp.diff(lambda t: f(t, v0, L_, A_, K_), u0),
+                "v": mp.diff(lambda t: f(u0, t, L_, A_, K_, s2), v0),
+                "lam": mp.diff(lambda t: f(u0, v0, t, A_, K_, s2), L_),
+                "a": mp.diff(lambda t: f(u0, v0, L_, t, K_, s2), A_),
+                "k": mp.diff(lambda t: f(u0, v0, L_, A_, t, s2), K_)}
+        for key, w in want.items():
+            w = float(w)
+            assert abs(got[key] - w) <= 1e-9 * abs(w) + 1e-300, (theta, side, lam, key, got[key], w)
