@@ -544,6 +544,18 @@ def measure_paths(nb, inputs, w, params_bf16, dev, stream, peak, reps=200):
         "sh3_bwd_f32": (lambda: nb.sh_eval_bwd(coeffs, means, cam, g, 3, g_coeffs=gco, g_means=gm,
                                                stream=stream), N * BYTES_SH3_BWD),
     }
+    # config 2 through the torch.autograd.Function (what a PyTorch user calls): forward,
+    # then .backward of the colours with the upstream gradient; gradients set to None
+    # before each pass, as optimizer.zero_grad() does
+    p_ag = p32.clone().requires_grad_(True)
+    c_ag = c32.clone().requires_grad_(True)
+    m_ag = means.clone().requires_grad_(True)
+
+    def autograd_pass():
+        p_ag.grad = c_ag.grad = m_ag.grad = None
+        nb.NasgEval.apply(p_ag, c_ag, m_ag, cam, L).backward(g)
+
+    kernels["nasgabor_autograd_f32"] = (autograd_pass, N * (bytes_fwd_f32(L) + bytes_bwd_f32(L)))
     res = {}
     for name, (fn, nbytes) in kernels.items():
         for _ in range(5):
@@ -568,6 +580,10 @@ def measure_paths(nb, inputs, w, params_bf16, dev, stream, peak, reps=200):
         "fused_bf16": {"value": N * L / (res["nasgabor_fused_bf16"]["us"] * 1e-6), "unit": UNIT},
         "sh3_fwd_then_bwd": {"value": N / (t_sh * 1e-6), "unit": "primitives/s",
                              "value_basis_lobes": 16 * N / (t_sh * 1e-6), "us": t_sh},
+        "autograd_f32": {"value": N * L / (res["nasgabor_autograd_f32"]["us"] * 1e-6), "unit": UNIT,
+                         "us": res["nasgabor_autograd_f32"]["us"],
+                         "note": "NasgEval.apply(...).backward(g): forward and backward kernels through the "
+                                 "torch.autograd.Function, outputs allocated per pass"},
     }
 
 
@@ -583,7 +599,13 @@ def measure_scene_step(nb, inputs, dev, stream, peak, n=6_000_000, L=8, seed=100
     """Scene-scale training step: noisy-shell scene (primitives stored in Morton order of
     their centres), 8 cameras on a ring, per camera the ordered frustum compaction then one
     fused forward+backward+Adam step (BF16 copies of an FP32 master) on the visible
-    primitives, all on one stream with no host sync."""
+    primitives, all on one stream with no host sync. Beside it, per camera: the same step
+    with the upstream gradient formed in the kernel from target colours (MSE loss mode),
+    and the unfused path a PyTorch user would write with this library's kernels: the
+    backward of the visible primitives (nasgabor_eval_bwd with the index list) into a
+    zeroed gradient buffer, torch.optim.Adam(foreach=True) over the parameters, and the
+    BF16 copies (note: the dense Adam also advances the moments of primitives that are
+    not visible, which the fused step leaves untouched)."""
     import torch
     sc = inputs.shell_scene(n, L, seed, order=order)
     st = nb.TrainState(torch.from_numpy(sc.params).to(dev), torch.from_numpy(sc.c0).to(dev))
@@ -591,39 +613,90 @@ def measure_scene_step(nb, inputs, dev, stream, peak, n=6_000_000, L=8, seed=100
     del sc.params
     gs = [torch.from_numpy(inputs.ring_upstream(n, j, seed)).to(dev) for j in range(len(sc.cameras))]
     ws = torch.empty(nb.nasg_frustum_workspace_bytes(n), device=dev, dtype=torch.uint8)
-    idx = torch.empty(n, device=dev, dtype=torch.int32)
+    idx = [torch.empty(n, device=dev, dtype=torch.int32) for _ in sc.cameras]
     nvis = [torch.empty(1, device=dev, dtype=torch.int32) for _ in sc.cameras]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * len(sc.cameras) + 1)]
+    nc = len(sc.cameras)
 
-    def ring(t0, record):
+    def ring(t0, record, loss="given", upstream=gs):
         for j, cam in enumerate(sc.cameras):
             if record:
                 ev[3 * j].record(stream)
-            nb.nasg_frustum_compact(means, cam.rot, cam.center, cam.tan_half_fov, idx=idx, n_visible=nvis[j],
+            nb.nasg_frustum_compact(means, cam.rot, cam.center, cam.tan_half_fov, idx=idx[j], n_visible=nvis[j],
                                     workspace=ws, stream=stream)
             if record:
                 ev[3 * j + 1].record(stream)
-            nb.nasgabor_fused_step(st, means, cam.center, gs[j], L, t0 + j + 1, idx=idx, n_idx_device=nvis[j],
-                                   stream=stream)
+            nb.nasgabor_fused_step(st, means, cam.center, upstream[j], L, t0 + j + 1, idx=idx[j],
+                                   n_idx_device=nvis[j], stream=stream, loss=loss)
             if record:
                 ev[3 * j + 2].record(stream)
 
     ring(0, False)
     torch.cuda.synchronize(dev)
-    ring(len(sc.cameras), True)
+    ring(nc, True)
     torch.cuda.synchronize(dev)
     vis = [int(v.item()) for v in nvis]
-    step_us = [ev[3 * j + 1].elapsed_time(ev[3 * j + 2]) * 1e3 for j in range(len(sc.cameras))]
-    comp_us = [ev[3 * j].elapsed_time(ev[3 * j + 1]) * 1e3 for j in range(len(sc.cameras))]
-    total_us = ev[0].elapsed_time(ev[3 * len(sc.cameras) - 1]) * 1e3
+    step_us = [ev[3 * j + 1].elapsed_time(ev[3 * j + 2]) * 1e3 for j in range(nc)]
+    comp_us = [ev[3 * j].elapsed_time(ev[3 * j + 1]) * 1e3 for j in range(nc)]
+    total_us = ev[0].elapsed_time(ev[3 * nc - 1]) * 1e3
     step_bytes = sum(v * bytes_step(L) for v in vis)
     gbs = step_bytes / (sum(step_us) * 1e-6) / 1e9
+
+    # target-driven step (MSE loss mode): targets U[0, 1]^3 per camera
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    targets = [torch.rand((n, 3), device=dev, generator=gen) for _ in range(nc)]
+    ring(2 * nc, False, "mse", targets)
+    torch.cuda.synchronize(dev)
+    ring(3 * nc, True, "mse", targets)
+    torch.cuda.synchronize(dev)
+    mse_us = [ev[3 * j + 1].elapsed_time(ev[3 * j + 2]) * 1e3 for j in range(nc)]
+    del targets
+
+    # unfused: backward of the visible primitives + torch.optim.Adam(foreach) + BF16 copies
+    master = torch.nn.Parameter(st.master.clone())
+    c0m = torch.nn.Parameter(st.c0_master.clone())
+    pbf, cbf = st.params_bf16, st.c0_bf16
+    del st
+    master.grad = torch.zeros_like(master)
+    c0m.grad = torch.zeros_like(c0m)
+    opt = torch.optim.Adam([master, c0m], lr=1e-3, foreach=True)
+    uev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * nc)]
+
+    def ring_unfused(record):
+        for j in range(nc):
+            if record:
+                uev[2 * j].record(stream)
+            master.grad.zero_()
+            c0m.grad.zero_()
+            nb.nasgabor_eval_bwd(pbf, means, sc.cameras[j].center, gs[j], L, idx=idx[j][:vis[j]],
+                                 g_params=master.grad, g_c0=c0m.grad, want_means=False, stream=stream)
+            opt.step()
+            with torch.no_grad():
+                pbf.copy_(master)
+                cbf.copy_(c0m)
+            if record:
+                uev[2 * j + 1].record(stream)
+
+    with torch.cuda.stream(stream):
+        ring_unfused(False)
+        torch.cuda.synchronize(dev)
+        ring_unfused(True)
+        torch.cuda.synchronize(dev)
+    unfused_us = [uev[2 * j].elapsed_time(uev[2 * j + 1]) * 1e3 for j in range(nc)]
+    del opt, master, c0m
+    torch.cuda.empty_cache()
     return {"workload": f"noisy shell N={n} ({order} storage order), L={L}, 8 ring cameras, ~45% visible each, "
                         "BF16 copies of FP32 master",
             "visible_per_camera": vis, "step_us_per_camera": step_us, "compaction_us_per_camera": comp_us,
             "total_us_8_cameras": total_us,
             "value": sum(vis) * L / (total_us * 1e-6), "unit": "visible primitive-lobes/s (incl. compaction)",
-            "step_alg_bytes_per_visible_primitive": bytes_step(L), "step_gbs": gbs, "step_frac": gbs / peak}
+            "step_alg_bytes_per_visible_primitive": bytes_step(L), "step_gbs": gbs, "step_frac": gbs / peak,
+            "mse_loss_step_us_per_camera": mse_us,
+            "unfused_us_per_camera": unfused_us,
+            "unfused_note": "nasgabor_eval_bwd (visible list) into zeroed f32 gradients + torch.optim.Adam(foreach=True) "
+                            "over all parameters + BF16 copies, per camera (compaction excluded)",
+            "fused_speedup_vs_unfused": sum(unfused_us) / sum(step_us)}
 
 
 def measure_batched(nb, inputs, dev, stream, peak, n_scenes=32, seed=1004, reps=20):
@@ -662,10 +735,18 @@ def measure_batched(nb, inputs, dev, stream, peak, n_scenes=32, seed=1004, reps=
             "frac": gbs / peak}
 
 
+def fit_lr(nb, inputs, step, steps):
+    """The fitting workload's rate at a (1-based) step: base 1e-3 times the library's cosine
+    schedule factor at iteration step - 1 (Supp. C), started at iteration 47 of 200."""
+    start = round(inputs.FIT_SCHEDULE_START * steps / inputs.FIT_STEPS)
+    return inputs.FIT_LR * nb.nasg_cosine_lr_factor(step - 1, steps, start)
+
+
 def measure_fit(nb, inputs, dev, stream, n=2_000_000, ls=16, lt=4, steps=200, n_dirs=64, seed=1005):
-    """Fitting loop: a 16-lobe BF16 student (FP32 master, Adam lr 1e-3) fitted to a 4-lobe
-    FP32 teacher field on the same primitives, 64 random view directions per step shared by
-    all primitives, 200 steps of the fused fitting kernel (compute-bound)."""
+    """Fitting loop: a 16-lobe BF16 student (FP32 master, Adam at base rate 1e-3 with the
+    cosine schedule) fitted to a 4-lobe FP32 teacher field on the same primitives, 64 random
+    view directions per step shared by all primitives, 200 steps of the fused fitting kernel
+    (compute-bound)."""
     import torch
     t = inputs.device_point_cloud(n, lt, seed, dev)
     s = inputs.device_point_cloud(n, ls, seed + 1, dev)
@@ -675,10 +756,11 @@ def measure_fit(nb, inputs, dev, stream, n=2_000_000, ls=16, lt=4, steps=200, n_
     losses = torch.empty(steps, device=dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    lrs = [fit_lr(nb, inputs, k + 1, steps) for k in range(steps)]
     e0.record(stream)
     for k in range(steps):
-        nb.nasgabor_fit_step(st, t["params"], t["c0"], lt, dirs[k], ls, k + 1, loss=losses[k:k + 1], workspace=ws,
-                             stream=stream)
+        nb.nasgabor_fit_step(st, t["params"], t["c0"], lt, dirs[k], ls, k + 1, lr=lrs[k], loss=losses[k:k + 1],
+                             workspace=ws, stream=stream)
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1)
@@ -686,7 +768,9 @@ def measure_fit(nb, inputs, dev, stream, n=2_000_000, ls=16, lt=4, steps=200, n_
     evals = n * n_dirs * (ls + lt) * steps
     sub = fit_subsample_check(nb, inputs, dev, stream) if n == 2_000_000 and steps == 200 else None
     return {"workload": f"fit N={n}, student L={ls} BF16 (FP32 master), teacher L={lt} FP32, {n_dirs} directions/step, "
-                        f"{steps} Adam steps lr 1e-3", "ms_total": ms, "ms_per_step": ms / steps,
+                        f"{steps} Adam steps, base lr 1e-3 with the cosine schedule from iteration "
+                        f"{round(inputs.FIT_SCHEDULE_START * steps / inputs.FIT_STEPS)}",
+            "ms_total": ms, "ms_per_step": ms / steps,
             "loss_first": float(l[0]), "loss_last": float(l[-1]),
             "lobe_evaluations_per_s": evals / (ms * 1e-3), "subsample_final_mse": sub,
             "note": "compute-bound; subsample_final_mse: the same fit on the workload's seeded 20k subsample "
@@ -713,7 +797,8 @@ def fit_subsample_check(nb, inputs, dev, stream):
     for k in range(1, steps + 2):
         nb.nasgabor_fit_step(st, tpd, tcd, wl["teacher_lobes"],
                              torch.from_numpy(inputs.fit_directions(k, wl["seed_teacher"])).to(dev),
-                             wl["student_lobes"], k, loss=losses[k - 1:k], stream=stream)
+                             wl["student_lobes"], k, lr=fit_lr(nb, inputs, k, steps), loss=losses[k - 1:k],
+                             stream=stream)
     gpu = float(losses[steps].item())
     ref = gold["bf16_storage"]["final_mse"]
     return {"gpu": gpu, "oracle": ref, "rel_diff": abs(gpu - ref) / ref, "oracle_fp64_storage": gold["fp64"]["final_mse"],

@@ -24,6 +24,11 @@
  *     rejected call launches nothing and returns a negative status.
  *   - n == 0 (or n_idx == 0) is valid and launches nothing.
  *   - No C++ exception crosses this boundary.
+ *   - The library looks up the device addresses of its own device variables (an
+ *     error word, the fixed scratch of nasg_frustum_compact_noalloc) once per
+ *     device and keeps them for the life of the process: after cudaDeviceReset, or
+ *     any release of a device's primary context, those addresses are stale, so do
+ *     not call into the library on that device again in the same process.
  *
  * Parameter layout ("planes"): a lobe has P raw scalars, P = 10 in QUAT frame
  * mode (q_w q_x q_y q_z lam_r a_r k_r w_r w_g w_b) and P = 9 in COS frame mode
@@ -126,7 +131,7 @@ int32_t nasg_last_cuda_error(void);
 nasg_status nasg_device_status(void* stream);
 
 /* ABI version of this header (bumped on any incompatible change). */
-#define NASG_ABI_VERSION 3
+#define NASG_ABI_VERSION 4
 int32_t nasg_abi_version(void);
 
 /*
@@ -195,25 +200,48 @@ typedef struct nasg_train_state {
   void* c0_bf16;        /* [3][N] bf16 copy, nullable                              */
 } nasg_train_state;
 
+/* Upstream gradient of nasgabor_fused_step. */
+#define NASG_LOSS_GIVEN 0   /* g_rgb_or_target is dLoss/dRGB [N][3]                            */
+#define NASG_LOSS_MSE   1   /* g_rgb_or_target is a target colour t [N][3]; the loss is the mean
+                               over the listed primitives i and channels c of (c_ic - t_ic)^2, so
+                               dLoss/dc_ic = 2 (c_ic - t_ic) / (3 n_listed), formed in the kernel */
+
 /*
  * Fused training step for the listed primitives: forward (eq:app_model), the
- * Supp. F backward for the given upstream gradient g_rgb [N][3] f32, and one
- * Adam update of master, m, v (lobe parameters and c0) in one pass, the
- * gradients never being written to memory. With desc->param_dtype = BF16 the
- * model is evaluated at RNE_bf16(master) (the stored BF16 copy); with F32 at
- * master. Primitives not listed are left untouched (their m, v do not advance).
- *   idx/n_idx     device list of primitives (NULL: all N). Entries outside [0, N) are skipped.
+ * Supp. F backward for the upstream gradient, and one Adam update of master, m,
+ * v (lobe parameters and c0) in one pass, the gradients never being written to
+ * memory. The upstream gradient is given (loss_mode NASG_LOSS_GIVEN: g_rgb_or_target
+ * holds dLoss/dRGB [N][3] f32), or formed in the kernel from each primitive's colour
+ * and a target colour (NASG_LOSS_MSE: g_rgb_or_target holds the target [N][3] f32;
+ * fitting the appearance model of Sec. 4.2, eq:app_model, to per-primitive colours
+ * without a residual kernel or a gradient buffer). With desc->param_dtype = BF16 the
+ * model is evaluated at RNE_bf16(master) (the stored BF16 copy); with F32 at master.
+ * Primitives not listed are left untouched (their m, v do not advance).
+ *   idx/n_idx     device list of primitives (NULL: all N). Entries outside [0, N) are
+ *                 skipped (and still counted in n_listed).
  *   n_idx_device  device int32, nullable: when given, the list length is
  *                 min(n_idx, *n_idx_device) (so the count produced by
- *                 nasg_frustum_compact can be used without a host round trip).
+ *                 nasg_frustum_compact can be used without a host round trip);
+ *                 n_listed is that length.
  *   rgb, g_means  device [N][3] f32 outputs for the listed primitives, nullable.
  * desc->accumulate must be 0. Errors as nasgabor_eval_bwd; NASG_ERR_RANGE for
- * bad hyperparameters.
+ * bad hyperparameters or an unknown loss_mode.
  */
 nasg_status nasgabor_fused_step(const nasg_desc* desc, const nasg_train_state* state, const float* means,
                                 const float* cam, const int32_t* idx, int64_t n_idx,
-                                const int32_t* n_idx_device, const float* g_rgb,
+                                const int32_t* n_idx_device, const float* g_rgb_or_target, int32_t loss_mode,
                                 const nasg_adam_hparams* hparams, float* rgb, float* g_means, void* stream);
+
+/*
+ * Writes the BF16 copies of a training state from its FP32 masters, for all N
+ * primitives: params_bf16 = RNE_bf16(master) [P][N*L] and c0_bf16 = RNE_bf16(c0_master)
+ * [3][N] (a NULL copy is skipped); m and v are not touched. The copies the fused step
+ * and the fitting step evaluate and write are these roundings (the model is
+ * evaluated at the stored BF16 values); use this after initialising or loading the
+ * masters. P = nasg_param_planes(desc->frame_mode, desc->lobe_family). Errors:
+ * NASG_ERR_NULL (a copy without its master), NASG_ERR_ALIGN, NASG_ERR_RANGE (desc).
+ */
+nasg_status nasg_train_state_refresh_bf16(const nasg_desc* desc, const nasg_train_state* state, void* stream);
 
 /* Bytes of device workspace nasg_frustum_compact needs for n primitives. */
 size_t nasg_frustum_workspace_bytes(int64_t n);
@@ -247,7 +275,8 @@ nasg_status nasg_frustum_compact(int64_t n, const float* means, const float* rot
  *     loads the library holds until the process exits; larger n is rejected
  *     with NASG_ERR_CAPACITY before anything is launched;
  *   - the first call on a device looks up the array's device address (once per
- *     device, with that device current); make that first call before any
+ *     device, with that device current) and keeps it for the process (see the
+ *     conventions above on cudaDeviceReset); make that first call before any
  *     stream capture;
  *   - every call shares the one array: calls that may overlap on the GPU (on
  *     different streams without ordering between them) race and corrupt each

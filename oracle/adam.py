@@ -11,6 +11,13 @@ order of torch.optim.Adam:
     theta <- theta - (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps)
 Parameters are stored as BF16 round-to-nearest-even copies of an FP32 master;
 the model is evaluated at the BF16 values.
+
+The fused step's upstream gradient is either given (dLoss/dRGB per primitive) or
+that of a mean squared error against per-primitive target colours, the fit of
+the appearance model (Sec. 4.2, eq:app_model) to colours: with the listed
+primitives I (n_listed = |I|),
+    Loss = (1 / (3 n_listed)) sum_{i in I} sum_c (c_ic - t_ic)^2,
+    dLoss/dc_ic = 2 (c_ic - t_ic) / (3 n_listed).
 """
 from __future__ import annotations
 
@@ -40,13 +47,15 @@ def bf16_round(x):
 
 def fused_step(master, m, v, c0_master, c0_m, c0_v, means, cam, g_rgb, idx, n_lobes, t,
                lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, frame_mode=ng.FRAME_QUAT,
-               norm_mode=ng.NORM_APPROX):
+               norm_mode=ng.NORM_APPROX, loss="given"):
     """Forward + backward + Adam for the primitives listed in idx (others untouched).
 
     master/m/v: (P, N*L); c0_master/c0_m/c0_v: (3, N); g_rgb: (N, 3) upstream
-    gradient for every primitive (only rows in idx are used). The model is
-    evaluated at bf16_round(master). Returns dict with rgb (len(idx), 3) and the
-    updated state arrays (float64, full size).
+    gradient for every primitive (loss "given"), or the target colours (loss
+    "mse": the mean squared error of the module docstring); only rows in idx are
+    used. The model is evaluated at bf16_round(master). Returns dict with rgb
+    (len(idx), 3), the upstream gradient used (g_rgb, len(idx) x 3), the loss
+    (mse only) and the updated state arrays (float64, full size).
     """
     idx = np.asarray(idx, dtype=np.int64)
     P = ng.lobe_planes(frame_mode)
@@ -56,8 +65,16 @@ def fused_step(master, m, v, c0_master, c0_m, c0_v, means, cam, g_rgb, idx, n_lo
     p_sub = bf16_round(np.asarray(master, dtype=np.float64)[:, lobe_idx])
     c0_sub = bf16_round(np.asarray(c0_master, dtype=np.float64)[:, idx])
     mu = np.asarray(means)[idx]
-    g = np.asarray(g_rgb, dtype=np.float64)[idx]
     rgb = ng.forward(p_sub, c0_sub, mu, cam, L, frame_mode, norm_mode)
+    value = None
+    if loss == "given":
+        g = np.asarray(g_rgb, dtype=np.float64)[idx]
+    elif loss == "mse":
+        res = rgb - np.asarray(g_rgb, dtype=np.float64)[idx]
+        value = float(np.sum(res * res) / (3.0 * len(idx))) if len(idx) else 0.0
+        g = 2.0 * res / (3.0 * max(len(idx), 1))
+    else:
+        raise ValueError(f"unknown loss {loss!r}")
     g_p, g_c0, _ = ng.backward(p_sub, c0_sub, mu, cam, g, L, frame_mode, norm_mode)
     out = {k: np.array(val, dtype=np.float64) for k, val in
            (("master", master), ("m", m), ("v", v), ("c0", c0_master), ("c0_m", c0_m), ("c0_v", c0_v))}
@@ -68,6 +85,8 @@ def fused_step(master, m, v, c0_master, c0_m, c0_v, means, cam, g_rgb, idx, n_lo
                              g_c0, t, lr, beta1, beta2, eps)
     out["c0"][:, idx], out["c0_m"][:, idx], out["c0_v"][:, idx] = th, mm, vv
     out["rgb"] = rgb
+    out["g_rgb"] = g
+    out["loss"] = value
     assert P == out["master"].shape[0]
     return out
 

@@ -26,6 +26,7 @@ lib = ctypes.CDLL(LIB_PATH)
 FRAME = {"quat": 0, "cos": 1}
 NORM = {"approx": 0, "none": 1, "exact": 2}
 FAMILY = {"nasgabor": 0, "nasg": 1, "sg": 2, "phase": 3}
+LOSS = {"given": 0, "mse": 1}
 ACT = {"raw": 0, "identity": 1}
 PLANES = {"quat": 10, "cos": 9}
 
@@ -92,7 +93,7 @@ _decl("nasgabor_fused_fwd_bwd", [_P(NasgDesc), _vp, _vp, _vp, _P(ctypes.c_float)
 _decl("sh_eval_fwd", [_i32, _i64, _vp, _vp, _P(ctypes.c_float), _vp, _vp])
 _decl("sh_eval_bwd", [_i32, _i64, _vp, _vp, _P(ctypes.c_float), _vp, _vp, _vp, _vp])
 _decl("nasg_math_probe", [_i32, _vp, _vp, _vp, _i64, _vp])
-_decl("nasgabor_fused_step", [_P(NasgDesc), _P(NasgTrainState), _vp, _P(ctypes.c_float), _vp, _i64, _vp, _vp,
+_decl("nasgabor_fused_step", [_P(NasgDesc), _P(NasgTrainState), _vp, _P(ctypes.c_float), _vp, _i64, _vp, _vp, _i32,
                               _P(NasgAdam), _vp, _vp, _vp])
 _decl("nasg_frustum_workspace_bytes", [_i64], ctypes.c_size_t)
 _decl("nasgabor_batched_workspace_bytes", [_i32], ctypes.c_size_t)
@@ -109,6 +110,7 @@ _decl("nasg_frustum_compact_noalloc", [_i64, _vp, _P(ctypes.c_float), _P(ctypes.
 _decl("nasg_lr_heuristic", [_vp, _i32, _i32, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                            ctypes.c_double, _P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)])
 _decl("nasg_cosine_lr_factor", [_i64, _i64, _i64], ctypes.c_double)
+_decl("nasg_train_state_refresh_bf16", [_P(NasgDesc), _P(NasgTrainState), _vp])
 _decl("nasg_frustum_compact", [_i64, _vp, _P(ctypes.c_float), _P(ctypes.c_float), ctypes.c_float, ctypes.c_float,
                                _vp, _vp, _vp, ctypes.c_size_t, _vp])
 
@@ -341,17 +343,43 @@ def nasg_math_probe(fn, x, stream=None):
 
 
 class TrainState:
-    """FP32 master, Adam moments and BF16 copies of one parameter set (device tensors)."""
+    """FP32 master, Adam moments and BF16 copies of one parameter set (device tensors).
+    The BF16 copies are written by the library (nasg_train_state_refresh_bf16)."""
 
-    def __init__(self, master, c0_master, m=None, v=None, c0_m=None, c0_v=None, bf16_copies=True):
+    # stored scalars per lobe -> a (frame, family) layout with that many planes
+    _LAYOUT_OF_PLANES = {10: ("quat", "nasgabor"), 9: ("cos", "nasgabor"), 8: ("quat", "sg"), 11: ("quat", "phase")}
+
+    def __init__(self, master, c0_master, m=None, v=None, c0_m=None, c0_v=None, bf16_copies=True,
+                 frame_mode=None, family=None, stream=None):
         self.master = _cuda(master, "master", torch.float32)
         self.c0_master = _cuda(c0_master, "c0_master", torch.float32)
         self.m = torch.zeros_like(master) if m is None else _cuda(m, "m", torch.float32)
         self.v = torch.zeros_like(master) if v is None else _cuda(v, "v", torch.float32)
         self.c0_m = torch.zeros_like(c0_master) if c0_m is None else _cuda(c0_m, "c0_m", torch.float32)
         self.c0_v = torch.zeros_like(c0_master) if c0_v is None else _cuda(c0_v, "c0_v", torch.float32)
-        self.params_bf16 = master.to(torch.bfloat16) if bf16_copies else None
-        self.c0_bf16 = c0_master.to(torch.bfloat16) if bf16_copies else None
+        self.params_bf16 = torch.empty(master.shape, dtype=torch.bfloat16, device=master.device) if bf16_copies else None
+        self.c0_bf16 = torch.empty(c0_master.shape, dtype=torch.bfloat16, device=master.device) if bf16_copies else None
+        n = c0_master.shape[1]
+        if frame_mode is None or family is None:
+            if master.dim() != 2 or master.shape[0] not in self._LAYOUT_OF_PLANES:
+                raise ValueError(f"master must be [P, N*L] with P in {sorted(self._LAYOUT_OF_PLANES)}")
+            f0, fam0 = self._LAYOUT_OF_PLANES[master.shape[0]]
+            frame_mode, family = frame_mode or f0, family or fam0
+        planes = param_planes(frame_mode, family)
+        if master.dim() != 2 or master.shape[0] != planes or (n and master.shape[1] % n):
+            raise ValueError(f"master must be [{planes}, N*L] with c0_master [3, N]")
+        self.n_lobes = master.shape[1] // n if n else 1
+        self.frame_mode, self.family = frame_mode, family
+        if bf16_copies:
+            self.refresh_bf16(stream)
+
+    def refresh_bf16(self, stream=None):
+        """BF16 copies = RNE(FP32 masters), written by the library."""
+        desc = make_desc(self.c0_master.shape[1], max(self.n_lobes, 1), self.frame_mode, torch.bfloat16,
+                         family=self.family)
+        st = self.as_c()
+        _check(lib.nasg_train_state_refresh_bf16(ctypes.byref(desc), ctypes.byref(st), _stream(stream)),
+               "nasg_train_state_refresh_bf16")
 
     def as_c(self):
         return NasgTrainState(_ptr(self.master), _ptr(self.m), _ptr(self.v), _ptr(self.params_bf16),
@@ -360,8 +388,10 @@ class TrainState:
 
 def nasgabor_fused_step(state, means, cam, g_rgb, n_lobes, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
                         idx=None, n_idx_device=None, frame_mode="quat", norm_mode="approx", act_mode="raw",
-                        evaluate_bf16=True, rgb=None, g_means=None, stream=None, family="nasgabor"):
-    """Forward + backward + Adam for the listed primitives; state (TrainState) updated in place."""
+                        evaluate_bf16=True, rgb=None, g_means=None, stream=None, family="nasgabor", loss="given"):
+    """Forward + backward + Adam for the listed primitives; state (TrainState) updated in place.
+    loss="given": g_rgb is dLoss/dRGB; loss="mse": g_rgb is the target colour [N, 3] and the
+    kernel forms dLoss/dc = 2 (c - target) / (3 n_listed) (mean squared error)."""
     _cuda(means, "means", torch.float32)
     _cuda(g_rgb, "g_rgb", torch.float32)
     n = means.shape[0]
@@ -377,7 +407,7 @@ def nasgabor_fused_step(state, means, cam, g_rgb, n_lobes, step, lr=1e-3, beta1=
     hp = NasgAdam(lr, beta1, beta2, eps, int(step))
     st = state.as_c()
     _check(lib.nasgabor_fused_step(ctypes.byref(desc), ctypes.byref(st), _ptr(means), _cam(cam), _ptr(idx),
-                                   0 if idx is None else idx.numel(), _ptr(n_idx_device), _ptr(g_rgb),
+                                   0 if idx is None else idx.numel(), _ptr(n_idx_device), _ptr(g_rgb), LOSS[loss],
                                    ctypes.byref(hp), _ptr(rgb), _ptr(g_means), _stream(stream)),
            "nasgabor_fused_step")
     return rgb

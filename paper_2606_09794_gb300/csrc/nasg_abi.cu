@@ -2,6 +2,10 @@
 // device properties cache.
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "nasg_host.h"
 #include "nasg_tma.cuh"
 
@@ -11,9 +15,11 @@ namespace nasg {
 __device__ int g_device_error = 0;
 
 int* device_error_word() {
+  static std::mutex mu;
   static int* cached[64] = {nullptr};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
   if (!cached[dev]) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) return nullptr;
@@ -26,10 +32,30 @@ static thread_local int32_t g_last_cuda_error = 0;
 
 void record_cuda_error(cudaError_t e) { g_last_cuda_error = static_cast<int32_t>(e); }
 
+nasg_status ensure_smem_limit(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> set;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return check_launch();
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = set[{dev, kernel}];
+  if (bytes > have) {
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e != cudaSuccess) {
+      record_cuda_error(e);
+      return NASG_ERR_CUDA;
+    }
+    have = bytes;
+  }
+  return NASG_OK;
+}
+
 int sm_count() {
+  static std::mutex mu;
   static int cached[64] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  std::lock_guard<std::mutex> lock(mu);
   if (cached[dev] == 0) {
     int v = 0;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;

@@ -503,13 +503,7 @@ static nasg_status launch_batched_k(const BatchArgs& b, int blocks_per_sm, bool 
     constexpr int NS = batch_stages<T>();
     const size_t smem = size_t(NS) * batch_stage_bytes<T, P>() + 2 * NS * sizeof(uint64_t) +
                         size_t(b.n_scenes) * sizeof(SceneDev);
-    static size_t configured[2] = {0, 0};  // per instantiation pair (default, run-time flags)
-    size_t& cfg = configured[dflt ? 0 : 1];
-    if (smem > cfg) {
-      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
-        return check_launch();
-      cfg = smem;
-    }
+    if (const nasg_status e = ensure_smem_limit(reinterpret_cast<const void*>(k), smem); e != NASG_OK) return e;
     int fit = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k, kStagedThreads, smem) != cudaSuccess || fit < 1)
       fit = 1;
@@ -602,8 +596,11 @@ extern "C" nasg_status nasgabor_batched_autotune(const nasg_scene* scenes, int32
         status = nasgabor_batched_run(&pl, &t, stream);  // warm-up
         if (status != NASG_OK) break;
         cudaEventRecord(e0, st);
-        for (int r = 0; r < reps; ++r) nasgabor_batched_run(&pl, &t, stream);
+        // every timed run is checked: a refused launch would otherwise time (almost) nothing
+        // and be picked as the fastest
+        for (int r = 0; r < reps && status == NASG_OK; ++r) status = nasgabor_batched_run(&pl, &t, stream);
         cudaEventRecord(e1, st);
+        if (status != NASG_OK) break;
         if (cudaEventSynchronize(e1) != cudaSuccess) {
           record_cuda_error(cudaGetLastError());
           status = NASG_ERR_CUDA;

@@ -324,6 +324,15 @@ struct LobePartials {
 // With a carrier phase phi the sin(k v) sin(phi) part of the carrier integrates
 // to zero (the envelope is even in v), so R = 2 / (1 + cos(phi) Psi), its
 // Lam / k derivatives scale by cos(phi), and d ln R/dphi = (R/2) sin(phi) Psi.
+// 1 + cos(phi) Psi cancels where phi ~ pi and Psi ~ 1 (k << Lam: the lobe's integral
+// tends to 0), so it is formed as (1 - Psi) + 2 cos^2(phi/2) Psi with 1 - Psi from
+// its own expression: for sig > 1, with delta = k^2/(s + Lam) = Lam - s and
+// e^{-delta} - 1 = em,
+//   (1 - Psi)(1 - e^{-2 Lam}) = -em - (delta/s)(1 + em) + e^{-2 Lam} (delta/s - em) / (1 + em);
+// for |sig| <= 1 and Lam <= 1, from S(Lam^2) c e^{-Lam} = 1 (the k = 0 integral),
+//   1 - Psi = c e^{-Lam} (S(Lam^2) - S(sig)) = c e^{-Lam} k^2 sum_n D_n/(2n+1)!,
+//   D_1 = 1, D_{n+1} = Lam^2 D_n + sig^n (the difference quotient of x^n);
+// elsewhere Psi < 0.9 and 1 - Psi has no cancellation.
 template <bool GRAD, bool PHASE = false>
 __device__ __forceinline__ void exact_norm1(float lam, float a, float k, float& r, float& dl, float& da,
                                             float& dk, float phi = 0.f, float* dphi = nullptr) {
@@ -336,8 +345,23 @@ __device__ __forceinline__ void exact_norm1(float lam, float a, float k, float& 
   float es, esp, dpsi_dl = 0.f;
   bool rearranged = false;
   float s = 0.f, A = 0.f, B = 0.f, rs2 = 0.f;
+  float omp = 0.f;        // 1 - Psi where it needs its own expression (PHASE)
+  bool have_omp = false;
   if (fabsf(sig) <= 1.f) {
     const float el = vexp(-L);
+    if (PHASE && L <= 1.f) {
+      const float L2 = L * L;
+      const float inv_fact[5] = {1.f / 6.f, 1.f / 120.f, 1.f / 5040.f, 1.f / 362880.f, 1.f / 39916800.f};
+      float dn = 1.f, pw = sig, acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        acc = fmaf(dn, inv_fact[j], acc);
+        dn = fmaf(L2, dn, pw);
+        pw *= sig;
+      }
+      omp = c * el * (k * k) * acc;
+      have_omp = true;
+    }
     float S = fmaf(sig, 1.f / 39916800.f, 1.f / 362880.f);
     S = fmaf(S, sig, 1.f / 5040.f);
     S = fmaf(S, sig, 1.f / 120.f);
@@ -359,6 +383,13 @@ __device__ __forceinline__ void exact_norm1(float lam, float a, float k, float& 
     es = (A - B) * (0.5f * rs);
     esp = fmaf(s, A + B, B - A) * (0.25f * rs2 * rs);
     rearranged = true;
+    if (PHASE) {
+      const float delta = (k * k) * rcpa(s + L);
+      const float em = vexpm1n(-delta);
+      const float q = delta * rs;
+      omp = (-em - q * (1.f + em) + vexp(-2.f * L) * (q - em) * rcpa(1.f + em)) * rom;
+      have_omp = true;
+    }
   } else {
     const float rt = rsqa(-sig);
     const float t = -sig * rt;
@@ -370,8 +401,14 @@ __device__ __forceinline__ void exact_norm1(float lam, float a, float k, float& 
   }
   const float psi = c * es;
   float cph = 1.f, sph = 0.f;
-  if (PHASE) vsincos<float>(phi, sph, cph);
-  r = 2.f * rcpa(fmaf(cph, psi, 1.f));
+  if (PHASE) {
+    vsincos<float>(phi, sph, cph);
+    float sh, ch;  // 1 + cos(phi) = 2 cos^2(phi/2)
+    vsincos<float>(0.5f * phi, sh, ch);
+    r = 2.f * rcpa(fmaf(2.f * ch * ch, psi, have_omp ? omp : 1.f - psi));
+  } else {
+    r = 2.f * rcpa(1.f + psi);
+  }
   if (GRAD) {
     if (rearranged) {
       const float e2 = vexp(-2.f * L);
@@ -422,10 +459,65 @@ __device__ __forceinline__ void exact_norm_phase(P2 lam, P2 a, P2 k, P2 phi, P2&
   exact_norm1<GRAD, true>(lam.v.y, a.v.y, k.v.y, r.v.y, dl.v.y, da.v.y, dk.v.y, phi.v.y, &dphi.v.y);
 }
 
-// One lobe of family FAM (a, k, phi ignored where the family has none; see Family).
+// The direction-independent factors of one lobe: the normalisation C^-1 (approximate,
+// or exact with the Sec. 5.1 closed form) and its logarithmic derivatives. A kernel that
+// evaluates a lobe at many directions forms them once (lobe_norm) and evaluates each
+// direction with lobe_at; lobe_family does both for one direction.
+template <class V>
+struct LobeNorm {
+  V cinv, dlam, da, dk, dphi;  // C^-1 and d ln C^-1 / d(lam, a, k, phi)
+};
+
 template <bool GRAD, int FAM, class V>
-__device__ __forceinline__ V lobe_family(const V* d, const V* x, const V* z, V lam, V a, V k, V phi,
-                                         bool normalised, bool exact, LobePartials<V>* pd) {
+__device__ __forceinline__ void lobe_norm(V lam, V a, V k, V phi, bool normalised, bool exact, LobeNorm<V>& nc) {
+  using F = Family<FAM>;
+  nc.cinv = vconst<V>(1.f);
+  nc.dlam = vconst<V>(0.f);
+  nc.da = vconst<V>(0.f);
+  nc.dk = vconst<V>(0.f);
+  nc.dphi = vconst<V>(0.f);
+  if (!normalised) return;
+  const V em = vexpm1n(-2.f * lam);  // e^{-2 lam} - 1 (negative)
+  const V r_em = vrcp(em);
+  if (F::HAS_A) {
+    const V opa = 1.f + a;
+    nc.cinv = -((lam * (opa * vrsqrt(opa))) * (kInvTwoPi * r_em));
+  } else {
+    nc.cinv = -(lam * (kInvTwoPi * r_em));
+  }
+  if (GRAD) {
+    // d ln C^-1/d lam = 1/lam - 2 e^{-2 lam}/(1 - e^{-2 lam}); d ln C^-1/d a = 1/(2 (1+a))
+    nc.dlam = vfma(2.f * (1.f + em), r_em, vrcp(lam));
+    if (F::HAS_A) nc.da = 0.5f * vrcp(1.f + a);
+  }
+  // without a carrier the closed form is the NASG constant itself (Psi = 1)
+  if (exact && F::HAS_PHASE) {
+    V r, dr_lam, dr_a, dr_k, dr_phi;
+    exact_norm_phase<GRAD>(lam, a, k, phi, r, dr_lam, dr_a, dr_k, dr_phi);
+    nc.cinv = nc.cinv * r;
+    if (GRAD) {
+      nc.dlam = nc.dlam + dr_lam;
+      nc.da = nc.da + dr_a;
+      nc.dk = dr_k;
+      nc.dphi = dr_phi;
+    }
+  } else if (exact && F::HAS_K) {
+    V r, dr_lam, dr_a, dr_k;
+    exact_norm<GRAD>(lam, a, k, r, dr_lam, dr_a, dr_k);
+    nc.cinv = nc.cinv * r;
+    if (GRAD) {
+      nc.dlam = nc.dlam + dr_lam;
+      nc.da = nc.da + dr_a;
+      nc.dk = dr_k;
+    }
+  }
+}
+
+// One lobe of family FAM at direction d, given its normalisation factors nc (a, k,
+// phi ignored where the family has none; see Family).
+template <bool GRAD, int FAM, class V>
+__device__ __forceinline__ V lobe_at(const V* d, const V* x, const V* z, V lam, V a, V k, V phi,
+                                     const LobeNorm<V>& nc, bool exact, LobePartials<V>* pd) {
   using F = Family<FAM>;
   using M = typename VecTraits<V>::Mask;
   const V u = vfma(d[0], z[0], vfma(d[1], z[1], d[2] * z[2]));
@@ -459,47 +551,9 @@ __device__ __forceinline__ V lobe_family(const V* d, const V* x, const V* z, V l
   } else if (F::HAS_K) {
     vcarrier(0.5f * k * v, h, sin_kv);
   }
-  V cinv = vconst<V>(1.f), dlnc_dlam = vconst<V>(0.f), dlnc_da = vconst<V>(0.f), dlnc_dk = vconst<V>(0.f);
-  V dlnc_dphi = vconst<V>(0.f);
-  if (normalised) {
-    const V em = vexpm1n(-2.f * lam);  // e^{-2 lam} - 1 (negative)
-    const V r_em = vrcp(em);
-    if (F::HAS_A) {
-      const V opa = 1.f + a;
-      cinv = -((lam * (opa * vrsqrt(opa))) * (kInvTwoPi * r_em));
-    } else {
-      cinv = -(lam * (kInvTwoPi * r_em));
-    }
-    if (GRAD) {
-      // d ln C^-1/d lam = 1/lam - 2 e^{-2 lam}/(1 - e^{-2 lam}); d ln C^-1/d a = 1/(2 (1+a))
-      dlnc_dlam = vfma(2.f * (1.f + em), r_em, vrcp(lam));
-      if (F::HAS_A) dlnc_da = 0.5f * vrcp(1.f + a);
-    }
-    // without a carrier the closed form is the NASG constant itself (Psi = 1)
-    if (exact && F::HAS_PHASE) {
-      V r, dr_lam, dr_a, dr_k, dr_phi;
-      exact_norm_phase<GRAD>(lam, a, k, phi, r, dr_lam, dr_a, dr_k, dr_phi);
-      cinv = cinv * r;
-      if (GRAD) {
-        dlnc_dlam = dlnc_dlam + dr_lam;
-        dlnc_da = dlnc_da + dr_a;
-        dlnc_dk = dr_k;
-        dlnc_dphi = dr_phi;
-      }
-    } else if (exact && F::HAS_K) {
-      V r, dr_lam, dr_a, dr_k;
-      exact_norm<GRAD>(lam, a, k, r, dr_lam, dr_a, dr_k);
-      cinv = cinv * r;
-      if (GRAD) {
-        dlnc_dlam = dlnc_dlam + dr_lam;
-        dlnc_da = dlnc_da + dr_a;
-        dlnc_dk = dr_k;
-      }
-    }
-  }
   // the antipode (G := 0 with zero derivatives) is applied once, through C^-1 p E;
   // every other factor below is finite there (tau, ln kappa, 1/(1+u) are 0)
-  const V cpe = vsel(anti, 0.f, cinv * pe);
+  const V cpe = vsel(anti, 0.f, nc.cinv * pe);
   const V G = cpe * h;
   if (GRAD) {
     pd->u = u;
@@ -515,22 +569,31 @@ __device__ __forceinline__ V lobe_family(const V* d, const V* x, const V* z, V l
       pd->G_u = G * vfma(two_lam_ek, dlne_du + inv_opu, dlne_du);
       const V gv_env = G * (two_lam_ek + 1.f) * dlne_dv;
       pd->G_v = F::HAS_K ? vfma(G * (two_lam_ek + 1.f), dlne_dv, -(cpe_sin * (0.5f * k))) : gv_env;
-      pd->G_a = G * vfma((two_lam_ek + 1.f) * ln_k, v * v * inv_s2, dlnc_da);
+      pd->G_a = G * vfma((two_lam_ek + 1.f) * ln_k, v * v * inv_s2, nc.da);
     } else {
       pd->G_u = G * lam;                                // d/du 2 lam (kappa - 1) = lam
       pd->G_v = vconst<V>(0.f);
       pd->G_a = vconst<V>(0.f);
     }
     if (F::HAS_K) {
-      pd->G_k = exact ? vfma(G, dlnc_dk, -(cpe_sin * (0.5f * v))) : -(cpe_sin * (0.5f * v));
+      pd->G_k = exact ? vfma(G, nc.dk, -(cpe_sin * (0.5f * v))) : -(cpe_sin * (0.5f * v));
     } else {
       pd->G_k = vconst<V>(0.f);
     }
-    pd->G_phi = F::HAS_PHASE ? (exact ? vfma(G, dlnc_dphi, -(0.5f * cpe_sin)) : -(0.5f * cpe_sin))
+    pd->G_phi = F::HAS_PHASE ? (exact ? vfma(G, nc.dphi, -(0.5f * cpe_sin)) : -(0.5f * cpe_sin))
                              : vconst<V>(0.f);
-    pd->G_lam = G * vfma(2.f, em1, dlnc_dlam);
+    pd->G_lam = G * vfma(2.f, em1, nc.dlam);
   }
   return G;
+}
+
+// One lobe of family FAM at one direction (normalisation included).
+template <bool GRAD, int FAM, class V>
+__device__ __forceinline__ V lobe_family(const V* d, const V* x, const V* z, V lam, V a, V k, V phi,
+                                         bool normalised, bool exact, LobePartials<V>* pd) {
+  LobeNorm<V> nc;
+  lobe_norm<GRAD, FAM>(lam, a, k, phi, normalised, exact, nc);
+  return lobe_at<GRAD, FAM>(d, x, z, lam, a, k, phi, nc, exact, pd);
 }
 
 // The NASGabor lobe.

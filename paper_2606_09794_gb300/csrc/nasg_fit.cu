@@ -9,10 +9,15 @@
 // to the mean (the loss value).
 //
 // Mapping: a slice of S lanes per primitive, each lane two student lobes
-// (packed FP32x2). Activations and frames are formed once per step. The
-// gradient is linear in the per-direction partials, so the lane accumulates
-// dLoss/dlam, /da, /dk, /dw and dLoss/dx, dLoss/dz over the directions and
-// applies the activation slopes and the quaternion-frame chain once at the end.
+// (packed FP32x2). Activations, frames and the normalisation factors (which do
+// not depend on the direction) are formed once per step; the direction loop
+// carries only what each direction needs (frame axes, activated values,
+// normalisation factors). The gradient is linear in the per-direction partials,
+// so the lane accumulates dLoss/dlam, /da, /dk, /dw and dLoss/dx, dLoss/dz over
+// the directions; after the loop it reloads its FP32 master values (which the
+// Adam update reads anyway), forms the activation slopes and the quaternion
+// frame from them again, and applies the chain once, so that none of those
+// quantities stays live across the loop.
 // The teacher's lobe pairs (Lt/2 of them) are spread over the slice: for a
 // group of G = S/(Lt/2) directions, lane g evaluates teacher pair g % (Lt/2) at
 // direction g / (Lt/2), and the teacher colours are exchanged by shuffles.
@@ -58,6 +63,39 @@ __device__ __forceinline__ void fit_adam(const FitArgs& s, float g, float& th, f
   th = fmaf(-s.step_size, m * rcpa(den), th);
 }
 
+// The per-step quantities of a lobe pair that its evaluation at each direction needs.
+struct FitLobes {
+  P2 x[3], z[3];
+  P2 lam, a, k, w[3];
+  LobeNorm<P2> nc;
+};
+
+template <bool GRAD, bool EXACT>
+__device__ __forceinline__ void fit_lobes(const P2* raw, bool identity, bool normalised, FitLobes& f) {
+  Act<P2> act;
+  activate(raw + 4, identity, act);
+  QuatFrame<P2> qf;
+  quat_frame(raw, qf);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    f.x[c] = qf.x[c];
+    f.z[c] = qf.z[c];
+    f.w[c] = act.w[c];
+  }
+  f.lam = act.lam;
+  f.a = act.a;
+  f.k = act.k;
+  lobe_norm<GRAD, kFamNasGabor>(act.lam, act.a, act.k, p2(0.f), normalised, EXACT, f.nc);
+}
+
+// A float2 load the compiler may not merge with an earlier load of the same address
+// (so that values reloaded after the direction loop are not kept live across it).
+__device__ __forceinline__ float2 ld_f2_fresh(const float* p) {
+  float2 v;
+  asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+
 // Loads the pair (2g, 2g+1) of lobes of primitive i from [P][N*L] raw planes.
 __device__ __forceinline__ void load_pair(const float* planes, int64_t n, int L, int64_t i, int l0, bool quant,
                                           P2* out) {
@@ -96,24 +134,23 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
     const bool ok = t < total;
     const int64_t i = ok ? (t >> slog) : 0;
     const bool mine = ok && l0 < ls;
-    // ---- per-step constants of the lane's student and teacher pairs ----
-    P2 sp[10], tpar[10];
-    if (mine) load_pair(s.master, s.n, ls, i, l0, s.quantize != 0, sp);
-    else {
+    // ---- per-step quantities of the lane's student and teacher pairs ----
+    FitLobes stu, tea;
+    {
+      P2 raw[10];
+      if (mine) load_pair(s.master, s.n, ls, i, l0, s.quantize != 0, raw);
+      else {
 #pragma unroll
-      for (int p = 0; p < 10; ++p) sp[p] = p2(p == 0 ? 1.f : 0.f);
-    }
-    if (ok) load_pair(s.teacher, s.n, lt, i, 2 * tp, false, tpar);
-    else {
+        for (int p = 0; p < 10; ++p) raw[p] = p2(p == 0 ? 1.f : 0.f);
+      }
+      fit_lobes<true, EXACT>(raw, s.identity != 0, s.normalised != 0, stu);
+      if (ok) load_pair(s.teacher, s.n, lt, i, 2 * tp, false, raw);
+      else {
 #pragma unroll
-      for (int p = 0; p < 10; ++p) tpar[p] = p2(p == 0 ? 1.f : 0.f);
+        for (int p = 0; p < 10; ++p) raw[p] = p2(p == 0 ? 1.f : 0.f);
+      }
+      fit_lobes<false, EXACT>(raw, s.identity != 0, s.normalised != 0, tea);
     }
-    Act<P2> act, tact;
-    activate(sp + 4, s.identity != 0, act);
-    activate(tpar + 4, s.identity != 0, tact);
-    QuatFrame<P2> qf, tqf;
-    quat_frame(sp, qf);
-    quat_frame(tpar, tqf);
     float c0s[3], c0t[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -132,10 +169,10 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
         const int j = min(base + tk, s.n_dirs - 1);
         const P2 d[3] = {p2(__ldg(s.dirs + 3 * j)), p2(__ldg(s.dirs + 3 * j + 1)), p2(__ldg(s.dirs + 3 * j + 2))};
         LobePartials<P2> pd;
-        const P2 Gt = lobe<false>(d, tqf.x, tqf.z, tact.lam, tact.a, tact.k, s.normalised != 0, EXACT, &pd);
+        const P2 Gt = lobe_at<false, kFamNasGabor>(d, tea.x, tea.z, tea.lam, tea.a, tea.k, zero, tea.nc, EXACT, &pd);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const P2 wg = tact.w[c] * Gt;
+          const P2 wg = tea.w[c] * Gt;
           tcol[c] = wg.v.x + wg.v.y;
         }
         for (int o = 1; o < tpairs; o <<= 1) {
@@ -151,11 +188,11 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
         const float dx = __ldg(s.dirs + 3 * j), dy = __ldg(s.dirs + 3 * j + 1), dz = __ldg(s.dirs + 3 * j + 2);
         const P2 d[3] = {p2(dx), p2(dy), p2(dz)};
         LobePartials<P2> pd;
-        const P2 Gs = lobe<true>(d, qf.x, qf.z, act.lam, act.a, act.k, s.normalised != 0, EXACT, &pd);
+        const P2 Gs = lobe_at<true, kFamNasGabor>(d, stu.x, stu.z, stu.lam, stu.a, stu.k, zero, stu.nc, EXACT, &pd);
         float col[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const P2 wg = act.w[c] * Gs;
+          const P2 wg = stu.w[c] * Gs;
           col[c] = mine ? wg.v.x + wg.v.y : 0.f;
         }
         for (int o = S >> 1; o >= 1; o >>= 1) {
@@ -170,7 +207,7 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
           gc[c] = inv3d * r;  // d(per-primitive mean over directions and channels)/dc
           acc_c0[c] += gc[c];
         }
-        const P2 gG = vfma(p2(gc[0]), act.w[0], vfma(p2(gc[1]), act.w[1], p2(gc[2]) * act.w[2]));
+        const P2 gG = vfma(p2(gc[0]), stu.w[0], vfma(p2(gc[1]), stu.w[1], p2(gc[2]) * stu.w[2]));
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc_w[c] = vfma(p2(gc[c]), Gs, acc_w[c]);
         acc_lam = vfma(gG, pd.G_lam, acc_lam);
@@ -186,6 +223,21 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
     }
     // ---- chain to the raw parameters and take the Adam step ----
     if (mine) {
+      const int64_t NL = s.n * ls;
+      const int64_t off = i * ls + l0;
+      // the FP32 master values, reloaded: the slopes and the frame are formed again from
+      // the values the step evaluated (their BF16 rounding when quantising)
+      float2 th[10];
+      P2 raw[10];
+#pragma unroll
+      for (int p = 0; p < 10; ++p) {
+        th[p] = ld_f2_fresh(s.master + p * NL + off);
+        raw[p] = s.quantize ? p2(fit_bf16_rne(th[p].x), fit_bf16_rne(th[p].y)) : p2(th[p].x, th[p].y);
+      }
+      Act<P2> act;
+      activate(raw + 4, s.identity != 0, act);
+      QuatFrame<P2> qf;
+      quat_frame(raw, qf);
       P2 grad[10];
       quat_frame_grad(qf, acc_gx, acc_gz, grad);
       grad[4] = acc_lam * act.s_lam;
@@ -193,20 +245,17 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
       grad[6] = acc_k * act.s_k;
 #pragma unroll
       for (int c = 0; c < 3; ++c) grad[7 + c] = acc_w[c] * act.s_w[c];
-      const int64_t NL = s.n * ls;
-      const int64_t off = i * ls + l0;
 #pragma unroll
       for (int p = 0; p < 10; ++p) {
-        float2 th = *reinterpret_cast<const float2*>(s.master + p * NL + off);
         float2 mm = *reinterpret_cast<const float2*>(s.m + p * NL + off);
         float2 vv = *reinterpret_cast<const float2*>(s.v + p * NL + off);
-        fit_adam(s, grad[p].v.x, th.x, mm.x, vv.x);
-        fit_adam(s, grad[p].v.y, th.y, mm.y, vv.y);
-        *reinterpret_cast<float2*>(s.master + p * NL + off) = th;
+        fit_adam(s, grad[p].v.x, th[p].x, mm.x, vv.x);
+        fit_adam(s, grad[p].v.y, th[p].y, mm.y, vv.y);
+        *reinterpret_cast<float2*>(s.master + p * NL + off) = th[p];
         *reinterpret_cast<float2*>(s.m + p * NL + off) = mm;
         *reinterpret_cast<float2*>(s.v + p * NL + off) = vv;
         if (s.pbf) {
-          const uint32_t w2 = uint32_t(fit_bf16_bits(th.x)) | (uint32_t(fit_bf16_bits(th.y)) << 16);
+          const uint32_t w2 = uint32_t(fit_bf16_bits(th[p].x)) | (uint32_t(fit_bf16_bits(th[p].y)) << 16);
           *reinterpret_cast<uint32_t*>(s.pbf + p * NL + off) = w2;
         }
       }

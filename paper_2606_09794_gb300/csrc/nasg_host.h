@@ -29,8 +29,14 @@ inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 int sm_count();
 
 // Device address of the library's device error word on the current device
-// (resolved once per device); nullptr if it cannot be resolved.
+// (resolved once per device, under a lock); nullptr if it cannot be resolved.
 int* device_error_word();
+
+// Raises `kernel`'s dynamic shared-memory limit to at least `bytes` on the current
+// device. The attribute belongs to the device, so what has been set is remembered
+// per (device, kernel) under a lock; later calls cost a lookup. NASG_OK or
+// NASG_ERR_CUDA.
+nasg_status ensure_smem_limit(const void* kernel, size_t bytes);
 
 // Grid for a grid-stride loop over `items` with `block` threads: one item per
 // thread, capped so that a 64-bit item count never overflows the grid.

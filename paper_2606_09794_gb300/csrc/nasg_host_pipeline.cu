@@ -40,23 +40,33 @@ inline SlotLayout slot_layout(int P, int L, int es, int64_t chunk) {
   return s;
 }
 
-// Two non-blocking copy streams per device, created on first use and kept for
-// the life of the process.
-struct CopyStreams {
+// Per device: two non-blocking copy streams and the ordering events of a call
+// (timing disabled), created on first use and kept for the life of the process,
+// and a lock that a call holds while it enqueues, so that calls from several host
+// threads on one device take the copy streams and events in turn.
+struct Pipeline {
   cudaStream_t in = nullptr, out = nullptr;
+  cudaEvent_t start = nullptr, in_done[kSlots] = {}, k_done[kSlots] = {}, out_done[kSlots] = {};
+  bool ready = false;
+  std::mutex call;
 };
-CopyStreams g_streams[kMaxDevices];
-std::mutex g_streams_mu;
+Pipeline g_pipes[kMaxDevices];
+std::mutex g_pipes_mu;
 
-bool copy_streams(CopyStreams& cs) {
+Pipeline* device_pipeline() {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
-  std::lock_guard<std::mutex> lk(g_streams_mu);
-  CopyStreams& s = g_streams[dev];
-  if (!s.in && cudaStreamCreateWithFlags(&s.in, cudaStreamNonBlocking) != cudaSuccess) return false;
-  if (!s.out && cudaStreamCreateWithFlags(&s.out, cudaStreamNonBlocking) != cudaSuccess) return false;
-  cs = s;
-  return true;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pipes_mu);
+  Pipeline& p = g_pipes[dev];
+  if (!p.ready) {
+    auto ev = [](cudaEvent_t& e) { return e || cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess; };
+    bool ok = (p.in || cudaStreamCreateWithFlags(&p.in, cudaStreamNonBlocking) == cudaSuccess) &&
+              (p.out || cudaStreamCreateWithFlags(&p.out, cudaStreamNonBlocking) == cudaSuccess) && ev(p.start);
+    for (int s = 0; ok && s < kSlots; ++s) ok = ev(p.in_done[s]) && ev(p.k_done[s]) && ev(p.out_done[s]);
+    if (!ok) return nullptr;
+    p.ready = true;
+  }
+  return &p;
 }
 
 }  // namespace
@@ -89,8 +99,10 @@ extern "C" nasg_status nasgabor_fused_fwd_bwd_host(const nasg_desc* desc, const 
   const int es = elem_size(desc->param_dtype);
   const SlotLayout sl = slot_layout(P, L, es, chunk);
   if (workspace_bytes < kSlots * sl.bytes) return NASG_ERR_RANGE;
-  CopyStreams cs;
-  if (!copy_streams(cs)) return check_launch();
+  Pipeline* pipe = device_pipeline();
+  if (!pipe) return check_launch();
+  std::lock_guard<std::mutex> call_lock(pipe->call);
+  Pipeline& cs = *pipe;
   cudaStream_t comp = as_stream(stream);
   const int64_t n = desc->n;
   const size_t NL = size_t(n) * L;
@@ -98,16 +110,12 @@ extern "C" nasg_status nasgabor_fused_fwd_bwd_host(const nasg_desc* desc, const 
   const unsigned char* ch = static_cast<const unsigned char*>(c0);
   unsigned char* ws = static_cast<unsigned char*>(workspace);
 
-  cudaEvent_t start, in_done[kSlots], k_done[kSlots], out_done[kSlots];
-  bool ok = cudaEventCreateWithFlags(&start, cudaEventDisableTiming) == cudaSuccess;
-  for (int s = 0; s < kSlots; ++s) {
-    ok = ok && cudaEventCreateWithFlags(&in_done[s], cudaEventDisableTiming) == cudaSuccess;
-    ok = ok && cudaEventCreateWithFlags(&k_done[s], cudaEventDisableTiming) == cudaSuccess;
-    ok = ok && cudaEventCreateWithFlags(&out_done[s], cudaEventDisableTiming) == cudaSuccess;
-  }
-  if (!ok) return check_launch();
+  cudaEvent_t start = cs.start;
+  cudaEvent_t* in_done = cs.in_done;
+  cudaEvent_t* k_done = cs.k_done;
+  cudaEvent_t* out_done = cs.out_done;
   // everything queued on the caller's stream so far happens first
-  ok = cudaEventRecord(start, comp) == cudaSuccess && cudaStreamWaitEvent(cs.in, start, 0) == cudaSuccess &&
+  bool ok = cudaEventRecord(start, comp) == cudaSuccess && cudaStreamWaitEvent(cs.in, start, 0) == cudaSuccess &&
        cudaStreamWaitEvent(cs.out, start, 0) == cudaSuccess;
   const int64_t n_chunks = (n + chunk - 1) / chunk;
   for (int64_t i = 0; ok && st == NASG_OK && i < n_chunks; ++i) {
@@ -156,12 +164,6 @@ extern "C" nasg_status nasgabor_fused_fwd_bwd_host(const nasg_desc* desc, const 
   }
   // the caller's stream resumes after the last outputs are back in host memory
   if (ok) ok = cudaEventRecord(start, cs.out) == cudaSuccess && cudaStreamWaitEvent(comp, start, 0) == cudaSuccess;
-  cudaEventDestroy(start);
-  for (int s = 0; s < kSlots; ++s) {
-    cudaEventDestroy(in_done[s]);
-    cudaEventDestroy(k_done[s]);
-    cudaEventDestroy(out_done[s]);
-  }
   if (st != NASG_OK) return st;
   return ok ? NASG_OK : check_launch();
 }

@@ -69,63 +69,85 @@ struct FrameTraits {
   static constexpr int P = W + 3;         // raw scalars per lobe
 };
 
-// Evaluates the lobes held in pv[0..P) (one lobe per component of V): adds their
-// colour into rgb and, with BWD, writes the P raw-parameter gradients into gp
-// and adds dLoss/dd into gd.
-template <int FRAME, bool FWD, bool BWD, class V>
-__device__ __forceinline__ void lobe_step(const V* pv, const V* d, const V* gc, bool identity, bool normalised,
-                                          bool exact, V* rgb, V* gd, V* gp) {
+// A lobe evaluated at one direction: activations, frame, value and (with the
+// backward) the scalar partials, kept until the upstream gradient is known.
+template <int FRAME, class V>
+struct LobeEval {
+  Act<V> act;
+  QuatFrame<V> qf;
+  CosFrame<V> cf;
+  V x[3], z[3];
+  LobePartials<V> pd;
+  V G;
+};
+
+// Evaluates the lobes held in pv[0..P) (one lobe per component of V) at d.
+template <int FRAME, bool BWD, class V>
+__device__ __forceinline__ void lobe_eval(const V* pv, const V* d, bool identity, bool normalised, bool exact,
+                                          LobeEval<FRAME, V>& e) {
+  using TR = FrameTraits<FRAME>;
+  constexpr int B = TR::B;
+  if constexpr (TR::FAM == kFamNasGabor) {
+    activate(pv + B, identity, e.act);
+  } else {
+    activate_family<TR::FAM>(pv + B, identity, e.act);
+  }
+  if (TR::QUAT) {
+    quat_frame(pv, e.qf);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { e.x[c] = e.qf.x[c]; e.z[c] = e.qf.z[c]; }
+  } else {
+    cos_frame(pv, identity, e.cf);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { e.x[c] = e.cf.x[c]; e.z[c] = e.cf.z[c]; }
+  }
+  if constexpr (TR::FAM == kFamNasGabor) {
+    e.G = lobe<BWD>(d, e.x, e.z, e.act.lam, e.act.a, e.act.k, normalised, exact, &e.pd);
+  } else {
+    e.G = lobe_family<BWD, TR::FAM>(d, e.x, e.z, e.act.lam, e.act.a, e.act.k, e.act.phi, normalised, exact, &e.pd);
+  }
+}
+
+// The backward of evaluated lobes for the upstream dLoss/dRGB gc: writes the P
+// raw-parameter gradients into gp and adds dLoss/dd into gd.
+template <int FRAME, class V>
+__device__ __forceinline__ void lobe_grad(const LobeEval<FRAME, V>& e, const V* d, const V* gc, V* gd, V* gp) {
   using TR = FrameTraits<FRAME>;
   using F = typename TR::F;
   constexpr int B = TR::B;
-  Act<V> act;
-  if constexpr (TR::FAM == kFamNasGabor) {
-    activate(pv + B, identity, act);
-  } else {
-    activate_family<TR::FAM>(pv + B, identity, act);
-  }
-  V x[3], z[3];
-  QuatFrame<V> qf;
-  CosFrame<V> cf;
+  const Act<V>& act = e.act;
+  const LobePartials<V>& pd = e.pd;
+  const V gG = vfma(gc[0], act.w[0], vfma(gc[1], act.w[1], gc[2] * act.w[2]));
+  gp[B] = gG * pd.G_lam * act.s_lam;
+  if constexpr (F::HAS_A) gp[TR::A] = gG * pd.G_a * act.s_a;
+  if constexpr (F::HAS_K) gp[TR::K] = gG * pd.G_k * act.s_k;
+  if constexpr (F::HAS_PHASE) gp[TR::PH] = gG * pd.G_phi;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) gp[TR::W + c] = gc[c] * e.G * act.s_w[c];
+  const V gv = gG * pd.G_v, gu = gG * pd.G_u;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) gd[c] = vfma(gu, e.z[c], vfma(gv, e.x[c], gd[c]));
   if (TR::QUAT) {
-    quat_frame(pv, qf);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) { x[c] = qf.x[c]; z[c] = qf.z[c]; }
+    quat_frame_grad_d(e.qf, d, gv, gu, pd.u, pd.v, gp);
   } else {
-    cos_frame(pv, identity, cf);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) { x[c] = cf.x[c]; z[c] = cf.z[c]; }
+    const V gx[3] = {gv * d[0], gv * d[1], gv * d[2]};
+    const V gz[3] = {gu * d[0], gu * d[1], gu * d[2]};
+    cos_frame_grad(e.cf, gx, gz, gp);
   }
-  LobePartials<V> pd;
-  V G;
-  if constexpr (TR::FAM == kFamNasGabor) {
-    G = lobe<BWD>(d, x, z, act.lam, act.a, act.k, normalised, exact, &pd);
-  } else {
-    G = lobe_family<BWD, TR::FAM>(d, x, z, act.lam, act.a, act.k, act.phi, normalised, exact, &pd);
-  }
+}
+
+// Evaluates the lobes held in pv[0..P): adds their colour into rgb and, with
+// BWD, writes the P raw-parameter gradients into gp and adds dLoss/dd into gd.
+template <int FRAME, bool FWD, bool BWD, class V>
+__device__ __forceinline__ void lobe_step(const V* pv, const V* d, const V* gc, bool identity, bool normalised,
+                                          bool exact, V* rgb, V* gd, V* gp) {
+  LobeEval<FRAME, V> e;
+  lobe_eval<FRAME, BWD>(pv, d, identity, normalised, exact, e);
   if (FWD) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) rgb[c] = vfma(act.w[c], G, rgb[c]);
+    for (int c = 0; c < 3; ++c) rgb[c] = vfma(e.act.w[c], e.G, rgb[c]);
   }
-  if (BWD) {
-    const V gG = vfma(gc[0], act.w[0], vfma(gc[1], act.w[1], gc[2] * act.w[2]));
-    gp[B] = gG * pd.G_lam * act.s_lam;
-    if constexpr (F::HAS_A) gp[TR::A] = gG * pd.G_a * act.s_a;
-    if constexpr (F::HAS_K) gp[TR::K] = gG * pd.G_k * act.s_k;
-    if constexpr (F::HAS_PHASE) gp[TR::PH] = gG * pd.G_phi;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) gp[TR::W + c] = gc[c] * G * act.s_w[c];
-    const V gv = gG * pd.G_v, gu = gG * pd.G_u;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) gd[c] = vfma(gu, z[c], vfma(gv, x[c], gd[c]));
-    if (TR::QUAT) {
-      quat_frame_grad_d(qf, d, gv, gu, pd.u, pd.v, gp);
-    } else {
-      const V gx[3] = {gv * d[0], gv * d[1], gv * d[2]};
-      const V gz[3] = {gu * d[0], gu * d[1], gu * d[2]};
-      cos_frame_grad(cf, gx, gz, gp);
-    }
-  }
+  if (BWD) lobe_grad<FRAME>(e, d, gc, gd, gp);
 }
 
 __device__ __forceinline__ void store1(float* p, float v, bool acc) { *p = acc ? *p + v : v; }
@@ -636,12 +658,7 @@ nasg_status launch_tma_geom(const EvalArgs& a, cudaStream_t s) {
   const TileGeom g = tile_geom<T, P, ANYN>(a.slice_log2, a.n_lobes);
   const size_t smem = size_t(kStages) * g.stage_bytes + 2 * kStages * sizeof(uint64_t);
   auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS, ANYN, LC>;
-  static size_t configured = 0;  // per instantiation
-  if (smem > configured) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
-      return check_launch();
-    configured = smem;
-  }
+  if (const nasg_status e = ensure_smem_limit(reinterpret_cast<const void*>(k), smem); e != NASG_OK) return e;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStagedThreads, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;

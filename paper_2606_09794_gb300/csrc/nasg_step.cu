@@ -4,12 +4,18 @@
 //
 // Step: for every listed primitive, the lobes are evaluated at the stored
 // parameter values (RNE bfloat16 of the FP32 master when desc->param_dtype is
-// BF16), the Supp. F gradients for the given upstream dLoss/dRGB are formed in
+// BF16), the Supp. F gradients for the upstream dLoss/dRGB are formed in
 // registers (never written to memory), and Adam (bias-corrected, in
 // torch.optim.Adam's operation order) updates master, m and v in place and
-// writes the BF16 copy. Primitives not listed are not touched. Mapping and
-// numerics are those of the evaluation kernels (nasg_kernels.cuh): a lane holds
-// two lobes in packed FP32x2 arithmetic and a slice of lanes covers a primitive.
+// writes the BF16 copy. Primitives not listed are not touched. The upstream
+// gradient is either given, or (loss mode MSE) formed in the kernel from the
+// primitive's colour and a target colour: the loss is the mean over the listed
+// primitives and the three channels of (c - target)^2, so dLoss/dc =
+// 2 (c - target) / (3 n_listed), which needs the primitive's whole colour before
+// the backward starts (the lanes' lobe partials wait in registers across the
+// slice reduction). Mapping and numerics are those of the evaluation kernels
+// (nasg_kernels.cuh): a lane holds two lobes in packed FP32x2 arithmetic and a
+// slice of lanes covers a primitive.
 //
 // Compaction: an ordered (deterministic, ascending) list of the primitives
 // whose centre is inside a pinhole frustum, in three launches: per-chunk
@@ -65,11 +71,12 @@ __device__ __forceinline__ void adam(const StepArgs& s, float g, float& th, floa
 // parked in its own shared-memory slot (gslot[p * 256]) rather than kept in
 // registers, so that phase two starts with a fresh register budget and can
 // issue all of its moment and master loads at once. Also does the
-// per-primitive work (colour, dLoss/dmu, c0 Adam). Returns whether the lane
-// holds lobes to update.
-template <int FRAME, typename IDX, bool EVEN>
+// per-primitive work (colour, dLoss/dmu, c0 Adam). LOSS: cur.gc holds the
+// target colour and gscale = 2 / (3 n_listed); the upstream gradient is
+// gscale (colour - target). Returns whether the lane holds lobes to update.
+template <int FRAME, typename IDX, bool EVEN, bool LOSS>
 __device__ __forceinline__ bool step_phase1(const StepArgs& s, const RawItem<float, FrameTraits<FRAME>::P>& cur,
-                                            IDX i, int l0, float2* gslot) {
+                                            IDX i, int l0, float gscale, float2* gslot) {
   constexpr int P = FrameTraits<FRAME>::P;
   const EvalArgs& a = s.e;
   const IDX n = IDX(a.n);
@@ -80,51 +87,92 @@ __device__ __forceinline__ bool step_phase1(const StepArgs& s, const RawItem<flo
   float rgb[3] = {0.f, 0.f, 0.f};
   float gd[3] = {0.f, 0.f, 0.f};
   float d[3] = {0.f, 0.f, 1.f};
+  float gc[3] = {cur.gc[0], cur.gc[1], cur.gc[2]};  // LOSS: the target until the residual is formed
   float inv_dist = 0.f;
+  bool second = true;
+  P2 dv[3];
+  LobeEval<FRAME, P2> ev;
   if (ok) {
     const float rx = cur.mu[0] - a.cam[0], ry = cur.mu[1] - a.cam[1], rz = cur.mu[2] - a.cam[2];
     inv_dist = rsqrtf(rx * rx + ry * ry + rz * rz);
     d[0] = rx * inv_dist; d[1] = ry * inv_dist; d[2] = rz * inv_dist;
     if (IDX(l0) < L) {
       mine = true;
-      const bool second = EVEN || (IDX(l0) + 1 < L);
+      second = EVEN || (IDX(l0) + 1 < L);
       P2 pv[P];
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         const float2 w = cur.w[p];
         pv[p] = quant ? p2(bf16_rne(w.x), bf16_rne(w.y)) : p2(w.x, w.y);
       }
-      const P2 dv[3] = {p2(d[0]), p2(d[1]), p2(d[2])};
-      const P2 gcv[3] = {p2(cur.gc[0]), p2(cur.gc[1]), p2(cur.gc[2])};
-      P2 rgbv[3] = {p2(0.f), p2(0.f), p2(0.f)};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) dv[c] = p2(d[c]);
+      if (LOSS) {
+        lobe_eval<FRAME, true>(pv, dv, a.identity != 0, a.normalised != 0, a.exact != 0, ev);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const P2 t = ev.act.w[c] * ev.G;
+          rgb[c] = t.v.x + (second ? t.v.y : 0.f);
+        }
+      } else {
+        const P2 gcv[3] = {p2(gc[0]), p2(gc[1]), p2(gc[2])};
+        P2 rgbv[3] = {p2(0.f), p2(0.f), p2(0.f)};
+        P2 gdv[3] = {p2(0.f), p2(0.f), p2(0.f)};
+        P2 gp[P];
+        lobe_step<FRAME, true, true>(pv, dv, gcv, a.identity != 0, a.normalised != 0, a.exact != 0, rgbv, gdv, gp);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          rgb[c] = rgbv[c].v.x + (second ? rgbv[c].v.y : 0.f);
+          gd[c] = gdv[c].v.x + (second ? gdv[c].v.y : 0.f);
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) gslot[p * 256] = gp[p].v;
+      }
+    }
+  }
+  float c0e[3];  // diffuse colour as evaluated (the BF16 value when quantising)
+#pragma unroll
+  for (int c = 0; c < 3; ++c) c0e[c] = quant ? bf16_rne(cur.c0[c]) : cur.c0[c];
+  if (LOSS) {
+    // the primitive's colour in every lane of the slice, then the residual
+    for (int o = a.slice >> 1; o >= 1; o >>= 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) rgb[c] += __shfl_xor_sync(0xffffffffu, rgb[c], o);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gc[c] = gscale * ((rgb[c] + c0e[c]) - gc[c]);
+    if (mine) {
+      const P2 gcv[3] = {p2(gc[0]), p2(gc[1]), p2(gc[2])};
       P2 gdv[3] = {p2(0.f), p2(0.f), p2(0.f)};
       P2 gp[P];
-      lobe_step<FRAME, true, true>(pv, dv, gcv, a.identity != 0, a.normalised != 0, a.exact != 0, rgbv, gdv, gp);
+      lobe_grad<FRAME>(ev, dv, gcv, gdv, gp);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        rgb[c] = rgbv[c].v.x + (second ? rgbv[c].v.y : 0.f);
-        gd[c] = gdv[c].v.x + (second ? gdv[c].v.y : 0.f);
-      }
+      for (int c = 0; c < 3; ++c) gd[c] = gdv[c].v.x + (second ? gdv[c].v.y : 0.f);
 #pragma unroll
       for (int p = 0; p < P; ++p) gslot[p * 256] = gp[p].v;
     }
-  }
-  for (int o = a.slice >> 1; o >= 1; o >>= 1) {
+    for (int o = a.slice >> 1; o >= 1; o >>= 1) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      rgb[c] += __shfl_xor_sync(0xffffffffu, rgb[c], o);
-      gd[c] += __shfl_xor_sync(0xffffffffu, gd[c], o);
+      for (int c = 0; c < 3; ++c) gd[c] += __shfl_xor_sync(0xffffffffu, gd[c], o);
+    }
+  } else {
+    for (int o = a.slice >> 1; o >= 1; o >>= 1) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        rgb[c] += __shfl_xor_sync(0xffffffffu, rgb[c], o);
+        gd[c] += __shfl_xor_sync(0xffffffffu, gd[c], o);
+      }
     }
   }
   if (ok) {
     const float dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
     for (int c = l0 >> 1; c < 3; c += a.slice) {
       float th = pick3(cur.c0, c);
-      if (a.rgb) a.rgb[3 * i + c] = pick3(rgb, c) + (quant ? bf16_rne(th) : th);
+      if (a.rgb) a.rgb[3 * i + c] = pick3(rgb, c) + pick3(c0e, c);
       if (a.g_means) a.g_means[3 * i + c] = (pick3(gd, c) - dot * pick3(d, c)) * inv_dist;
       const IDX o = IDX(c) * n + i;
       float mm = s.c0m[o], vv = s.c0v[o];
-      adam(s, pick3(cur.gc, c), th, mm, vv);
+      adam(s, pick3(gc, c), th, mm, vv);
       float* c0master = static_cast<float*>(const_cast<void*>(a.c0));
       c0master[o] = th;
       s.c0m[o] = mm;
@@ -200,7 +248,7 @@ __device__ __forceinline__ void step_phase2(const StepArgs& s, IDX i, int l0, co
 template <int P, bool EVEN>
 constexpr size_t step_smem_bytes() { return size_t(EVEN ? 4 : 1) * P * 256 * sizeof(float2); }
 
-template <int FRAME, typename IDX, bool EVEN>
+template <int FRAME, typename IDX, bool EVEN, bool LOSS>
 __global__ void __launch_bounds__(256, 2) step_kernel(const StepArgs s) {
   constexpr int P = FrameTraits<FRAME>::P;
   extern __shared__ __align__(16) float2 step_smem[];
@@ -213,6 +261,7 @@ __global__ void __launch_bounds__(256, 2) step_kernel(const StepArgs s) {
   const int l0 = 2 * (threadIdx.x & (a.slice - 1));
   const IDX total = IDX(items) << a.slice_log2;
   const IDX stride = IDX(gridDim.x) * blockDim.x;
+  const float gscale = LOSS && items > 0 ? 2.f / (3.f * float(items)) : 0.f;  // d mean / d colour
   float2* gslot = step_smem + threadIdx.x;
   float2* tslot = gslot + P * 256;
   float2* mslot = tslot + P * 256;
@@ -234,23 +283,18 @@ __global__ void __launch_bounds__(256, 2) step_kernel(const StepArgs s) {
         cp_async8(vslot + p * 256, s.v + off);
       }
     }
-    const bool mine = step_phase1<FRAME, IDX, EVEN>(s, cur, i, l0, gslot);
+    const bool mine = step_phase1<FRAME, IDX, EVEN, LOSS>(s, cur, i, l0, gscale, gslot);
     if (EVEN) cp_async_wait_all();
     if (mine) step_phase2<P, IDX, EVEN>(s, i, l0, gslot, tslot, mslot, vslot);
   }
 }
 
-template <int FRAME, typename IDX, bool EVEN>
+template <int FRAME, typename IDX, bool EVEN, bool LOSS>
 static nasg_status launch_step_k(const StepArgs& s, cudaStream_t st) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr size_t smem = step_smem_bytes<P, EVEN>();
-  auto k = step_kernel<FRAME, IDX, EVEN>;
-  static bool configured = false;  // per instantiation
-  if (!configured) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
-      return check_launch();
-    configured = true;
-  }
+  auto k = step_kernel<FRAME, IDX, EVEN, LOSS>;
+  if (const nasg_status e = ensure_smem_limit(reinterpret_cast<const void*>(k), smem); e != NASG_OK) return e;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
   const int64_t threads = s.e.n_items << s.e.slice_log2;
@@ -261,8 +305,9 @@ static nasg_status launch_step_k(const StepArgs& s, cudaStream_t st) {
 }
 
 template <int FRAME, typename IDX>
-static nasg_status launch_step_idx(const StepArgs& s, bool even, cudaStream_t st) {
-  return even ? launch_step_k<FRAME, IDX, true>(s, st) : launch_step_k<FRAME, IDX, false>(s, st);
+static nasg_status launch_step_idx(const StepArgs& s, bool even, bool loss, cudaStream_t st) {
+  if (loss) return even ? launch_step_k<FRAME, IDX, true, true>(s, st) : launch_step_k<FRAME, IDX, false, true>(s, st);
+  return even ? launch_step_k<FRAME, IDX, true, false>(s, st) : launch_step_k<FRAME, IDX, false, false>(s, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -406,12 +451,13 @@ extern "C" nasg_status nasg_frustum_compact(int64_t n, const float* means, const
 
 extern "C" nasg_status nasgabor_fused_step(const nasg_desc* desc, const nasg_train_state* st, const float* means,
                                            const float* cam, const int32_t* idx, int64_t n_idx,
-                                           const int32_t* n_idx_device, const float* g_rgb,
+                                           const int32_t* n_idx_device, const float* g_rgb, int32_t loss_mode,
                                            const nasg_adam_hparams* hp, float* rgb, float* g_means, void* stream) {
   nasg_status e = check_desc(desc);
   if (e != NASG_OK) return e;
   if (desc->lobe_family != NASG_FAMILY_NASGABOR) return NASG_ERR_UNSUPPORTED;
   if (desc->accumulate != 0) return NASG_ERR_RANGE;
+  if (loss_mode != NASG_LOSS_GIVEN && loss_mode != NASG_LOSS_MSE) return NASG_ERR_RANGE;
   if (!st || !hp || !cam) return NASG_ERR_NULL;
   if (idx && n_idx < 0) return NASG_ERR_RANGE;
   if (hp->step < 1 || !(hp->lr >= 0.f) || !(hp->beta1 >= 0.f && hp->beta1 < 1.f) ||
@@ -472,12 +518,71 @@ extern "C" nasg_status nasgabor_fused_step(const nasg_desc* desc, const nasg_tra
   const bool idx32 = NL * nasg_lobe_planes(desc->frame_mode) < lim && 3 * desc->n < lim &&
                      2 * (a.n_items << a.slice_log2) + (int64_t(1) << 24) < lim;
   cudaStream_t cs = as_stream(stream);
+  const bool loss = loss_mode == NASG_LOSS_MSE;
   if (desc->frame_mode == NASG_FRAME_QUAT) {
-    return idx32 ? launch_step_idx<NASG_FRAME_QUAT, uint32_t>(s, even, cs)
-                 : launch_step_idx<NASG_FRAME_QUAT, uint64_t>(s, even, cs);
+    return idx32 ? launch_step_idx<NASG_FRAME_QUAT, uint32_t>(s, even, loss, cs)
+                 : launch_step_idx<NASG_FRAME_QUAT, uint64_t>(s, even, loss, cs);
   }
-  return idx32 ? launch_step_idx<NASG_FRAME_COS, uint32_t>(s, even, cs)
-               : launch_step_idx<NASG_FRAME_COS, uint64_t>(s, even, cs);
+  return idx32 ? launch_step_idx<NASG_FRAME_COS, uint32_t>(s, even, loss, cs)
+               : launch_step_idx<NASG_FRAME_COS, uint64_t>(s, even, loss, cs);
+}
+
+// ---------------------------------------------------------------------------
+// BF16 copies of a training state
+// ---------------------------------------------------------------------------
+namespace nasg {
+
+// dst[j] = RNE_bf16(src[j]), eight elements per thread where both arrays allow
+// 16-byte (src) and 16-byte (dst, eight bf16) accesses, single elements otherwise.
+__global__ void __launch_bounds__(256) round_bf16_kernel(const float* __restrict__ src, uint16_t* __restrict__ dst,
+                                                         int64_t n, int vec) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (vec) {
+    const int64_t n8 = n / 8;
+    for (; j < n8; j += stride) {
+      const float4 a = reinterpret_cast<const float4*>(src)[2 * j];
+      const float4 b = reinterpret_cast<const float4*>(src)[2 * j + 1];
+      uint4 w;
+      w.x = uint32_t(bf16_bits(a.x)) | (uint32_t(bf16_bits(a.y)) << 16);
+      w.y = uint32_t(bf16_bits(a.z)) | (uint32_t(bf16_bits(a.w)) << 16);
+      w.z = uint32_t(bf16_bits(b.x)) | (uint32_t(bf16_bits(b.y)) << 16);
+      w.w = uint32_t(bf16_bits(b.z)) | (uint32_t(bf16_bits(b.w)) << 16);
+      reinterpret_cast<uint4*>(dst)[j] = w;
+    }
+    j = n8 * 8 + (int64_t(blockIdx.x) * blockDim.x + threadIdx.x);
+  }
+  for (; j < n; j += stride) dst[j] = bf16_bits(src[j]);
+}
+
+static nasg_status round_bf16(const float* src, void* dst, int64_t n, cudaStream_t s) {
+  if (n == 0 || !dst) return NASG_OK;
+  const int vec = aligned(src, 16) && aligned(dst, 16);
+  const int64_t work = vec ? n / 8 + 1 : n;
+  const unsigned grid = grid_for(work, 256);
+  const unsigned cap = unsigned(sm_count()) * 8u;
+  round_bf16_kernel<<<grid < cap ? grid : cap, 256, 0, s>>>(src, static_cast<uint16_t*>(dst), n, vec);
+  return check_launch();
+}
+
+}  // namespace nasg
+
+extern "C" nasg_status nasg_train_state_refresh_bf16(const nasg_desc* desc, const nasg_train_state* st,
+                                                     void* stream) {
+  nasg_status e = check_desc(desc);
+  if (e != NASG_OK) return e;
+  if (!st) return NASG_ERR_NULL;
+  const int P = nasg_param_planes(desc->frame_mode, desc->lobe_family);
+  if (P < 0) return NASG_ERR_UNSUPPORTED;
+  if (desc->n == 0) return NASG_OK;
+  if ((st->params_bf16 && !st->master) || (st->c0_bf16 && !st->c0_master)) return NASG_ERR_NULL;
+  if ((st->master && !aligned(st->master, 4)) || (st->c0_master && !aligned(st->c0_master, 4)) ||
+      (st->params_bf16 && !aligned(st->params_bf16, 2)) || (st->c0_bf16 && !aligned(st->c0_bf16, 2)))
+    return NASG_ERR_ALIGN;
+  cudaStream_t s = as_stream(stream);
+  e = round_bf16(st->master, st->params_bf16, int64_t(P) * desc->n * desc->n_lobes, s);
+  if (e != NASG_OK) return e;
+  return round_bf16(st->c0_master, st->c0_bf16, 3 * desc->n, s);
 }
 
 // ---------------------------------------------------------------------------

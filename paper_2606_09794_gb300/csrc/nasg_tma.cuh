@@ -1,11 +1,14 @@
 // Bulk asynchronous copies (TMA, cp.async.bulk) into shared memory with
 // mbarrier completion, for sm_90 and later, written as inline PTX.
 //
-// Every wait is bounded: after kWaitLimit unsuccessful try_wait rounds the
-// waiter records NASG_DEVERR_WAIT_TIMEOUT in the library's device error word
-// (passed to kernels as a pointer, see device_error_word()) and gives up (the
-// caller then returns from the kernel). The error word is read, and cleared,
-// by nasg_device_status() on the host.
+// Every wait is bounded, in wall time and in rounds: a waiter whose first try_wait
+// fails reads the global nanosecond timer and gives up once kWaitNs (one second)
+// have passed (checked every 256 rounds) or after `limit` rounds, whichever comes
+// first. Each try_wait may suspend the thread for a hardware-chosen interval, so
+// the round count alone does not bound the time. On giving up it records
+// NASG_DEVERR_WAIT_TIMEOUT in the library's device error word (passed to kernels as
+// a pointer, see device_error_word()); the caller then returns from the kernel.
+// The error word is read, and cleared, by nasg_device_status() on the host.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -15,6 +18,7 @@ namespace nasg {
 
 constexpr int NASG_DEVERR_WAIT_TIMEOUT = 1;
 constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint64_t kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -70,15 +74,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// Waits for phase `parity` of `bar` to complete; false (and the device error
-// word set) if it did not complete within the limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
-                                          uint32_t limit = kWaitLimit) {
-  for (uint32_t it = 0; it < limit; ++it) {
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Slow path of mbar_wait: the phase was not complete at the first try.
+static __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, int* err, uint32_t limit) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0 && global_ns() - t0 > kWaitNs) break;
   }
   if (err) atomicExch(err, NASG_DEVERR_WAIT_TIMEOUT);
   return false;
+}
+
+// Waits for phase `parity` of `bar` to complete; false (and the device error
+// word set) if it did not complete within one second or `limit` rounds.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
+                                          uint32_t limit = kWaitLimit) {
+  if (mbar_try_wait(bar, parity)) return true;
+  return mbar_wait_slow(bar, parity, err, limit);
 }
 
 }  // namespace nasg

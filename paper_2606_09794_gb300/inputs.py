@@ -313,6 +313,16 @@ def batched_scene_sizes(n_scenes: int, seed: int, n_min: int = 50_000, n_max: in
 # Fitting workload: a K=4 FP32 teacher field and a K=16 student.
 # ---------------------------------------------------------------------------
 
+# Learning-rate schedule of the fitting workload (constants only; the factor itself is
+# the library's nasg_cosine_lr_factor and the oracle's schedule.cosine_factor): base
+# rate 1e-3, 200 steps, the cosine schedule starting at iteration 47 = 200 x 7k/30k, the
+# fraction of the optimisation after which the paper starts it (Supp. C). Step s (1-based)
+# is iteration s - 1.
+FIT_LR = 1e-3
+FIT_STEPS = 200
+FIT_SCHEDULE_START = 47
+
+
 def fit_directions(step: int, seed: int, n_dirs: int = 64) -> np.ndarray:
     """View directions uniform on S^2 for one fitting step, (n_dirs, 3) float32 (unit up to fp32 rounding)."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0xD1, step]))

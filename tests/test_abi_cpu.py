@@ -110,3 +110,30 @@ def test_status_strings_and_planes(so):
 def test_lobe_family_needs_quaternion_frames(so):
     fwd = _fwd(so)
     assert fwd(ctypes.byref(Desc(16, 4, 1, 0, 0, 0, 0, 2)), P, P, P, CAM, None, 0, P, None) == -4
+
+
+def test_fused_step_loss_mode_validation(so):
+    """nasgabor_fused_step takes the loss mode after the gradient/target pointer (ABI 4):
+    an unknown mode is rejected before any launch; with every list empty the two valid
+    modes return NASG_OK without touching the device."""
+    class Adam(ctypes.Structure):
+        _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                    ("eps", ctypes.c_float), ("step", ctypes.c_int32)]
+
+    f = so.nasgabor_fused_step
+    f.argtypes = [ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                  ctypes.POINTER(Adam), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int32
+    state = (ctypes.c_void_p * 8)(*([0x10000] * 8))
+    hp = Adam(1e-3, 0.9, 0.999, 1e-8, 1)
+    good = Desc(16, 8, 0, 1, 0, 0, 0)
+    assert so.nasg_abi_version() == 4
+    for mode in (-1, 2, 7):
+        assert f(ctypes.byref(good), state, P, CAM, None, 0, None, P, mode, ctypes.byref(hp), None, None,
+                 None) == NASG_ERR_RANGE
+    for mode in (0, 1):
+        assert f(ctypes.byref(good), state, P, CAM, P, 0, None, P, mode, ctypes.byref(hp), None, None,
+                 None) == NASG_OK
+        assert f(ctypes.byref(Desc(0, 8, 0, 1, 0, 0, 0)), state, P, CAM, None, 0, None, P, mode,
+                 ctypes.byref(hp), None, None, None) == NASG_OK

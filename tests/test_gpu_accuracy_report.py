@@ -2,9 +2,11 @@
 precision on the parity workload (N = 4096, L = 4) and on a sampled slice of the
 N = 1e6, L = 8 workload, through the fused forward+backward the benchmark times.
 Prints one JSON line per case (run with -s to see it) and checks the bounds:
-colours |dc| <= base + 4 nu (base 1e-5 FP32, 4e-3 BF16 against the dequantised
-values), gradients relative L2 <= 1e-4 per plane; the BF16 storage error
-(BF16 parameters against the FP32 master values, both in the oracle) is reported."""
+colours |dc| <= 1e-5 + 4 nu (FP32 parameters, and BF16 parameters against the
+dequantised values), gradients relative L2 <= 1e-4 per plane. The BF16 storage
+error (the oracle at the BF16 values against the oracle at the FP32 master
+values) is reported and held to its first-order bound (tests/test_bf16_storage.py):
+it is not within 4e-3 at these sharpnesses."""
 import json
 
 import numpy as np
@@ -13,6 +15,7 @@ import pytest
 from oracle import nasgabor as ong
 from paper_2606_09794_gb300 import inputs
 from tests._parity import colour_report, rel_l2, sensitivity_floor
+from tests.test_bf16_storage import storage_error_and_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +40,7 @@ def _case(lib, w, bf16, sample=None):
         return ong.forward(p_, c_, m_, cam_, L)
 
     ref, nu = sensitivity_floor(fwd, (pn, cn, mu, w.cam), (0, 1, 2, 3))
-    rep = colour_report(rgb.cpu().numpy()[idx], ref, nu, 4e-3 if bf16 else 1e-5)
+    rep = colour_report(rgb.cpu().numpy()[idx], ref, nu, 1e-5)
     r_p, _, r_mu = ong.backward(pn, cn, mu, w.cam, g_np, L)
     gpn = gp.cpu().numpy()[:, lobes]
     planes = [rel_l2(gpn[k], r_p[k]) for k in range(gpn.shape[0])]
@@ -45,10 +48,11 @@ def _case(lib, w, bf16, sample=None):
            "grad_rel_l2_max": max(planes), "grad_rel_l2_per_plane": [float(f"{x:.3g}") for x in planes],
            "g_means_rel_l2": rel_l2(gm.cpu().numpy()[idx], r_mu)}
     if bf16:
-        master = ong.forward(w.params[:, lobes], w.c0[:, idx], mu, w.cam, L)
-        q = np.abs(ref - master)
+        q, bound, master = storage_error_and_bound(w, idx)
         out["bf16_storage_error"] = {"max_abs": float(q.max()),
-                                     "max_rel1": float((q / np.maximum(1.0, np.abs(master))).max())}
+                                     "max_rel1": float((q / np.maximum(1.0, np.abs(master))).max()),
+                                     "max_over_first_order_bound": float((q / np.maximum(bound, 1e-300)).max())}
+        assert np.all(q <= 1.5 * bound + 1e-9)
     print(json.dumps(out))
     return out
 

@@ -124,7 +124,7 @@ def test_batched_oracle_parity(lib):
             return ong.forward(p, c, m, cm, L)
 
         ref, nu = sensitivity_floor(fwd, (pq, cq, w.means, cam), (0, 1, 2, 3))
-        rep = colour_report(sc["rgb"].cpu().numpy(), ref, nu, 4e-3)
+        rep = colour_report(sc["rgb"].cpu().numpy(), ref, nu, 1e-5)
         assert rep["violations"] == 0, rep
         r_p, _, r_mu = ong.backward(pq, cq, w.means, cam, w.g_rgb, L)
         gp = sc["g_params"].cpu().numpy()

@@ -123,6 +123,61 @@ def test_fused_step_updates_only_visible():
     np.testing.assert_allclose(out["rgb"], ng.forward(pq, c0q, w.means[idx], w.cam, L), rtol=1e-15)
 
 
+def test_fused_step_mse_gradient_matches_finite_differences():
+    """loss "mse": the gradient the step uses (m / (1 - b1) after a cold first step) is
+    the derivative of the mean over listed primitives and channels of the squared colour
+    error, by central differences of the oracle's forward at the BF16 values."""
+    n, L = 12, 3
+    w = inputs.point_cloud_workload(n, L, 41)
+    P = w.params.shape[0]
+    idx = np.array([1, 2, 5, 7, 11])
+    master = oad.bf16_round(w.params)          # on the BF16 grid, so FD moves it freely
+    target = np.random.default_rng(42).uniform(0, 2, (n, 3))
+    zeros = np.zeros((P, n * L))
+    out = oad.fused_step(master, zeros, zeros, w.c0, np.zeros((3, n)), np.zeros((3, n)), w.means, w.cam, target,
+                         idx, L, t=1, loss="mse")
+    g = out["m"] / 0.1
+    lobes = (idx[:, None] * L + np.arange(L)).reshape(-1)
+    c0q = oad.bf16_round(w.c0[:, idx])
+
+    def loss_at(p):
+        col = ng.forward(p[:, lobes], c0q, w.means[idx], w.cam, L)
+        return np.sum((col - target[idx]) ** 2) / (3 * len(idx))
+
+    assert abs(loss_at(master) - out["loss"]) <= 1e-15 * out["loss"]
+    rng = np.random.default_rng(43)
+    for p in range(P):
+        for j in rng.choice(lobes, 4, replace=False):
+            h = 1e-6 * max(1.0, abs(master[p, j]))
+            pp, pm = master.copy(), master.copy()
+            pp[p, j] += h
+            pm[p, j] -= h
+            fd = (loss_at(pp) - loss_at(pm)) / (2 * h)
+            tol = 1e-6 * abs(fd) + 64 * np.finfo(float).eps * out["loss"] / h + 1e-14
+            assert abs(g[p, j] - fd) <= tol, (p, j, g[p, j], fd)
+    # c0: d loss / d c0_ic = 2 (c_ic - t_ic) / (3 n_listed)
+    np.testing.assert_allclose(out["c0_m"][:, idx] / 0.1, (2.0 * (out["rgb"] - target[idx]) / (3 * len(idx))).T,
+                               rtol=1e-12)
+
+
+def test_fused_step_mse_at_own_colours_does_not_move():
+    """A target equal to the model's own colours gives a zero gradient: from a cold state
+    nothing moves (m = v = 0, and the update 0 / (0 + eps) is 0)."""
+    n, L = 32, 4
+    w = inputs.point_cloud_workload(n, L, 44)
+    P = w.params.shape[0]
+    idx = np.arange(0, n, 2)
+    zeros = np.zeros((P, n * L))
+    lobes = (idx[:, None] * L + np.arange(L)).reshape(-1)
+    own = np.zeros((n, 3))
+    own[idx] = ng.forward(oad.bf16_round(w.params[:, lobes]), oad.bf16_round(w.c0[:, idx]), w.means[idx], w.cam, L)
+    out = oad.fused_step(w.params, zeros, zeros, w.c0, np.zeros((3, n)), np.zeros((3, n)), w.means, w.cam, own,
+                         idx, L, t=1, loss="mse")
+    assert out["loss"] == 0.0
+    np.testing.assert_array_equal(out["master"], w.params.astype(np.float64))
+    np.testing.assert_array_equal(out["c0"], w.c0.astype(np.float64))
+
+
 def _bf16_exact(x):
     return oad.bf16_round(x)
 
