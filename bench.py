@@ -767,14 +767,66 @@ def measure_fit(nb, inputs, dev, stream, n=2_000_000, ls=16, lt=4, steps=200, n_
     l = losses.cpu().numpy()
     evals = n * n_dirs * (ls + lt) * steps
     sub = fit_subsample_check(nb, inputs, dev, stream) if n == 2_000_000 and steps == 200 else None
+    ceilings = pipe_ceilings(nb)
+    counts = profiled_fit_counts()
+    fractions = None
+    if counts is not None:
+        per_s = n * steps / (ms * 1e-3)          # (primitive, step) pairs per second
+        fractions = {"xu": counts["xu_per_prim_step"] * 32 * per_s / ceilings["mufu_ex2_per_s"],
+                     "fma": counts["fma_per_prim_step"] * 32 * per_s / ceilings["fma_instr_per_s"],
+                     "issue_note": "pipe instructions per (primitive, step) from the committed ncu summary "
+                                   "(profiles/nasgabor_fit_step_500k_ls16_lt4.md), lane rates over the probe's "
+                                   "measured issue rates"}
     return {"workload": f"fit N={n}, student L={ls} BF16 (FP32 master), teacher L={lt} FP32, {n_dirs} directions/step, "
                         f"{steps} Adam steps, base lr 1e-3 with the cosine schedule from iteration "
                         f"{round(inputs.FIT_SCHEDULE_START * steps / inputs.FIT_STEPS)}",
             "ms_total": ms, "ms_per_step": ms / steps,
             "loss_first": float(l[0]), "loss_last": float(l[-1]),
             "lobe_evaluations_per_s": evals / (ms * 1e-3), "subsample_final_mse": sub,
+            "pipe_ceilings": ceilings, "pipe_fractions": fractions,
             "note": "compute-bound; subsample_final_mse: the same fit on the workload's seeded 20k subsample "
                     "against the stored FP64 oracle fit (BF16 storage emulated; oracle_fp64_storage without it)"}
+
+
+def pipe_ceilings(nb):
+    """Issue rates measured by the library's pipe microbenchmark on this GPU: MUFU ex2
+    results per second, FP32 FMA lane-instructions per second (scalar, and packed FP32x2
+    counted as one instruction per lane pair)."""
+    mufu = nb.nasg_pipe_rate(0)
+    ffma2_ops = nb.nasg_pipe_rate(1)
+    ffma = nb.nasg_pipe_rate(2)
+    return {"mufu_ex2_per_s": mufu, "ffma_scalar_per_s": ffma, "ffma2_flops_pairs_per_s": ffma2_ops,
+            "fma_instr_per_s": max(ffma, ffma2_ops / 2)}
+
+
+def profiled_fit_counts():
+    """Per (primitive, step) warp-level pipe instruction counts of the fitting kernel from
+    the committed ncu summary, or None when the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "nasgabor_fit_step_500k_ls16_lt4.md")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if line.startswith("- ") and ":" in line:
+                    k, v = line[2:].split(":", 1)
+                    kv[k.strip()] = v.strip().strip("`")
+        if kv.get("source_sha256_16") != fit_source_hash():
+            return None
+        return {"xu_per_prim_step": float(kv["xu_warp_inst_per_prim_step"]),
+                "fma_per_prim_step": float(kv["fma_warp_inst_per_prim_step"])}
+    except Exception:
+        return None
+
+
+def fit_source_hash():
+    """Hash of the sources the fitting kernel is compiled from (csrc/nasg_*.cuh, nasg_*.h, nasg_fit.cu)."""
+    csrc = os.path.join(ROOT, "paper_2606_09794_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if (f.startswith("nasg_") and (f.endswith(".cuh") or f.endswith(".h"))) or f == "nasg_fit.cu":
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
 
 
 def fit_subsample_check(nb, inputs, dev, stream):

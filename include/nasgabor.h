@@ -423,6 +423,22 @@ nasg_status sh_eval_bwd(int32_t degree, int64_t n, const float* coeffs, const fl
  */
 nasg_status nasg_math_probe(int32_t fn, const float* x, float* y, float* y2, int64_t n, void* stream);
 
+/*
+ * Diagnostic microbenchmark: launches SMs x blocks_per_sm blocks of 256 threads,
+ * each thread running `iters` rounds of eight independent dependency chains of one
+ * instruction kind, so that the kernel's duration (timed by the caller on
+ * `stream`) gives the device's issue rate for it. The paper has no counterpart;
+ * it measures the ceilings the arithmetic-bound kernels are graded against.
+ *   pipe 0: ex2.approx.ftz.f32 (the multi-function unit: exponentials, reciprocals);
+ *   pipe 1: packed FP32x2 fused multiply-add (two FMAs per instruction);
+ *   pipe 2: scalar FP32 fused multiply-add.
+ * *ops (host) receives the number of lane operations the launch performs (a packed
+ * FMA counts two). out: device scratch of SMs x blocks_per_sm floats (written only
+ * in a case that does not occur). iters 1..2^24, blocks_per_sm 1..8.
+ */
+nasg_status nasg_pipe_probe(int32_t pipe, int64_t iters, int32_t blocks_per_sm, float* out, int64_t* ops,
+                            void* stream);
+
 /* ------------------------------------------------------------------------- */
 /* Host-resident data                                                         */
 /* ------------------------------------------------------------------------- */

@@ -111,6 +111,7 @@ _decl("nasg_lr_heuristic", [_vp, _i32, _i32, ctypes.c_double, ctypes.c_double, c
                            ctypes.c_double, _P(ctypes.c_double), _P(ctypes.c_double), _P(ctypes.c_double)])
 _decl("nasg_cosine_lr_factor", [_i64, _i64, _i64], ctypes.c_double)
 _decl("nasg_train_state_refresh_bf16", [_P(NasgDesc), _P(NasgTrainState), _vp])
+_decl("nasg_pipe_probe", [_i32, _i64, _i32, _vp, _P(_i64), _vp])
 _decl("nasg_frustum_compact", [_i64, _vp, _P(ctypes.c_float), _P(ctypes.c_float), ctypes.c_float, ctypes.c_float,
                                _vp, _vp, _vp, ctypes.c_size_t, _vp])
 
@@ -331,6 +332,25 @@ def sh_eval_bwd(coeffs, means, cam, g_rgb, degree=3, g_coeffs=None, g_means=None
     _check(lib.sh_eval_bwd(degree, n, _ptr(coeffs), _ptr(means), _cam(cam), _ptr(g_rgb), _ptr(g_coeffs),
                            _ptr(g_means), _stream(stream)), "sh_eval_bwd")
     return g_coeffs, g_means
+
+
+def nasg_pipe_rate(pipe, iters=1 << 14, blocks_per_sm=4, reps=3, stream=None):
+    """Diagnostic: measured issue rate (lane operations per second) of one pipe
+    (0 MUFU ex2, 1 packed FP32x2 FMA, 2 scalar FMA); best of `reps` timed launches."""
+    s = torch.cuda.current_stream() if stream is None else stream
+    out = torch.empty(4096, device="cuda", dtype=torch.float32)
+    ops = _i64(0)
+    best = None
+    for _ in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        _check(lib.nasg_pipe_probe(int(pipe), int(iters), int(blocks_per_sm), _ptr(out), ctypes.byref(ops),
+                                   _vp(s.cuda_stream)), "nasg_pipe_probe")
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return ops.value / (best * 1e-3)
 
 
 def nasg_math_probe(fn, x, stream=None):

@@ -177,3 +177,53 @@ extern "C" nasg_status nasg_probe_wait_timeout(int32_t limit, void* stream) {
   nasg::wait_timeout_probe_kernel<<<1, 32, 0, nasg::as_stream(stream)>>>(err, uint32_t(limit));
   return nasg::check_launch();
 }
+
+// ---------------------------------------------------------------------------
+// Diagnostic: issue rate of one arithmetic pipe (microbenchmark)
+// ---------------------------------------------------------------------------
+namespace nasg {
+constexpr int kProbeChains = 8;  // independent dependency chains per thread (latency hidden)
+
+__global__ void __launch_bounds__(256) pipe_probe_kernel(int pipe, int64_t iters, float seed, float* out) {
+  float acc[kProbeChains];
+  float2 acc2[kProbeChains];
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) {
+    acc[c] = seed * float(threadIdx.x + c + 1) * 1e-6f;
+    acc2[c] = make_float2(acc[c], -acc[c]);
+  }
+  if (pipe == 0) {  // MUFU: ex2.approx, each result feeding its chain's next argument
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int c = 0; c < kProbeChains; ++c) acc[c] = ex2a(acc[c]) - 1.5f;
+    }
+  } else if (pipe == 1) {  // packed FP32x2 fused multiply-add
+    const float2 m = make_float2(0.999f, 0.999f), b = make_float2(1e-3f, 1e-3f);
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int c = 0; c < kProbeChains; ++c) acc2[c] = __ffma2_rn(acc2[c], m, b);
+    }
+  } else {  // scalar FP32 fused multiply-add
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+      for (int c = 0; c < kProbeChains; ++c) acc[c] = fmaf(acc[c], 0.999f, 1e-3f);
+    }
+  }
+  float r = 0.f;
+#pragma unroll
+  for (int c = 0; c < kProbeChains; ++c) r += acc[c] + acc2[c].x + acc2[c].y;
+  if (r == 12345.678f) out[blockIdx.x] = r;  // keeps the chains live; never true in practice
+}
+}  // namespace nasg
+
+extern "C" nasg_status nasg_pipe_probe(int32_t pipe, int64_t iters, int32_t blocks_per_sm, float* out,
+                                       int64_t* ops, void* stream) {
+  if (pipe < 0 || pipe > 2 || iters < 1 || iters > (int64_t(1) << 24) || blocks_per_sm < 1 || blocks_per_sm > 8)
+    return NASG_ERR_RANGE;
+  if (!out || !ops) return NASG_ERR_NULL;
+  const int64_t blocks = int64_t(nasg::sm_count()) * blocks_per_sm;
+  nasg::pipe_probe_kernel<<<unsigned(blocks), 256, 0, nasg::as_stream(stream)>>>(pipe, iters, 0.5f, out);
+  // one op = one instruction's lane result: a packed FFMA2 counts as two FMAs
+  *ops = blocks * 256 * iters * nasg::kProbeChains * (pipe == 1 ? 2 : 1);
+  return nasg::check_launch();
+}

@@ -89,13 +89,29 @@ __device__ __forceinline__ void fetch_scene_item(const EvalArgs& sc, int64_t pri
 
 // The item arithmetic of the single-scene kernels. PAIRS: every scene of the batch
 // has even L, pair-aligned planes and 32-bit offsets (pair loads and stores, 32-bit
-// index arithmetic); else the general form (any L, 64-bit offsets).
+// index arithmetic); else the general form (any L, 64-bit offsets). With the default
+// modes and pairs, L = 4, 8 and 16 run the arithmetic with the lobe count fixed at
+// compile time (slice width and reduction bounds constants), as the single-scene
+// kernel does; the scene table is ordered by lobe count, so a block's consecutive
+// units (and the units all blocks work on at one time) mostly share one instance.
 template <int FRAME, typename T, int FLAGS, bool PAIRS>
 __device__ __forceinline__ void eval_scene_item(const EvalArgs& a, const RawItem<T, FrameTraits<FRAME>::P>& r,
                                                 int64_t prim, int l0) {
+  if constexpr (PAIRS && FLAGS == kFlagsDefault) {
+    switch (a.n_lobes) {  // block-uniform
+      case 4: eval_item<FRAME, T, uint32_t, kFwdBwd, true, FLAGS, 4>(a, r, uint32_t(prim), l0); return;
+      case 8: eval_item<FRAME, T, uint32_t, kFwdBwd, true, FLAGS, 8>(a, r, uint32_t(prim), l0); return;
+      case 16: eval_item<FRAME, T, uint32_t, kFwdBwd, true, FLAGS, 16>(a, r, uint32_t(prim), l0); return;
+      default: break;
+    }
+  }
   if (PAIRS) eval_item<FRAME, T, uint32_t, kFwdBwd, true, FLAGS>(a, r, uint32_t(prim), l0);
   else eval_item<FRAME, T, int64_t, kFwdBwd, false, FLAGS>(a, r, prim, l0);
 }
+
+// Order of the scenes in the device table: by lobe-count class (4, 8, 16, others),
+// then as given (the table is internal; each record holds its scene's own buffers).
+inline int lobe_class(int32_t L) { return L == 4 ? 0 : (L == 8 ? 1 : (L == 16 ? 2 : 3)); }
 
 // FLAGS: kFlagsDefault (raw activations, approximate normalisation) or
 // kFlagsRuntime (modes read from the arguments).
@@ -411,10 +427,15 @@ extern "C" nasg_status nasgabor_batched_prepare(const nasg_scene* scenes, int32_
   if (modes->act_mode != NASG_ACT_RAW && modes->act_mode != NASG_ACT_IDENTITY) return NASG_ERR_RANGE;
   const int es = elem_size(modes->param_dtype);
   std::vector<SceneDev> tab(n_scenes, SceneDev{});
+  std::vector<int> order(n_scenes);
+  for (int j = 0; j < n_scenes; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return lobe_class(scenes[x].n_lobes) < lobe_class(scenes[y].n_lobes);
+  });
   int64_t tiles = 0, prims = 0, lobes = 0;
   bool pair_path = true;
   for (int j = 0; j < n_scenes; ++j) {
-    const nasg_scene& s = scenes[j];
+    const nasg_scene& s = scenes[order[j]];
     if (s.n < 0 || s.n > (int64_t(1) << 40) || s.n_lobes < 1 || s.n_lobes > NASG_MAX_LOBES) return NASG_ERR_RANGE;
     if (s.n > 0 && (!s.params || !s.c0 || !s.means || !s.g_rgb || !s.rgb || !s.g_params || !s.g_c0))
       return NASG_ERR_NULL;

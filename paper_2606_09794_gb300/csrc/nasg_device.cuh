@@ -292,9 +292,12 @@ __device__ __forceinline__ void cos_frame_grad(const CosFrame<V>& f, const V* gx
 // The lobe and its partial derivatives
 // ---------------------------------------------------------------------------
 
+// G_lam and G_a are the derivatives with respect to the stored scalars: dG/dlam and
+// dG/da, or (logscale: raw activations, lam = e^{lam_r}, a = e^{a_r}) dG/dlam_r =
+// lam dG/dlam and dG/da_r = a dG/da, which need no reciprocal of lam or 1 + a.
 template <class V>
 struct LobePartials {
-  V G_u, G_v, G_lam, G_a, G_k;  // dG/du, dG/dv, dG/dlam, dG/da, dG/dk
+  V G_u, G_v, G_lam, G_a, G_k;  // dG/du, dG/dv, dG/d(lam | lam_r), dG/d(a | a_r), dG/dk
   V G_phi;                      // dG/dphi (phase family)
   V u, v;                       // d.z and d.x
 };
@@ -332,7 +335,13 @@ struct LobePartials {
 // for |sig| <= 1 and Lam <= 1, from S(Lam^2) c e^{-Lam} = 1 (the k = 0 integral),
 //   1 - Psi = c e^{-Lam} (S(Lam^2) - S(sig)) = c e^{-Lam} k^2 sum_n D_n/(2n+1)!,
 //   D_1 = 1, D_{n+1} = Lam^2 D_n + sig^n (the difference quotient of x^n);
-// elsewhere Psi < 0.9 and 1 - Psi has no cancellation.
+// elsewhere Psi < 0.9 and 1 - Psi has no cancellation. Where R is that large its
+// derivative needs dPsi/dLam to full relative accuracy too (it is O(k^2) while its
+// usual form is a difference of O(Lam) terms), so the phase path forms it as
+//   sig > 1:  d ln Psi/dLam = -k^2/(Lam s^2) + (delta/s) coth s + sinh delta/(sinh s sinh Lam),
+//             the last term 2 e^{-2s} (1 - e^{-2 delta}) / ((1 - e^{-2s})(1 - e^{-2 Lam}));
+//   |sig| <= 1, Lam <= 1, from Psi = S(sig)/S(Lam^2):
+//             dPsi/dLam = (2 Lam / S(Lam^2)) (-k^2 sum_m (m+1) D_m/(2m+3)! + (1 - Psi) S'(Lam^2)).
 template <bool GRAD, bool PHASE = false>
 __device__ __forceinline__ void exact_norm1(float lam, float a, float k, float& r, float& dl, float& da,
                                             float& dk, float phi = 0.f, float* dphi = nullptr) {
@@ -347,20 +356,32 @@ __device__ __forceinline__ void exact_norm1(float lam, float a, float k, float& 
   float s = 0.f, A = 0.f, B = 0.f, rs2 = 0.f;
   float omp = 0.f;        // 1 - Psi where it needs its own expression (PHASE)
   bool have_omp = false;
+  float dpsi_acc = 0.f;   // dPsi/dLam in full relative accuracy (PHASE, same branches)
   if (fabsf(sig) <= 1.f) {
     const float el = vexp(-L);
     if (PHASE && L <= 1.f) {
       const float L2 = L * L;
-      const float inv_fact[5] = {1.f / 6.f, 1.f / 120.f, 1.f / 5040.f, 1.f / 362880.f, 1.f / 39916800.f};
-      float dn = 1.f, pw = sig, acc = 0.f;
+      // 1/(2n+1)! for n = 1..6
+      const float inv_fact[6] = {1.f / 6.f, 1.f / 120.f, 1.f / 5040.f, 1.f / 362880.f, 1.f / 39916800.f,
+                                 1.f / 6227020800.f};
+      float dn = 1.f, pw = sig, acc = 0.f, acc2 = 0.f;
 #pragma unroll
       for (int j = 0; j < 5; ++j) {
         acc = fmaf(dn, inv_fact[j], acc);
+        acc2 = fmaf(float(j + 2) * dn, inv_fact[j + 1], acc2);
         dn = fmaf(L2, dn, pw);
         pw *= sig;
       }
-      omp = c * el * (k * k) * acc;
+      const float ce = c * el;  // = 1/S(Lam^2)
+      omp = ce * (k * k) * acc;
       have_omp = true;
+      // S'(Lam^2) by its series (the coefficients of Sp below)
+      float spx = fmaf(L2, 1.f / 1037836800.f, 1.f / 7983360.f);
+      spx = fmaf(spx, L2, 1.f / 90720.f);
+      spx = fmaf(spx, L2, 1.f / 1680.f);
+      spx = fmaf(spx, L2, 1.f / 60.f);
+      spx = fmaf(spx, L2, 1.f / 6.f);
+      dpsi_acc = 2.f * L * ce * fmaf(omp, spx, -(k * k) * acc2);
     }
     float S = fmaf(sig, 1.f / 39916800.f, 1.f / 362880.f);
     S = fmaf(S, sig, 1.f / 5040.f);
@@ -389,6 +410,14 @@ __device__ __forceinline__ void exact_norm1(float lam, float a, float k, float& 
       const float q = delta * rs;
       omp = (-em - q * (1.f + em) + vexp(-2.f * L) * (q - em) * rcpa(1.f + em)) * rom;
       have_omp = true;
+      if (GRAD) {
+        const float e2s = vexp(-2.f * s);
+        const float roms = rcpa(-vexpm1n(-2.f * s));  // 1/(1 - e^{-2s})
+        const float t1 = -(k * k) * rcpa(L) * rs2;
+        const float t2 = q * (1.f + e2s) * roms;
+        const float t3 = -2.f * e2s * vexpm1n(-2.f * delta) * roms * rom;
+        dpsi_acc = (c * es) * (t1 + t2 + t3);
+      }
     }
   } else {
     const float rt = rsqa(-sig);
@@ -429,6 +458,7 @@ __device__ __forceinline__ void exact_norm1(float lam, float a, float k, float& 
       }
       dpsi_dl = fmaf(psi, lg, 2.f * L * c * esp);
     }
+    if (PHASE && have_omp) dpsi_dl = dpsi_acc;
     const float dpsi_dk = -2.f * k * c * esp;
     const float h = -0.5f * r * cph;
     dl = h * dpsi_dl * opa;
@@ -465,11 +495,12 @@ __device__ __forceinline__ void exact_norm_phase(P2 lam, P2 a, P2 k, P2 phi, P2&
 // direction with lobe_at; lobe_family does both for one direction.
 template <class V>
 struct LobeNorm {
-  V cinv, dlam, da, dk, dphi;  // C^-1 and d ln C^-1 / d(lam, a, k, phi)
+  V cinv, dlam, da, dk, dphi;  // C^-1 and d ln C^-1 / d(lam | lam_r, a | a_r, k, phi) (see LobePartials)
 };
 
 template <bool GRAD, int FAM, class V>
-__device__ __forceinline__ void lobe_norm(V lam, V a, V k, V phi, bool normalised, bool exact, LobeNorm<V>& nc) {
+__device__ __forceinline__ void lobe_norm(V lam, V a, V k, V phi, bool normalised, bool exact, bool logscale,
+                                          LobeNorm<V>& nc) {
   using F = Family<FAM>;
   nc.cinv = vconst<V>(1.f);
   nc.dlam = vconst<V>(0.f);
@@ -479,16 +510,24 @@ __device__ __forceinline__ void lobe_norm(V lam, V a, V k, V phi, bool normalise
   if (!normalised) return;
   const V em = vexpm1n(-2.f * lam);  // e^{-2 lam} - 1 (negative)
   const V r_em = vrcp(em);
+  V rs = vconst<V>(1.f);  // 1/sqrt(1 + a)
   if (F::HAS_A) {
     const V opa = 1.f + a;
-    nc.cinv = -((lam * (opa * vrsqrt(opa))) * (kInvTwoPi * r_em));
+    rs = vrsqrt(opa);
+    nc.cinv = -((lam * (opa * rs)) * (kInvTwoPi * r_em));
   } else {
     nc.cinv = -(lam * (kInvTwoPi * r_em));
   }
   if (GRAD) {
-    // d ln C^-1/d lam = 1/lam - 2 e^{-2 lam}/(1 - e^{-2 lam}); d ln C^-1/d a = 1/(2 (1+a))
-    nc.dlam = vfma(2.f * (1.f + em), r_em, vrcp(lam));
-    if (F::HAS_A) nc.da = 0.5f * vrcp(1.f + a);
+    // d ln C^-1/d lam = 1/lam - 2 e^{-2 lam}/(1 - e^{-2 lam}); d ln C^-1/d a = 1/(2 (1+a));
+    // logscale: lam d ln C^-1/d lam = 1 + 2 lam (1 + em)/em, a d ln C^-1/d a = a rs^2 / 2
+    if (logscale) {
+      nc.dlam = vfma(2.f * lam * (1.f + em), r_em, 1.f);
+      if (F::HAS_A) nc.da = 0.5f * a * (rs * rs);
+    } else {
+      nc.dlam = vfma(2.f * (1.f + em), r_em, vrcp(lam));
+      if (F::HAS_A) nc.da = 0.5f * (rs * rs);
+    }
   }
   // without a carrier the closed form is the NASG constant itself (Psi = 1)
   if (exact && F::HAS_PHASE) {
@@ -496,8 +535,8 @@ __device__ __forceinline__ void lobe_norm(V lam, V a, V k, V phi, bool normalise
     exact_norm_phase<GRAD>(lam, a, k, phi, r, dr_lam, dr_a, dr_k, dr_phi);
     nc.cinv = nc.cinv * r;
     if (GRAD) {
-      nc.dlam = nc.dlam + dr_lam;
-      nc.da = nc.da + dr_a;
+      nc.dlam = logscale ? vfma(lam, dr_lam, nc.dlam) : nc.dlam + dr_lam;
+      nc.da = logscale ? vfma(a, dr_a, nc.da) : nc.da + dr_a;
       nc.dk = dr_k;
       nc.dphi = dr_phi;
     }
@@ -506,8 +545,8 @@ __device__ __forceinline__ void lobe_norm(V lam, V a, V k, V phi, bool normalise
     exact_norm<GRAD>(lam, a, k, r, dr_lam, dr_a, dr_k);
     nc.cinv = nc.cinv * r;
     if (GRAD) {
-      nc.dlam = nc.dlam + dr_lam;
-      nc.da = nc.da + dr_a;
+      nc.dlam = logscale ? vfma(lam, dr_lam, nc.dlam) : nc.dlam + dr_lam;
+      nc.da = logscale ? vfma(a, dr_a, nc.da) : nc.da + dr_a;
       nc.dk = dr_k;
     }
   }
@@ -517,7 +556,7 @@ __device__ __forceinline__ void lobe_norm(V lam, V a, V k, V phi, bool normalise
 // phi ignored where the family has none; see Family).
 template <bool GRAD, int FAM, class V>
 __device__ __forceinline__ V lobe_at(const V* d, const V* x, const V* z, V lam, V a, V k, V phi,
-                                     const LobeNorm<V>& nc, bool exact, LobePartials<V>* pd) {
+                                     const LobeNorm<V>& nc, bool exact, bool logscale, LobePartials<V>* pd) {
   using F = Family<FAM>;
   using M = typename VecTraits<V>::Mask;
   const V u = vfma(d[0], z[0], vfma(d[1], z[1], d[2] * z[2]));
@@ -543,11 +582,20 @@ __device__ __forceinline__ V lobe_at(const V* d, const V* x, const V* z, V lam, 
   const V ln_k = F::HAS_A ? vsel(anti, 0.f, vlnkappa(t, vmax(kap, kFltMin))) : vconst<V>(0.f);  // ln kappa
   const V tau = F::HAS_A ? a * v * v * inv_s2 : vconst<V>(0.f);
   const V ln_e = tau * ln_k;                                      // ln E
-  const V em1 = F::HAS_A ? vexpm1n(ln_e + ln_k) : t;              // E kappa - 1
-  const V pe = F::HAS_A ? vexp(vfma(2.f * lam, em1, ln_e)) : vexp(2.f * lam * t);  // p E
+  // E kappa - 1 and E kappa, each to full relative accuracy (E kappa is tiny far from the
+  // lobe, where 2 lam E kappa / (1 + u) = lam E still enters dG/du)
+  V em1, ek;
+  if (F::HAS_A) {
+    vexp_expm1n(ln_e + ln_k, ek, em1);
+  } else {
+    em1 = t;    // kappa - 1
+    ek = kap;   // kappa
+  }
+  const V two_lam = 2.f * lam;
+  const V pe = F::HAS_A ? vexp(vfma(two_lam, em1, ln_e)) : vexp(two_lam * t);  // p E
   V h = vconst<V>(1.f), sin_kv = vconst<V>(0.f);  // (1 + cos(k v + phi))/2 and sin(k v + phi)
   if (F::HAS_PHASE) {
-    vcarrier(0.5f * vfma(k, v, phi), h, sin_kv);
+    vcarrier_sum(0.5f * phi, 0.5f * k * v, h, sin_kv);
   } else if (F::HAS_K) {
     vcarrier(0.5f * k * v, h, sin_kv);
   }
@@ -558,8 +606,7 @@ __device__ __forceinline__ V lobe_at(const V* d, const V* x, const V* z, V lam, 
   if (GRAD) {
     pd->u = u;
     pd->v = v;
-    const V ek = em1 + 1.f;                             // E kappa
-    const V two_lam_ek = 2.f * lam * ek;
+    const V two_lam_ek = two_lam * ek;
     const V dtau_du = 2.f * u * tau * inv_s2;
     const V dtau_dv = 2.f * a * v * inv_s2;
     const V dlne_du = vfma(ln_k, dtau_du, tau * inv_opu);
@@ -569,7 +616,8 @@ __device__ __forceinline__ V lobe_at(const V* d, const V* x, const V* z, V lam, 
       pd->G_u = G * vfma(two_lam_ek, dlne_du + inv_opu, dlne_du);
       const V gv_env = G * (two_lam_ek + 1.f) * dlne_dv;
       pd->G_v = F::HAS_K ? vfma(G * (two_lam_ek + 1.f), dlne_dv, -(cpe_sin * (0.5f * k))) : gv_env;
-      pd->G_a = G * vfma((two_lam_ek + 1.f) * ln_k, v * v * inv_s2, nc.da);
+      // d(tau)/da = v^2/(1-u^2); logscale: a d(tau)/da = tau
+      pd->G_a = G * vfma((two_lam_ek + 1.f) * ln_k, logscale ? tau : v * v * inv_s2, nc.da);
     } else {
       pd->G_u = G * lam;                                // d/du 2 lam (kappa - 1) = lam
       pd->G_v = vconst<V>(0.f);
@@ -582,7 +630,7 @@ __device__ __forceinline__ V lobe_at(const V* d, const V* x, const V* z, V lam, 
     }
     pd->G_phi = F::HAS_PHASE ? (exact ? vfma(G, nc.dphi, -(0.5f * cpe_sin)) : -(0.5f * cpe_sin))
                              : vconst<V>(0.f);
-    pd->G_lam = G * vfma(2.f, em1, nc.dlam);
+    pd->G_lam = G * vfma(logscale ? two_lam : vconst<V>(2.f), em1, nc.dlam);
   }
   return G;
 }
@@ -590,17 +638,17 @@ __device__ __forceinline__ V lobe_at(const V* d, const V* x, const V* z, V lam, 
 // One lobe of family FAM at one direction (normalisation included).
 template <bool GRAD, int FAM, class V>
 __device__ __forceinline__ V lobe_family(const V* d, const V* x, const V* z, V lam, V a, V k, V phi,
-                                         bool normalised, bool exact, LobePartials<V>* pd) {
+                                         bool normalised, bool exact, bool logscale, LobePartials<V>* pd) {
   LobeNorm<V> nc;
-  lobe_norm<GRAD, FAM>(lam, a, k, phi, normalised, exact, nc);
-  return lobe_at<GRAD, FAM>(d, x, z, lam, a, k, phi, nc, exact, pd);
+  lobe_norm<GRAD, FAM>(lam, a, k, phi, normalised, exact, logscale, nc);
+  return lobe_at<GRAD, FAM>(d, x, z, lam, a, k, phi, nc, exact, logscale, pd);
 }
 
 // The NASGabor lobe.
 template <bool GRAD, class V>
 __device__ __forceinline__ V lobe(const V* d, const V* x, const V* z, V lam, V a, V k, bool normalised, bool exact,
-                                  LobePartials<V>* pd) {
-  return lobe_family<GRAD, kFamNasGabor>(d, x, z, lam, a, k, vconst<V>(0.f), normalised, exact, pd);
+                                  bool logscale, LobePartials<V>* pd) {
+  return lobe_family<GRAD, kFamNasGabor>(d, x, z, lam, a, k, vconst<V>(0.f), normalised, exact, logscale, pd);
 }
 
 // ---------------------------------------------------------------------------
@@ -615,6 +663,25 @@ __device__ __forceinline__ float view_dir(const float* means, int64_t i, float c
   const float inv = rsqrtf(rx * rx + ry * ry + rz * rz);
   d[0] = rx * inv; d[1] = ry * inv; d[2] = rz * inv;
   return inv;
+}
+
+// The per-primitive scalar arithmetic of the kernels (view direction, dot products,
+// dLoss/dmu) with every operation explicitly rounded, so that no contraction choice is
+// left to the compiler and every kernel instance forms the same bits for the same inputs.
+__device__ __forceinline__ float view_dir_rn(const float mu[3], const float cam[3], float d[3]) {
+  const float rx = __fsub_rn(mu[0], cam[0]), ry = __fsub_rn(mu[1], cam[1]), rz = __fsub_rn(mu[2], cam[2]);
+  const float inv = rsqrtf(__fmaf_rn(rz, rz, __fmaf_rn(ry, ry, __fmul_rn(rx, rx))));
+  d[0] = __fmul_rn(rx, inv);
+  d[1] = __fmul_rn(ry, inv);
+  d[2] = __fmul_rn(rz, inv);
+  return inv;
+}
+__device__ __forceinline__ float dot3_rn(const float a[3], const float b[3]) {
+  return __fmaf_rn(a[2], b[2], __fmaf_rn(a[1], b[1], __fmul_rn(a[0], b[0])));
+}
+// component c of dLoss/dmu = (gd_c - (gd . d) d_c) / |mu - cam|
+__device__ __forceinline__ float mean_grad_rn(float gd_c, float dot, float d_c, float inv_dist) {
+  return __fmul_rn(__fmaf_rn(-dot, d_c, gd_c), inv_dist);
 }
 
 // dLoss/dmu = (I - d d^T) dLoss/dd / |mu - cam|

@@ -6,19 +6,22 @@
 //
 //   vexp(x)       2^(x log2 e) by ex2.approx (relative error ~2^-22 plus the
 //                 rounding of x log2 e, i.e. ~|x| 6e-8).
-//   vexpm1n(y)    e^y - 1 for y <= 0: Taylor polynomial to y^9 on [-0.5, 0]
-//                 (truncation < 3e-10 relative), 2^(y log2 e) - 1 below -0.5
+//   vexpm1n(y)    e^y - 1 for y <= 0: Taylor polynomial to y^8 on [-0.5, 0]
+//                 (truncation < 1.1e-8 relative), 2^(y log2 e) - 1 below -0.5
 //                 (|result| >= 0.39 there, so the subtraction loses nothing).
 //   vtanh(x)      odd Taylor series to x^9 for |x| < 1/4, else
 //                 (1 - e)/(1 + e) with e = e^{-2|x|}; 1 - tanh^2 x = 4 e/(1 + e)^2.
 //   vlnkappa(t)   ln(1 + t) for t in [-1, 0]: 2 atanh(t/(2 + t)) series to
-//                 s^9 where 1 + t >= 0.75, lg2.approx elsewhere.
+//                 s^7 where 1 + t >= 0.75 (|s| <= 1/7: truncation < 1.9e-8 relative),
+//                 lg2.approx elsewhere.
 //   vcarrier(x)   cos^2 x and sin 2x (the NASGabor carrier and its slope) for
 //                 |x| <= 6400; vsincos(x) gives sin x, cos x from the same
 //                 Cody-Waite reduction x = n pi/2 + r with pi/2 split in three
 //                 float parts (the first two with 12 significant bits, so n*C1
 //                 and n*C2 are exact) and the Taylor polynomials of sin (to r^9)
 //                 and cos (to r^10) on |r| <= pi/4 (truncation < 3e-9).
+//   vcarrier_sum(y, w)  cos^2(y + w) and sin 2(y + w) by angle addition (the
+//                 phase-shifted carrier, y = phi/2, w = k v/2).
 #pragma once
 
 #include "nasg_vec.cuh"
@@ -40,8 +43,7 @@ __device__ __forceinline__ V vexp(V x) {
 
 template <class V>
 __device__ __forceinline__ V taylor_expm1(V y) {
-  V p = vfma(y, kF9, kF8);
-  p = vfma(p, y, kF7);
+  V p = vfma(y, kF8, kF7);
   p = vfma(p, y, kF6);
   p = vfma(p, y, kF5);
   p = vfma(p, y, kF4);
@@ -54,6 +56,18 @@ __device__ __forceinline__ V taylor_expm1(V y) {
 template <class V>
 __device__ __forceinline__ V vexpm1n(V y) {
   return vsel(vgt(y, -0.5f), taylor_expm1(y), vex2(y * kLog2e) - 1.f);
+}
+
+// e^y and e^y - 1 for y <= 0, each to full relative accuracy: below -1/2 both from
+// 2^(y log2 e) (e^y - 1 <= -0.39 there), above from the Taylor polynomial (e^y >= 0.6).
+// (e^y recovered as (e^y - 1) + 1 would keep no digits where e^y is tiny.)
+template <class V>
+__device__ __forceinline__ void vexp_expm1n(V y, V& e, V& em1) {
+  const V ex = vex2(y * kLog2e);
+  const V tl = taylor_expm1(y);
+  const auto small = vgt(y, -0.5f);
+  em1 = vsel(small, tl, ex - 1.f);
+  e = vsel(small, tl + 1.f, ex);
 }
 
 template <class V>
@@ -78,8 +92,7 @@ template <class V>
 __device__ __forceinline__ V vlnkappa(V t, V kap) {
   const V s = t * vrcp(2.f + t);
   const V s2 = s * s;
-  V q = vfma(s2, 1.f / 9.f, 1.f / 7.f);
-  q = vfma(q, s2, 1.f / 5.f);
+  V q = vfma(s2, 1.f / 7.f, 1.f / 5.f);
   q = vfma(q, s2, 1.f / 3.f);
   q = vfma(q, s2, 1.f);
   const V ser = 2.f * s * q;
@@ -163,6 +176,26 @@ __device__ __forceinline__ void vsincos<float>(float x, float& s, float& c) {
   pc = fmaf(pc, r2, -kF2);
   pc = fmaf(pc, r2, 1.f);
   quadrant(n, ps, pc, s, c);
+}
+template <>
+__device__ __forceinline__ void vsincos<P2>(P2 x, P2& s, P2& c) {
+  vsincos<float>(x.v.x, s.v.x, c.v.x);
+  vsincos<float>(x.v.y, s.v.y, c.v.y);
+}
+
+// The phase-shifted carrier cos^2(y + w) and sin(2 (y + w)) for y = phi/2, w = k v/2,
+// by angle addition from the sines and cosines of y and w. Summing y + w first would
+// round w to the spacing of y (~1e-7 near pi/2), and near phi = pi, where cos(y + w)
+// is itself ~k v, that rounding is most of the carrier.
+template <class V>
+__device__ __forceinline__ void vcarrier_sum(V y, V w, V& h, V& s2x) {
+  V sy, cy, sw, cw;
+  vsincos<V>(y, sy, cy);
+  vsincos<V>(w, sw, cw);
+  const V cx = vfma(cy, cw, -(sy * sw));
+  const V sx = vfma(sy, cw, cy * sw);
+  h = cx * cx;
+  s2x = 2.f * sx * cx;
 }
 
 }  // namespace nasg

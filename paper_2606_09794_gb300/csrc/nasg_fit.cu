@@ -85,7 +85,7 @@ __device__ __forceinline__ void fit_lobes(const P2* raw, bool identity, bool nor
   f.lam = act.lam;
   f.a = act.a;
   f.k = act.k;
-  lobe_norm<GRAD, kFamNasGabor>(act.lam, act.a, act.k, p2(0.f), normalised, EXACT, f.nc);
+  lobe_norm<GRAD, kFamNasGabor>(act.lam, act.a, act.k, p2(0.f), normalised, EXACT, !identity, f.nc);
 }
 
 // A float2 load the compiler may not merge with an earlier load of the same address
@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
         const int j = min(base + tk, s.n_dirs - 1);
         const P2 d[3] = {p2(__ldg(s.dirs + 3 * j)), p2(__ldg(s.dirs + 3 * j + 1)), p2(__ldg(s.dirs + 3 * j + 2))};
         LobePartials<P2> pd;
-        const P2 Gt = lobe_at<false, kFamNasGabor>(d, tea.x, tea.z, tea.lam, tea.a, tea.k, zero, tea.nc, EXACT, &pd);
+        const P2 Gt = lobe_at<false, kFamNasGabor>(d, tea.x, tea.z, tea.lam, tea.a, tea.k, zero, tea.nc, EXACT,
+                                                   s.identity == 0, &pd);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const P2 wg = tea.w[c] * Gt;
@@ -188,7 +189,8 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
         const float dx = __ldg(s.dirs + 3 * j), dy = __ldg(s.dirs + 3 * j + 1), dz = __ldg(s.dirs + 3 * j + 2);
         const P2 d[3] = {p2(dx), p2(dy), p2(dz)};
         LobePartials<P2> pd;
-        const P2 Gs = lobe_at<true, kFamNasGabor>(d, stu.x, stu.z, stu.lam, stu.a, stu.k, zero, stu.nc, EXACT, &pd);
+        const P2 Gs = lobe_at<true, kFamNasGabor>(d, stu.x, stu.z, stu.lam, stu.a, stu.k, zero, stu.nc, EXACT,
+                                                  s.identity == 0, &pd);
         float col[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -240,8 +242,8 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
       quat_frame(raw, qf);
       P2 grad[10];
       quat_frame_grad(qf, acc_gx, acc_gz, grad);
-      grad[4] = acc_lam * act.s_lam;
-      grad[5] = acc_a * act.s_a;
+      grad[4] = acc_lam;  // the lobe partials are with respect to the stored scalars
+      grad[5] = acc_a;
       grad[6] = acc_k * act.s_k;
 #pragma unroll
       for (int c = 0; c < 3; ++c) grad[7 + c] = acc_w[c] * act.s_w[c];

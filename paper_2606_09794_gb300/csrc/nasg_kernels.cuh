@@ -101,10 +101,12 @@ __device__ __forceinline__ void lobe_eval(const V* pv, const V* d, bool identity
 #pragma unroll
     for (int c = 0; c < 3; ++c) { e.x[c] = e.cf.x[c]; e.z[c] = e.cf.z[c]; }
   }
+  // raw activations: the lam / a partials come out with respect to the stored log values
   if constexpr (TR::FAM == kFamNasGabor) {
-    e.G = lobe<BWD>(d, e.x, e.z, e.act.lam, e.act.a, e.act.k, normalised, exact, &e.pd);
+    e.G = lobe<BWD>(d, e.x, e.z, e.act.lam, e.act.a, e.act.k, normalised, exact, !identity, &e.pd);
   } else {
-    e.G = lobe_family<BWD, TR::FAM>(d, e.x, e.z, e.act.lam, e.act.a, e.act.k, e.act.phi, normalised, exact, &e.pd);
+    e.G = lobe_family<BWD, TR::FAM>(d, e.x, e.z, e.act.lam, e.act.a, e.act.k, e.act.phi, normalised, exact,
+                                    !identity, &e.pd);
   }
 }
 
@@ -118,8 +120,8 @@ __device__ __forceinline__ void lobe_grad(const LobeEval<FRAME, V>& e, const V* 
   const Act<V>& act = e.act;
   const LobePartials<V>& pd = e.pd;
   const V gG = vfma(gc[0], act.w[0], vfma(gc[1], act.w[1], gc[2] * act.w[2]));
-  gp[B] = gG * pd.G_lam * act.s_lam;
-  if constexpr (F::HAS_A) gp[TR::A] = gG * pd.G_a * act.s_a;
+  gp[B] = gG * pd.G_lam;  // the partials are already with respect to the stored scalars
+  if constexpr (F::HAS_A) gp[TR::A] = gG * pd.G_a;
   if constexpr (F::HAS_K) gp[TR::K] = gG * pd.G_k * act.s_k;
   if constexpr (F::HAS_PHASE) gp[TR::PH] = gG * pd.G_phi;
 #pragma unroll
@@ -291,9 +293,7 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
   float d[3] = {0.f, 0.f, 1.f};
   float inv_dist = 0.f;
   if (ok) {
-    const float rx = cur.mu[0] - a.cam[0], ry = cur.mu[1] - a.cam[1], rz = cur.mu[2] - a.cam[2];
-    inv_dist = rsqrtf(rx * rx + ry * ry + rz * rz);
-    d[0] = rx * inv_dist; d[1] = ry * inv_dist; d[2] = rz * inv_dist;
+    inv_dist = view_dir_rn(cur.mu, a.cam, d);
     if (IDX(l0) < L) {
       const bool second = EVEN || (IDX(l0) + 1 < L);
       P2 pv[P];
@@ -348,7 +348,7 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
     // group of four ends with channel c and lane 3 with the dot product: seven
     // shuffles in place of the twelve of an all-reduce of six values.
     const int lane = threadIdx.x & 31;
-    float v[7] = {rgb[0], gd[0], rgb[1], gd[1], rgb[2], gd[2], gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2]};
+    float v[7] = {rgb[0], gd[0], rgb[1], gd[1], rgb[2], gd[2], dot3_rn(gd, d)};
     for (int o = S() >> 1; o >= 4; o >>= 1) {
 #pragma unroll
       for (int k = 0; k < 7; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
@@ -368,7 +368,7 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
       a.rgb[3 * i + c] = e0 + pick3(cur.c0, c);
       store1(a.g_c0 + c * n + i, pick3(cur.gc, c), acc);
       // dLoss/dmu = (I - d d^T) dLoss/dd / |mu - cam|
-      if (a.g_means) store1(a.g_means + 3 * i + c, (e1 - dot * pick3(d, c)) * inv_dist, acc);
+      if (a.g_means) store1(a.g_means + 3 * i + c, mean_grad_rn(e1, dot, pick3(d, c), inv_dist), acc);
     }
     return;
   }
@@ -381,13 +381,13 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
     }
   }
   if (ok) {
-    const float dot = BWD ? gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2] : 0.f;
+    const float dot = BWD ? dot3_rn(gd, d) : 0.f;
     for (int c = l0 >> 1; c < 3; c += S()) {
       if (FWD) a.rgb[3 * i + c] = pick3(rgb, c) + pick3(cur.c0, c);
       if (BWD) {
         store1(a.g_c0 + c * n + i, pick3(cur.gc, c), acc);
         // dLoss/dmu = (I - d d^T) dLoss/dd / |mu - cam|
-        if (a.g_means) store1(a.g_means + 3 * i + c, (pick3(gd, c) - dot * pick3(d, c)) * inv_dist, acc);
+        if (a.g_means) store1(a.g_means + 3 * i + c, mean_grad_rn(pick3(gd, c), dot, pick3(d, c), inv_dist), acc);
       }
     }
   }

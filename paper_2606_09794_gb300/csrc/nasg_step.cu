@@ -93,9 +93,7 @@ __device__ __forceinline__ bool step_phase1(const StepArgs& s, const RawItem<flo
   P2 dv[3];
   LobeEval<FRAME, P2> ev;
   if (ok) {
-    const float rx = cur.mu[0] - a.cam[0], ry = cur.mu[1] - a.cam[1], rz = cur.mu[2] - a.cam[2];
-    inv_dist = rsqrtf(rx * rx + ry * ry + rz * rz);
-    d[0] = rx * inv_dist; d[1] = ry * inv_dist; d[2] = rz * inv_dist;
+    inv_dist = view_dir_rn(cur.mu, a.cam, d);
     if (IDX(l0) < L) {
       mine = true;
       second = EVEN || (IDX(l0) + 1 < L);
@@ -165,11 +163,11 @@ __device__ __forceinline__ bool step_phase1(const StepArgs& s, const RawItem<flo
     }
   }
   if (ok) {
-    const float dot = gd[0] * d[0] + gd[1] * d[1] + gd[2] * d[2];
+    const float dot = dot3_rn(gd, d);
     for (int c = l0 >> 1; c < 3; c += a.slice) {
       float th = pick3(cur.c0, c);
       if (a.rgb) a.rgb[3 * i + c] = pick3(rgb, c) + pick3(c0e, c);
-      if (a.g_means) a.g_means[3 * i + c] = (pick3(gd, c) - dot * pick3(d, c)) * inv_dist;
+      if (a.g_means) a.g_means[3 * i + c] = mean_grad_rn(pick3(gd, c), dot, pick3(d, c), inv_dist);
       const IDX o = IDX(c) * n + i;
       float mm = s.c0m[o], vv = s.c0v[o];
       adam(s, pick3(gc, c), th, mm, vv);

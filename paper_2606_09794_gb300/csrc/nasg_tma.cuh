@@ -81,7 +81,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Slow path of mbar_wait: the phase was not complete at the first try.
-static __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, int* err, uint32_t limit) {
+static __device__ __forceinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, int* err, uint32_t limit) {
   const uint64_t t0 = global_ns();
   for (uint32_t it = 1; it < limit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;

@@ -17,22 +17,26 @@ import math
 import numpy as np
 
 
-def ulp_perturb(x, rng):
+def ulp_perturb(x, rng, ulps=1):
+    """Every element moved by `ulps` FP32 ulps up or down (random direction)."""
     x = np.asarray(x, dtype=np.float32)
-    up = np.nextafter(x, np.float32(np.inf))
-    dn = np.nextafter(x, np.float32(-np.inf))
-    return np.where(rng.random(x.shape) < 0.5, up, dn).astype(np.float32)
+    up = rng.random(x.shape) < 0.5
+    y = x.copy()
+    for _ in range(ulps):
+        y = np.where(up, np.nextafter(y, np.float32(np.inf)), np.nextafter(y, np.float32(-np.inf)))
+    return y.astype(np.float32)
 
 
-def sensitivity_floor(forward, args, perturb_idx, draws=4, seed=99):
-    """max over draws of |forward(perturbed args) - forward(args)| (elementwise)."""
+def sensitivity_floor(forward, args, perturb_idx, draws=4, seed=99, ulps=1):
+    """max over draws of |forward(perturbed args) - forward(args)| (elementwise), every
+    FP32 input moved by `ulps` ulps in a random direction."""
     rng = np.random.default_rng(seed)
     ref = forward(*args)
     nu = np.zeros_like(ref)
     for _ in range(draws):
         pa = list(args)
         for j in perturb_idx:
-            pa[j] = ulp_perturb(args[j], rng)
+            pa[j] = ulp_perturb(args[j], rng, ulps)
         nu = np.maximum(nu, np.abs(forward(*pa) - ref))
     return ref, nu
 
@@ -51,8 +55,8 @@ def colour_report(gpu, ref, nu, base):
 
 def grad_report(gpu, ref, nu, rtol=1e-4, atol=1e-20):
     """Element-wise gradient check: |g_gpu - g_ref| <= rtol |g_ref| + 4 nu + atol, with nu
-    the oracle's sensitivity floor of each element (as for the colours); atol only absorbs
-    FP32 flush-to-zero of values far below any gradient that matters."""
+    the oracle's sensitivity floor of each element (as for the colours); atol (scalar or
+    per element) only absorbs values far below any gradient that matters."""
     gpu = np.asarray(gpu, dtype=np.float64).ravel()
     ref = np.asarray(ref, dtype=np.float64).ravel()
     nu = np.asarray(nu, dtype=np.float64).ravel()

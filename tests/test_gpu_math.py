@@ -62,3 +62,17 @@ def test_sincos(lib):
     assert np.abs(c - np.cos(x64))[small].max() <= 1.5e-7
     assert np.abs(s - np.sin(x64)).max() <= 2e-6
     assert np.abs(c - np.cos(x64)).max() <= 2e-6
+
+
+def test_pipe_probe_rates(lib):
+    """The pipe microbenchmark gives issue rates within the nominal range of a 152-SM part
+    at up to 2.07 GHz: MUFU ex2 results (16 or 32 per clock per SM: 5e12..1.1e13/s), FP32
+    FMA lane-instructions (128 per clock per SM: at most 4.0e13/s), packed pairs counting
+    two operations, and each rate reproducible (two measurements within 5 %)."""
+    r0, r0b = lib.nasg_pipe_rate(0), lib.nasg_pipe_rate(0)
+    r1 = lib.nasg_pipe_rate(1)
+    r2 = lib.nasg_pipe_rate(2)
+    assert 1e12 < r0 < 2e13 and abs(r0 - r0b) <= 0.05 * r0, (r0, r0b)
+    assert 5e12 < r2 < 5e13, r2
+    assert 5e12 < r1 < 1e14, r1
+    print({"mufu_ex2_per_s": r0, "ffma2_ops_per_s": r1, "ffma_per_s": r2})
