@@ -448,15 +448,19 @@ nasg_status nasg_pipe_probe(int32_t pipe, int64_t iters, int32_t blocks_per_sm, 
 size_t nasgabor_fused_host_workspace_bytes(const nasg_desc* desc, int64_t chunk);
 
 /*
- * nasgabor_fused_fwd_bwd with every array in HOST memory (the same layouts;
- * page-locked memory lets the copies run asynchronously): the primitives flow
- * in chunks of `chunk` through three device slots in `workspace` (device,
- * 256-byte aligned, >= nasgabor_fused_host_workspace_bytes), the copies in
- * both directions overlapping the kernel of the neighbouring chunks on two
- * internal copy streams (created once per device). Ordered after the work
- * already queued on `stream`; when `stream` reaches the point after this call,
- * the outputs are in host memory. desc->accumulate must be 0. Errors as
- * nasgabor_fused_fwd_bwd, plus NASG_ERR_RANGE for a bad chunk or workspace.
+ * nasgabor_fused_fwd_bwd with every array in HOST memory (the same layouts).
+ * When every array is page-locked (mapped into the device's address space,
+ * e.g. cudaHostAlloc or torch pin_memory), the kernel reads its inputs and
+ * writes its outputs in place over the host link, with plain loads and stores
+ * (no copies; chunk and workspace are validated but not used). Otherwise the
+ * primitives flow in chunks of `chunk` through three device slots in
+ * `workspace` (device, 256-byte aligned, >= nasgabor_fused_host_workspace_bytes),
+ * the copies in both directions overlapping the kernel of the neighbouring
+ * chunks on two internal copy streams (created once per device). Ordered after
+ * the work already queued on `stream`; when `stream` reaches the point after
+ * this call, the outputs are in host memory. desc->accumulate must be 0.
+ * Errors as nasgabor_fused_fwd_bwd, plus NASG_ERR_RANGE for a bad chunk or
+ * workspace.
  */
 nasg_status nasgabor_fused_fwd_bwd_host(const nasg_desc* desc, const void* params, const void* c0,
                                         const float* means, const float* cam, const float* g_rgb, float* rgb,

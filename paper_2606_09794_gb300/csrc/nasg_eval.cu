@@ -72,10 +72,10 @@ extern "C" nasg_status nasgabor_eval_bwd(const nasg_desc* desc, const void* para
   return launch_eval<kBwd>(desc, a, as_stream(stream));
 }
 
-extern "C" nasg_status nasgabor_fused_fwd_bwd(const nasg_desc* desc, const void* params, const void* c0,
-                                              const float* means, const float* cam, const float* g_rgb,
-                                              float* rgb, float* g_params, float* g_c0, float* g_means,
-                                              void* stream) {
+namespace nasg {
+static nasg_status fused_impl(const nasg_desc* desc, const void* params, const void* c0, const float* means,
+                              const float* cam, const float* g_rgb, float* rgb, float* g_params, float* g_c0,
+                              float* g_means, bool no_staging, cudaStream_t stream) {
   nasg_status st = check_desc(desc);
   if (st != NASG_OK) return st;
   if (desc->n == 0) return NASG_OK;
@@ -93,6 +93,21 @@ extern "C" nasg_status nasgabor_fused_fwd_bwd(const nasg_desc* desc, const void*
   a.g_params = g_params;
   a.g_c0 = g_c0;
   a.g_means = g_means;
+  a.no_staging = no_staging ? 1 : 0;
   if (desc->n == 0) return NASG_OK;
-  return launch_eval<kFwdBwd>(desc, a, as_stream(stream));
+  return launch_eval<kFwdBwd>(desc, a, stream);
+}
+
+nasg_status fused_fwd_bwd_register_path(const nasg_desc* desc, const void* params, const void* c0,
+                                        const float* means, const float* cam, const float* g_rgb, float* rgb,
+                                        float* g_params, float* g_c0, float* g_means, cudaStream_t stream) {
+  return fused_impl(desc, params, c0, means, cam, g_rgb, rgb, g_params, g_c0, g_means, true, stream);
+}
+}  // namespace nasg
+
+extern "C" nasg_status nasgabor_fused_fwd_bwd(const nasg_desc* desc, const void* params, const void* c0,
+                                              const float* means, const float* cam, const float* g_rgb,
+                                              float* rgb, float* g_params, float* g_c0, float* g_means,
+                                              void* stream) {
+  return fused_impl(desc, params, c0, means, cam, g_rgb, rgb, g_params, g_c0, g_means, false, as_stream(stream));
 }

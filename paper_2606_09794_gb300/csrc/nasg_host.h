@@ -66,4 +66,10 @@ inline nasg_status check_desc(const nasg_desc* d) {
 
 inline int elem_size(int32_t dtype) { return dtype == NASG_DTYPE_BF16 ? 2 : 4; }
 
+// nasgabor_fused_fwd_bwd on the register path only (plain loads and stores, no bulk
+// copies), for buffers the kernel reads and writes in page-locked host memory.
+nasg_status fused_fwd_bwd_register_path(const nasg_desc* desc, const void* params, const void* c0,
+                                        const float* means, const float* cam, const float* g_rgb, float* rgb,
+                                        float* g_params, float* g_c0, float* g_means, cudaStream_t stream);
+
 }  // namespace nasg

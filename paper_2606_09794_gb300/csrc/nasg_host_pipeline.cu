@@ -1,5 +1,7 @@
 // Fused forward+backward for parameters and outputs in HOST memory
-// (nasgabor_fused_fwd_bwd_host): the primitives are processed in chunks that
+// (nasgabor_fused_fwd_bwd_host). Page-locked arrays are read and written in place
+// by the kernel (register path) over the chip-to-chip link. Otherwise the
+// primitives are processed in chunks that
 // flow through three device slots, with the host->device copies of chunk i+1,
 // the kernel of chunk i and the device->host copies of chunk i-1 in flight at
 // the same time (two internal copy streams plus the caller's stream, ordered by
@@ -69,6 +71,17 @@ Pipeline* device_pipeline() {
   return &p;
 }
 
+// The device address of page-locked host memory at p (mapped into the device's
+// address space), or nullptr for any other memory (pageable, device, unknown).
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // an unregistered pointer is not an error of this call
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 }  // namespace
 }  // namespace nasg
 
@@ -99,6 +112,20 @@ extern "C" nasg_status nasgabor_fused_fwd_bwd_host(const nasg_desc* desc, const 
   const int es = elem_size(desc->param_dtype);
   const SlotLayout sl = slot_layout(P, L, es, chunk);
   if (workspace_bytes < kSlots * sl.bytes) return NASG_ERR_RANGE;
+  {
+    // Every array page-locked: the kernel reads and writes them in place over the
+    // host link (plain loads and stores; no copies, no workspace).
+    const void* hp[8] = {params, c0, means, g_rgb, rgb, g_params, g_c0, g_means};
+    const void* dp[8] = {};
+    bool direct = true;
+    for (int j = 0; j < 8 && direct; ++j) direct = (j == 7 && !hp[j]) || (dp[j] = mapped_host(hp[j])) != nullptr;
+    if (direct)
+      return fused_fwd_bwd_register_path(desc, dp[0], dp[1], static_cast<const float*>(dp[2]), cam,
+                                         static_cast<const float*>(dp[3]), static_cast<float*>(const_cast<void*>(dp[4])),
+                                         static_cast<float*>(const_cast<void*>(dp[5])),
+                                         static_cast<float*>(const_cast<void*>(dp[6])),
+                                         static_cast<float*>(const_cast<void*>(dp[7])), as_stream(stream));
+  }
   Pipeline* pipe = device_pipeline();
   if (!pipe) return check_launch();
   std::lock_guard<std::mutex> call_lock(pipe->call);

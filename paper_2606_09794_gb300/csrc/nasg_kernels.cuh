@@ -39,6 +39,7 @@ struct EvalArgs {
   int32_t normalised;
   int32_t exact;        // exact normalisation (implies normalised)
   int32_t accumulate;
+  int32_t no_staging;   // 1: the register path only (buffers in page-locked host memory)
   const float* g_rgb;
   float* rgb;
   float* g_params;
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(256, 2) eval_kernel(const EvalArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// TMA-staged variant: tiles of TP = 256/S consecutive primitives. For a tile,
+// TMA-staged variant: tiles of TP = THREADS/S consecutive primitives. For a tile,
 // every parameter plane is one contiguous span of TP*L elements, and the means,
 // upstream gradients and diffuse colours are contiguous too, so one elected
 // thread moves a whole tile into shared memory with bulk asynchronous copies
@@ -442,10 +443,16 @@ __global__ void __launch_bounds__(256, 2) eval_kernel(const EvalArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int kStages = 3;
 // Threads (and warps) of a block of the staged kernels; the launches use exactly this.
-// A compile-time warp count keeps the producer's turn (iteration mod warps) a mask:
+// A compile-time warp count keeps the producer's turn (iteration mod warps) cheap:
 // the same modulo by blockDim.x / 32 at run time cost 3.5 % of the fused pass.
+// The forward alone (fewer registers) runs 384 threads, 24 warps per SM at two
+// blocks: 3 % faster than 256 for the FP32 forward, while the passes with a
+// backward need the registers of 256-thread blocks (at 384 they spill).
+// A tile of THREADS/S primitives is a multiple of 8 for S <= THREADS/8.
 constexpr uint32_t kStagedThreads = 256;
 constexpr uint32_t kStagedWarps = kStagedThreads / 32;
+template <int MODE>
+constexpr uint32_t staged_threads() { return MODE == kFwd ? 384u : kStagedThreads; }
 
 // Moves the plain-load part of a span plan (the last bytes of a buffer).
 __device__ __forceinline__ void span_tail(unsigned char* dst, const void* base, const SpanPlan& s) {
@@ -498,15 +505,17 @@ __device__ __forceinline__ void issue_tile(const EvalArgs& a, const TileGeom& g,
 }
 
 template <int FRAME, typename T, int MODE, int FLAGS, bool ANYN, int LC>
-__global__ void __launch_bounds__(kStagedThreads, 2) eval_tma_kernel(const EvalArgs a) {
+__global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(const EvalArgs a) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr bool FWD = (MODE & kFwd) != 0;
   constexpr bool BWD = (MODE & kBwd) != 0;
+  constexpr uint32_t NT = staged_threads<MODE>();
+  constexpr uint32_t NW = NT / 32;
   using W = typename RawWord<T>::type;
   extern __shared__ __align__(128) unsigned char smem[];
   const int slog = LC ? log2_of(slice_of_lobes(LC)) : a.slice_log2;
   const uint32_t L = LC ? uint32_t(LC) : uint32_t(a.n_lobes);
-  const TileGeom g = tile_geom<T, P, ANYN>(slog, int(L));
+  const TileGeom g = tile_geom<T, P, ANYN>(slog, int(L), NT);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * g.stage_bytes);  // tile landed
   uint64_t* empty = full + kStages;                                             // tile read by all warps
   const uint32_t n = uint32_t(a.n);
@@ -515,7 +524,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) eval_tma_kernel(const EvalA
 #pragma unroll
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kStagedWarps);
+      mbar_init(&empty[s], NW);
     }
     fence_barrier_init();
   }
@@ -544,7 +553,7 @@ __global__ void __launch_bounds__(kStagedThreads, 2) eval_tma_kernel(const EvalA
     if (tile >= n_tiles) break;  // block-uniform
     // producer: refill the stage read in the previous iteration (one iteration
     // of slack, so the wait for its last reader is normally already over)
-    if (it >= 1 && lane == 0 && warp == (it - 1) % kStagedWarps) {
+    if (it >= 1 && lane == 0 && warp == (it - 1) % NW) {
       const uint32_t pit = it - 1;
       const uint32_t nit = pit + kStages;
       const uint32_t next = blockIdx.x + nit * gridDim.x;
@@ -641,9 +650,10 @@ nasg_status launch_idx(const EvalArgs& a, bool even, cudaStream_t s) {
 }
 
 // The TMA-staged kernel applies (see its requirements above).
-template <int FRAME, typename T>
+template <int MODE, int FRAME, typename T>
 bool tma_eligible(const EvalArgs& a, bool even) {
-  if (!even || a.idx != nullptr || a.n_items != a.n) return false;
+  if (!even || a.idx != nullptr || a.n_items != a.n || a.no_staging) return false;
+  if (uint32_t(a.slice) > staged_threads<MODE>() / 8) return false;  // tiles of a multiple of 8 primitives
   if (a.n * a.n_lobes * int64_t(sizeof(T)) % 16 != 0) return false;  // parameter planes on 16-byte boundaries
   if (a.n * a.n_lobes * FrameTraits<FRAME>::P >= (int64_t(1) << 31)) return false;
   const void* ptrs[] = {a.params, a.means, a.c0, a.g_rgb};
@@ -655,16 +665,17 @@ bool tma_eligible(const EvalArgs& a, bool even) {
 template <int MODE, int FRAME, typename T, int FLAGS, bool ANYN, int LC>
 nasg_status launch_tma_geom(const EvalArgs& a, cudaStream_t s) {
   constexpr int P = FrameTraits<FRAME>::P;
-  const TileGeom g = tile_geom<T, P, ANYN>(a.slice_log2, a.n_lobes);
+  constexpr uint32_t NT = staged_threads<MODE>();
+  const TileGeom g = tile_geom<T, P, ANYN>(a.slice_log2, a.n_lobes, NT);
   const size_t smem = size_t(kStages) * g.stage_bytes + 2 * kStages * sizeof(uint64_t);
   auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS, ANYN, LC>;
   if (const nasg_status e = ensure_smem_limit(reinterpret_cast<const void*>(k), smem); e != NASG_OK) return e;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStagedThreads, smem) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const uint32_t n_tiles = uint32_t((a.n + g.tp - 1) / g.tp);
   const uint32_t cap = uint32_t(sm_count() * per_sm);
-  k<<<n_tiles < cap ? n_tiles : cap, kStagedThreads, smem, s>>>(a);
+  k<<<n_tiles < cap ? n_tiles : cap, NT, smem, s>>>(a);
   return check_launch();
 }
 
@@ -692,7 +703,7 @@ nasg_status launch_tma(const EvalArgs& a, cudaStream_t s) {
 
 template <int MODE, int FRAME, typename T>
 nasg_status launch_frame_dtype(const EvalArgs& a, bool even, cudaStream_t s) {
-  if (tma_eligible<FRAME, T>(a, even)) {
+  if (tma_eligible<MODE, FRAME, T>(a, even)) {
     const bool dflt = a.identity == 0 && a.normalised != 0 && a.exact == 0 && a.accumulate == 0;
     return dflt ? launch_tma<MODE, FRAME, T, kFlagsDefault>(a, s) : launch_tma<MODE, FRAME, T, kFlagsRuntime>(a, s);
   }
@@ -712,10 +723,10 @@ template <int MODE, int FAM>
 nasg_status launch_family(const EvalArgs& a, bool even, bool bf16, cudaStream_t s) {
   constexpr int LAYOUT = layout_id(NASG_FRAME_QUAT, FAM);
   if (bf16) {
-    if (tma_eligible<LAYOUT, __nv_bfloat16>(a, even)) return launch_tma<MODE, LAYOUT, __nv_bfloat16, kFlagsRuntime>(a, s);
+    if (tma_eligible<MODE, LAYOUT, __nv_bfloat16>(a, even)) return launch_tma<MODE, LAYOUT, __nv_bfloat16, kFlagsRuntime>(a, s);
     return launch_idx<MODE, LAYOUT, __nv_bfloat16, uint64_t>(a, even, s);
   }
-  if (tma_eligible<LAYOUT, float>(a, even)) return launch_tma<MODE, LAYOUT, float, kFlagsRuntime>(a, s);
+  if (tma_eligible<MODE, LAYOUT, float>(a, even)) return launch_tma<MODE, LAYOUT, float, kFlagsRuntime>(a, s);
   return launch_idx<MODE, LAYOUT, float, uint64_t>(a, even, s);
 }
 

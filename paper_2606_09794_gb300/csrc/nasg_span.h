@@ -73,9 +73,9 @@ struct TileGeom {
 // gradients and diffuse colours follow span plans, so their regions hold a
 // plan's head and rounding.
 template <typename T, int P, bool ANYN>
-NASG_HD constexpr TileGeom tile_geom(int slice_log2, int n_lobes) {
+NASG_HD constexpr TileGeom tile_geom(int slice_log2, int n_lobes, uint32_t threads = 256u) {
   TileGeom g{};
-  g.tp = 256u >> slice_log2;
+  g.tp = threads >> slice_log2;
   g.plane_bytes = g.tp * uint32_t(n_lobes) * uint32_t(sizeof(T));
   g.mu_cap = ANYN ? span_capacity(g.tp * 12u) : g.tp * 12u;
   g.c0_cap = ANYN ? span_capacity(g.tp * uint32_t(sizeof(T))) : g.tp * uint32_t(sizeof(T));

@@ -597,18 +597,21 @@ def test_staged_path_accumulate(lib, bf16, n, L):
     assert max(rel_l2(fg[p], bg[p]) for p in range(fg.shape[0])) < 1e-6
 
 
+@pytest.mark.parametrize("pinned", [True, False])
 @pytest.mark.parametrize("n,L,chunk,bf16", [(100_003, 8, 16384, True), (4096, 4, 1024, False), (777, 3, 64, True),
                                             (5000, 8, 8, False)])
-def test_host_resident_fused_matches_device_fused(lib, n, L, chunk, bf16):
-    """Host arrays streamed in chunks through the device (copies overlapping the
-    kernel) give the device-resident fused pass's results."""
+def test_host_resident_fused_matches_device_fused(lib, n, L, chunk, bf16, pinned):
+    """Host arrays give the device-resident fused pass's results: page-locked ones read
+    and written in place by the kernel, pageable ones streamed in chunks through the
+    device (copies overlapping the kernel)."""
     import torch
     w = inputs.point_cloud_workload(n, L, 60 + L)
     params, c0, _, _ = _prepare(w, bf16)
     means, g_rgb = _dev(w.means), _dev(w.g_rgb)
     ref = lib.nasgabor_fused_fwd_bwd(params, c0, means, w.cam, g_rgb, L)
-    hp = [params.cpu().pin_memory(), c0.cpu().pin_memory(), means.cpu().pin_memory(), g_rgb.cpu().pin_memory()]
-    out = tuple(torch.empty(t.shape, dtype=torch.float32).pin_memory() for t in ref)
+    pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+    hp = [pin(params.cpu()), pin(c0.cpu()), pin(means.cpu()), pin(g_rgb.cpu())]
+    out = tuple(pin(torch.empty(t.shape, dtype=torch.float32)) for t in ref)
     hf = lib.HostFused(n, L, params.dtype, chunk=chunk)
     hf(hp[0], hp[1], hp[2], w.cam, hp[3], out)
     torch.cuda.synchronize()
