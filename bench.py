@@ -772,14 +772,15 @@ def measure_fit(nb, inputs, dev, stream, n=2_000_000, ls=16, lt=4, steps=200, n_
     fractions = None
     if counts is not None:
         per_s = n * steps / (ms * 1e-3)          # (primitive, step) pairs per second
-        fractions = {"xu_of_measured_mufu": counts["xu_per_prim_step"] * 32 * per_s / ceilings["mufu_ex2_per_s"],
+        fractions = {"mufu_of_measured": counts["mufu_ops_per_prim_step"] * per_s / ceilings["mufu_ex2_per_s"],
+                     "xu_pipe_active": counts["xu_pipe_active_pct"] / 100.0,
                      "fma_pipe_active": counts["fma_pipe_active_pct"] / 100.0,
                      "issue_active": counts["issue_active_pct"] / 100.0,
-                     "note": "xu: XU-pipe lane instructions per second (the count per (primitive, step) "
-                             "from the committed ncu summary profiles/nasgabor_fit_step_500k_ls16_lt4.md "
-                             "times this run's rate) over the MUFU ex2 rate the pipe probe measured; "
-                             "fma_pipe_active and issue_active: the ncu pipe and issue utilisation of the "
-                             "same capture (500k primitives, same kernel instance)"}
+                     "note": "mufu_of_measured: the kernel's MUFU operations per (primitive, step), counted "
+                             "in its source (profiles/nasgabor_fit_step_500k_ls16_lt4.md), times this run's "
+                             "(primitive, step) rate, over the MUFU ex2 rate the pipe probe measured; "
+                             "xu/fma_pipe_active and issue_active: ncu utilisation of the committed capture "
+                             "(500k primitives, the same kernel instance)"}
     return {"workload": f"fit N={n}, student L={ls} BF16 (FP32 master), teacher L={lt} FP32, {n_dirs} directions/step, "
                         f"{steps} Adam steps, base lr 1e-3 with the cosine schedule from iteration "
                         f"{round(inputs.FIT_SCHEDULE_START * steps / inputs.FIT_STEPS)}",
@@ -815,7 +816,8 @@ def profiled_fit_counts():
                     kv[k.strip()] = v.strip().strip("`")
         if kv.get("source_sha256_16") != fit_source_hash():
             return None
-        return {"xu_per_prim_step": float(kv["xu_warp_inst_per_prim_step"]),
+        return {"mufu_ops_per_prim_step": float(kv["mufu_ops_per_prim_step"]),
+                "xu_pipe_active_pct": float(kv["xu_pipe_active_pct"]),
                 "fma_pipe_active_pct": float(kv["fma_pipe_active_pct"]),
                 "issue_active_pct": float(kv["issue_active_pct"])}
     except Exception:

@@ -545,6 +545,24 @@ def test_bounded_wait_reports_device_error(lib):
     assert float((x * 2).sum()) == 32.0
 
 
+def test_bounded_wait_time(lib):
+    """The longest wait the probe allows (2^20 tries) ends on its own, in at most the
+    one-second wall-time bound plus the rounds before the next timer check; the time per
+    try (the hardware's suspension interval) gives the worst case of the kernels' 2^22."""
+    import torch
+    lib.nasg_device_status()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lib.nasg_probe_wait_timeout(1 << 20)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    with pytest.raises(lib.NasgError):
+        lib.nasg_device_status()
+    print(f"bounded wait: 2^20 tries in {ms:.3f} ms, {ms * 1e6 / 2 ** 20:.1f} ns per try")
+    assert ms < 1500.0
+
+
 @pytest.mark.parametrize("bf16,n,L", [(True, 4096, 8), (False, 4096, 8), (True, 1000, 4), (True, 2056, 16),
                                       (False, 1048, 2), (True, 8, 8),
                                       # any N: diffuse-colour planes off 16-byte boundaries, buffer ends
