@@ -419,6 +419,7 @@ nasg_status sh_eval_bwd(int32_t degree, int64_t n, const float* coeffs, const fl
  *   fn 0: y = e^x - 1 for x <= 0            (y2 unused, may be NULL)
  *   fn 1: y = tanh(x), y2 = 1 - tanh(x)^2
  *   fn 2: y = sin(x),  y2 = cos(x)          (|x| <= 6400)
+ *   fn 3: fn 1 by the BF16 weight table the BF16 kernels use (x BF16-valued, finite)
  * x, y, y2 device [n] f32. Errors: NASG_ERR_RANGE (fn or n), NASG_ERR_NULL.
  */
 nasg_status nasg_math_probe(int32_t fn, const float* x, float* y, float* y2, int64_t n, void* stream);

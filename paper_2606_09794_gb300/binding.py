@@ -354,7 +354,8 @@ def nasg_pipe_rate(pipe, iters=1 << 14, blocks_per_sm=4, reps=3, stream=None):
 
 
 def nasg_math_probe(fn, x, stream=None):
-    """Diagnostic: the library's FP32 elementary function `fn` (0 expm1, 1 tanh, 2 sincos) at x."""
+    """Diagnostic: the library's FP32 elementary function `fn` (0 expm1, 1 tanh, 2 sincos, 3 tanh
+    by the BF16 weight table) at x."""
     _cuda(x, "x", torch.float32)
     y = torch.empty_like(x)
     y2 = torch.empty_like(x) if fn > 0 else None

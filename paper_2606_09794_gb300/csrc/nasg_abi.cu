@@ -128,6 +128,11 @@ extern "C" nasg_status nasg_device_status(void* stream) {
 namespace nasg {
 __global__ void math_probe_kernel(int fn, const float* __restrict__ x, float* __restrict__ y,
                                   float* __restrict__ y2, int64_t n) {
+  __shared__ float4 tab[kTanhEntries];
+  if (fn == 3) {  // block-uniform
+    fill_tanh_table(tab);
+    __syncthreads();
+  }
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
     const float v = x[i];
@@ -136,6 +141,8 @@ __global__ void math_probe_kernel(int fn, const float* __restrict__ x, float* __
       a = vexpm1n(v);
     } else if (fn == 1) {
       vtanh(v, a, b);
+    } else if (fn == 3) {
+      tanh_lookup(tab, v, a, b);
     } else {
       vsincos(v, a, b);
     }
@@ -147,7 +154,7 @@ __global__ void math_probe_kernel(int fn, const float* __restrict__ x, float* __
 
 extern "C" nasg_status nasg_math_probe(int32_t fn, const float* x, float* y, float* y2, int64_t n,
                                        void* stream) {
-  if (fn < 0 || fn > 2 || n < 0) return NASG_ERR_RANGE;
+  if (fn < 0 || fn > 3 || n < 0) return NASG_ERR_RANGE;
   if (n == 0) return NASG_OK;
   if (!x || !y || (fn > 0 && !y2)) return NASG_ERR_NULL;
   nasg::math_probe_kernel<<<nasg::grid_for(n, 256), 256, 0, nasg::as_stream(stream)>>>(fn, x, y, y2, n);

@@ -95,9 +95,10 @@ struct Act {
   V phi;  // carrier phase (phase family; stored as is)
 };
 
-// r: lam_r, a_r, k_r, w_r, w_g, w_b
-template <class V>
-__device__ __forceinline__ void activate(const V* r, bool identity, Act<V>& o) {
+// r: lam_r, a_r, k_r, w_r, w_g, w_b. TAB: the raw values are BF16 and the weights'
+// tanh comes from the block's table (tanh_lookup).
+template <bool TAB = false, class V>
+__device__ __forceinline__ void activate(const V* r, bool identity, Act<V>& o, const float4* tab = nullptr) {
   if (identity) {
     const V one = vconst<V>(1.f);
     o.lam = r[0]; o.a = r[1]; o.k = r[2];
@@ -118,7 +119,13 @@ __device__ __forceinline__ void activate(const V* r, bool identity, Act<V>& o) {
   o.k = 40.f * sig;
   o.s_k = 80.f * sig * one_m_sig;
 #pragma unroll
-  for (int c = 0; c < 3; ++c) vtanh(r[3 + c], o.w[c], o.s_w[c]);
+  for (int c = 0; c < 3; ++c) {
+    if constexpr (TAB) {
+      tanh_lookup(tab, r[3 + c], o.w[c], o.s_w[c]);
+    } else {
+      vtanh(r[3 + c], o.w[c], o.s_w[c]);
+    }
+  }
 }
 
 // Activations of a lobe family's stored scalars r = [lam, (a), (k), (phi), w_r, w_g, w_b];

@@ -10,7 +10,8 @@
 //                 (truncation < 1.1e-8 relative), 2^(y log2 e) - 1 below -0.5
 //                 (|result| >= 0.39 there, so the subtraction loses nothing).
 //   vtanh(x)      odd Taylor series to x^9 for |x| < 1/4, else
-//                 (1 - e)/(1 + e) with e = e^{-2|x|}; 1 - tanh^2 x = 4 e/(1 + e)^2.
+//                 (1 - e)/(1 + e) with e = e^{-2|x|}; 1 - tanh^2 x = 4 e/(1 + e)^2;
+//                 tanh_lookup the same values by table for BF16-valued arguments.
 //   vlnkappa(t)   ln(1 + t) for t in [-1, 0]: 2 atanh(t/(2 + t)) series to
 //                 s^7 where 1 + t >= 0.75 (|s| <= 1/7: truncation < 1.9e-8 relative),
 //                 lg2.approx elsewhere.
@@ -86,6 +87,51 @@ __device__ __forceinline__ void vtanh(V x, V& t, V& sech2) {
   const V tl = vcopysign((1.f - ex) * inv, x);
   t = vsel(vlt(ax, 0.25f), x * q, tl);
   sech2 = 4.f * ex * (inv * inv);           // 1 - tanh^2 = 4 e/(1 + e)^2
+}
+
+// Weight activation for BF16-stored raw values by table: the entries are vtanh of
+// every BF16 magnitude in [2^-13, 64) (2432 values), formed on the device by vtanh
+// itself, so there a lookup returns the bits of the evaluation. Outside, closed forms:
+// from 64 on t = +-1 and 1 - tanh^2 = 0 (what vtanh gives there); below 2^-13 t = x
+// (what the series gives) and 1 - tanh^2 = 1 - x^2 (within a few ulps of vtanh's
+// 4 e/(1 + e)^2, and exact to rounding). An entry (A, B, C, D) gives
+// t = B x + copysign(A, x) and 1 - tanh^2 = D x^2 + C: (tanh|x_j|, 0, sech^2 x_j, 0) in
+// the range, (1, 0, 0, 0) past it, (0, 1, 1, -1) below it. Finite inputs only (an
+// infinite raw value gives NaN, where the evaluation gives +-1).
+constexpr uint32_t kTanhLo = 0x3900u;                // BF16 magnitude bits of 2^-13
+constexpr uint32_t kTanhHi = 0x4280u;                // BF16 magnitude bits of 64
+constexpr uint32_t kTanhN = kTanhHi - kTanhLo;       // 2432 entries
+constexpr uint32_t kTanhEntries = kTanhN + 2;        // and the two closed forms
+constexpr uint32_t kTanhBytes = kTanhEntries * 16u;  // 38944 bytes of shared memory
+
+// Fills the table (all threads of the block; the caller synchronises before use).
+__device__ __forceinline__ void fill_tanh_table(float4* tab) {
+  for (uint32_t j = threadIdx.x; j < kTanhEntries; j += blockDim.x) {
+    float4 e;
+    if (j < kTanhN) {
+      float t, s2;
+      vtanh<float>(__uint_as_float((kTanhLo + j) << 16), t, s2);
+      e = make_float4(t, 0.f, s2, 0.f);
+    } else if (j == kTanhN) {
+      e = make_float4(1.f, 0.f, 0.f, 0.f);
+    } else {
+      e = make_float4(0.f, 1.f, 1.f, -1.f);
+    }
+    tab[j] = e;
+  }
+}
+
+// tanh x and 1 - tanh^2 x for x a BF16 value (in an FP32 register) from the table.
+__device__ __forceinline__ void tanh_lookup(const float4* tab, float x, float& t, float& sech2) {
+  const uint32_t m = (__float_as_uint(x) >> 16) & 0x7fffu;
+  const uint32_t j = m < kTanhLo ? kTanhN + 1u : min(m - kTanhLo, kTanhN);
+  const float4 e = tab[j];
+  t = fmaf(e.y, x, copysignf(e.x, x));
+  sech2 = fmaf(e.w * x, x, e.z);
+}
+__device__ __forceinline__ void tanh_lookup(const float4* tab, P2 x, P2& t, P2& sech2) {
+  tanh_lookup(tab, x.v.x, t.v.x, sech2.v.x);
+  tanh_lookup(tab, x.v.y, t.v.y, sech2.v.y);
 }
 
 template <class V>

@@ -82,14 +82,15 @@ struct LobeEval {
   V G;
 };
 
-// Evaluates the lobes held in pv[0..P) (one lobe per component of V) at d.
-template <int FRAME, bool BWD, class V>
+// Evaluates the lobes held in pv[0..P) (one lobe per component of V) at d. TAB: the
+// stored values are BF16 and `tab` is the block's tanh table (see tanh_lookup).
+template <int FRAME, bool BWD, bool TAB = false, class V>
 __device__ __forceinline__ void lobe_eval(const V* pv, const V* d, bool identity, bool normalised, bool exact,
-                                          LobeEval<FRAME, V>& e) {
+                                          LobeEval<FRAME, V>& e, const float4* tab = nullptr) {
   using TR = FrameTraits<FRAME>;
   constexpr int B = TR::B;
   if constexpr (TR::FAM == kFamNasGabor) {
-    activate(pv + B, identity, e.act);
+    activate<TAB>(pv + B, identity, e.act, tab);
   } else {
     activate_family<TR::FAM>(pv + B, identity, e.act);
   }
@@ -141,11 +142,11 @@ __device__ __forceinline__ void lobe_grad(const LobeEval<FRAME, V>& e, const V* 
 
 // Evaluates the lobes held in pv[0..P): adds their colour into rgb and, with
 // BWD, writes the P raw-parameter gradients into gp and adds dLoss/dd into gd.
-template <int FRAME, bool FWD, bool BWD, class V>
+template <int FRAME, bool FWD, bool BWD, bool TAB = false, class V>
 __device__ __forceinline__ void lobe_step(const V* pv, const V* d, const V* gc, bool identity, bool normalised,
-                                          bool exact, V* rgb, V* gd, V* gp) {
+                                          bool exact, V* rgb, V* gd, V* gp, const float4* tab = nullptr) {
   LobeEval<FRAME, V> e;
-  lobe_eval<FRAME, BWD>(pv, d, identity, normalised, exact, e);
+  lobe_eval<FRAME, BWD, TAB>(pv, d, identity, normalised, exact, e, tab);
   if (FWD) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) rgb[c] = vfma(e.act.w[c], e.G, rgb[c]);
@@ -163,6 +164,12 @@ __device__ __forceinline__ void store2(float* p, P2 v, bool acc) {
   }
   *q = v.v;
 }
+
+// The kernels that read BF16-stored NASGabor lobes take the weights' tanh from a
+// shared-memory table (tanh_lookup; the bits of the evaluation but for 1 - tanh^2 of
+// raw weights below 2^-13, a few ulps apart).
+template <int FRAME, typename T>
+constexpr bool tanh_table() { return sizeof(T) == 2 && FrameTraits<FRAME>::FAM == kFamNasGabor; }
 
 // Raw words of one lane's work item, fetched one item ahead of the compute:
 // the two lobes' P stored scalars (one 32-bit word per plane for bf16 pairs, a
@@ -277,9 +284,9 @@ constexpr int slice_of_lobes(int L) { return L <= 2 ? 1 : 2 * slice_of_lobes((L 
 constexpr int log2_of(int x) { return x <= 1 ? 0 : 1 + log2_of(x >> 1); }
 
 // LC: the lobe count when fixed at compile time (0: read from the arguments).
-template <int FRAME, typename T, typename IDX, int MODE, bool EVEN, int FLAGS, int LC = 0>
+template <int FRAME, typename T, typename IDX, int MODE, bool EVEN, int FLAGS, int LC = 0, bool TAB = false>
 __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, FrameTraits<FRAME>::P>& cur, IDX i,
-                                          int l0) {
+                                          int l0, const float4* tab = nullptr) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr bool FWD = (MODE & kFwd) != 0;
   constexpr bool BWD = (MODE & kBwd) != 0;
@@ -309,8 +316,8 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
       P2 rgbv[3] = {p2(0.f), p2(0.f), p2(0.f)};
       P2 gdv[3] = {p2(0.f), p2(0.f), p2(0.f)};
       P2 gp[P];
-      lobe_step<FRAME, FWD, BWD>(pv, dv, gcv, Flags<FLAGS>::identity(a), Flags<FLAGS>::normalised(a),
-                                 Flags<FLAGS>::exact(a), rgbv, gdv, gp);
+      lobe_step<FRAME, FWD, BWD, TAB>(pv, dv, gcv, Flags<FLAGS>::identity(a), Flags<FLAGS>::normalised(a),
+                                      Flags<FLAGS>::exact(a), rgbv, gdv, gp, tab);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         rgb[c] = rgbv[c].v.x + (second ? rgbv[c].v.y : 0.f);
@@ -406,6 +413,12 @@ __global__ void __launch_bounds__(256, 2) eval_kernel(const EvalArgs a) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr bool FWD = (MODE & kFwd) != 0;
   constexpr bool BWD = (MODE & kBwd) != 0;
+  constexpr bool TAB = tanh_table<FRAME, T>();
+  __shared__ float4 tab[TAB ? kTanhEntries : 1];
+  if constexpr (TAB) {
+    fill_tanh_table(tab);
+    __syncthreads();
+  }
   const int l0 = 2 * (threadIdx.x & (a.slice - 1));
   const IDX total = IDX(a.n_items) << a.slice_log2;
   const IDX stride = IDX(gridDim.x) * blockDim.x;
@@ -416,11 +429,11 @@ __global__ void __launch_bounds__(256, 2) eval_kernel(const EvalArgs a) {
   // block-uniform loop: every lane of a warp reaches the shuffles
   while (t0 < total) {
     fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, total, t0 + stride + threadIdx.x, l0, b1, i1);
-    eval_item<FRAME, T, IDX, MODE, EVEN, FLAGS>(a, b0, i0, l0);
+    eval_item<FRAME, T, IDX, MODE, EVEN, FLAGS, 0, TAB>(a, b0, i0, l0, tab);
     t0 += stride;
     if (t0 >= total) break;
     fetch_item<T, P, IDX, EVEN, FWD, BWD>(a, total, t0 + stride + threadIdx.x, l0, b0, i0);
-    eval_item<FRAME, T, IDX, MODE, EVEN, FLAGS>(a, b1, i1, l0);
+    eval_item<FRAME, T, IDX, MODE, EVEN, FLAGS, 0, TAB>(a, b1, i1, l0, tab);
     t0 += stride;
   }
 }
@@ -453,6 +466,8 @@ constexpr uint32_t kStagedThreads = 256;
 constexpr uint32_t kStagedWarps = kStagedThreads / 32;
 template <int MODE>
 constexpr uint32_t staged_threads() { return MODE == kFwd ? 384u : kStagedThreads; }
+// The full and empty barriers of the stages, rounded to 16 bytes.
+constexpr uint32_t kBarrierBytes = (2u * kStages * 8u + 15u) & ~15u;
 
 // Moves the plain-load part of a span plan (the last bytes of a buffer).
 __device__ __forceinline__ void span_tail(unsigned char* dst, const void* base, const SpanPlan& s) {
@@ -518,6 +533,10 @@ __global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(con
   const TileGeom g = tile_geom<T, P, ANYN>(slog, int(L), NT);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * g.stage_bytes);  // tile landed
   uint64_t* empty = full + kStages;                                             // tile read by all warps
+  constexpr bool TAB = tanh_table<FRAME, T>();
+  // after the barriers, on a 16-byte boundary (the stages are 128-byte multiples)
+  float4* tab = reinterpret_cast<float4*>(smem + kStages * g.stage_bytes + kBarrierBytes);
+  if constexpr (TAB) fill_tanh_table(tab);
   const uint32_t n = uint32_t(a.n);
   const uint32_t n_tiles = (n + g.tp - 1) / g.tp;
   if (threadIdx.x == 0) {
@@ -606,7 +625,7 @@ __global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(con
     }
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
-    eval_item<FRAME, T, uint32_t, MODE, true, FLAGS, LC>(a, r, i, l0);
+    eval_item<FRAME, T, uint32_t, MODE, true, FLAGS, LC, TAB>(a, r, i, l0, tab);
   }
 }
 
@@ -667,7 +686,7 @@ nasg_status launch_tma_geom(const EvalArgs& a, cudaStream_t s) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr uint32_t NT = staged_threads<MODE>();
   const TileGeom g = tile_geom<T, P, ANYN>(a.slice_log2, a.n_lobes, NT);
-  const size_t smem = size_t(kStages) * g.stage_bytes + 2 * kStages * sizeof(uint64_t);
+  const size_t smem = size_t(kStages) * g.stage_bytes + kBarrierBytes + (tanh_table<FRAME, T>() ? kTanhBytes : 0u);
   auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS, ANYN, LC>;
   if (const nasg_status e = ensure_smem_limit(reinterpret_cast<const void*>(k), smem); e != NASG_OK) return e;
   int per_sm = 0;

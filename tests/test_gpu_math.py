@@ -49,6 +49,24 @@ def test_tanh_and_sech2(lib):
     assert (rel[keep] <= bound[keep]).all()
 
 
+def test_tanh_table_matches_evaluation_bitwise(lib):
+    """The BF16 kernels' weight table against the evaluation at every finite BF16 value,
+    both signs: tanh bit for bit everywhere (the table's range and the closed forms on
+    either side of it); 1 - tanh^2 bit for bit from 2^-13 on, and below it the closed
+    form 1 - x^2, within 8 ulps of the evaluation and exact to rounding."""
+    bits = np.arange(0, 0x7f80, dtype=np.uint32)             # every finite BF16 magnitude
+    bits = np.concatenate([bits, bits | 0x8000])
+    x = (bits << 16).view(np.float32)
+    t_eval, s_eval = _run(lib, 1, x)
+    t_tab, s_tab = _run(lib, 3, x)
+    assert np.array_equal(t_eval.view(np.uint32), t_tab.view(np.uint32))
+    big = np.abs(x) >= 2.0 ** -13
+    assert np.array_equal(s_eval[big].view(np.uint32), s_tab[big].view(np.uint32))
+    x64 = x[~big].astype(np.float64)
+    assert np.array_equal(s_tab[~big], (1.0 - x64 * x64).astype(np.float32))
+    assert _ulp_err(s_eval[~big], 1.0 - x64 * x64).max() <= 8.0
+
+
 def test_sincos(lib):
     rng = np.random.default_rng(3)
     x = np.concatenate([rng.uniform(-4, 4, 200000), rng.uniform(-25, 25, 200000),
