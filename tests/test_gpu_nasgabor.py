@@ -615,19 +615,24 @@ def test_staged_path_accumulate(lib, bf16, n, L):
     assert max(rel_l2(fg[p], bg[p]) for p in range(fg.shape[0])) < 1e-6
 
 
-@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("pinned", ["all", "none", "some"])
 @pytest.mark.parametrize("n,L,chunk,bf16", [(100_003, 8, 16384, True), (4096, 4, 1024, False), (777, 3, 64, True),
                                             (5000, 8, 8, False)])
 def test_host_resident_fused_matches_device_fused(lib, n, L, chunk, bf16, pinned):
     """Host arrays give the device-resident fused pass's results: page-locked ones read
-    and written in place by the kernel, pageable ones streamed in chunks through the
-    device (copies overlapping the kernel)."""
+    and written in place by the kernel; when any array is pageable, all of them are
+    streamed in chunks through the device (copies overlapping the kernel)."""
     import torch
     w = inputs.point_cloud_workload(n, L, 60 + L)
     params, c0, _, _ = _prepare(w, bf16)
     means, g_rgb = _dev(w.means), _dev(w.g_rgb)
     ref = lib.nasgabor_fused_fwd_bwd(params, c0, means, w.cam, g_rgb, L)
-    pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
+    count = iter(range(8))
+
+    def pin(t):   # "some": every other array page-locked
+        j = next(count)
+        return t.pin_memory() if pinned == "all" or (pinned == "some" and j % 2 == 0) else t
+
     hp = [pin(params.cpu()), pin(c0.cpu()), pin(means.cpu()), pin(g_rgb.cpu())]
     out = tuple(pin(torch.empty(t.shape, dtype=torch.float32)) for t in ref)
     hf = lib.HostFused(n, L, params.dtype, chunk=chunk)
