@@ -132,6 +132,52 @@ def test_batched_oracle_parity(lib):
         assert rel_l2(sc["g_means"].cpu().numpy(), r_mu) <= 1e-4
 
 
+def test_batched_full_workload_sampled(lib):
+    """The 32-scene batched workload at full size (28M primitives, 2.0e8 BF16 lobes) in
+    the launch configuration the benchmark times (autotuned, replayed from a captured
+    CUDA graph); the oracle checks a seeded sample of 48 primitives of every scene:
+    colours within the usual bound, gradients within relative L2 1e-4 per plane over
+    the sample."""
+    import torch
+    sizes = inputs.batched_scene_sizes(32, 1004)
+    scenes = [inputs.device_point_cloud(n, L, 1004 * 100 + j, "cuda", torch.bfloat16)
+              for j, (n, L) in enumerate(sizes)]
+    b = lib.Batch(scenes)
+    b.autotune(reps=1)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            b.run(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize()
+    lib.nasg_device_status()
+    for j, ((n, L), sc) in enumerate(zip(sizes, scenes)):
+        sample = inputs.subsample_indices(n, 48, 31 + j)
+        lobes = (sample[:, None] * L + np.arange(L)).reshape(-1)
+        ti = torch.from_numpy(sample).cuda()
+        tl = torch.from_numpy(lobes).cuda()
+        pq = sc["params"][:, tl].float().cpu().numpy()
+        cq = sc["c0"][:, ti].float().cpu().numpy()
+        ms = sc["means"][ti].cpu().numpy()
+        gs = sc["g_rgb"][ti].cpu().numpy()
+        cam = np.asarray(sc["cam"], np.float32)
+
+        def fwd(p_, c_, m_, cm_):
+            return ong.forward(p_, c_, m_, cm_, L)
+
+        ref, nu = sensitivity_floor(fwd, (pq, cq, ms, cam), (0, 1, 2, 3))
+        rep = colour_report(sc["rgb"][ti].cpu().numpy(), ref, nu, 1e-5)
+        assert rep["violations"] == 0, (j, rep)
+        r_p, r_c0, r_mu = ong.backward(pq, cq, ms, cam, gs, L)
+        gp = sc["g_params"][:, tl].cpu().numpy()
+        assert max(rel_l2(gp[p], r_p[p]) for p in range(gp.shape[0])) <= 1e-4, j
+        np.testing.assert_array_equal(sc["g_c0"][:, ti].cpu().numpy(), r_c0.astype(np.float32))
+        assert rel_l2(sc["g_means"][ti].cpu().numpy(), r_mu) <= 1e-4, j
+
+
 def test_batched_cuda_graph_replay_and_autotune(lib):
     import torch
     scenes = _scenes([(20000, 8), (3000, 16), (7000, 4), (50, 8)], 600, True)
