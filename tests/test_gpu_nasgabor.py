@@ -4,7 +4,9 @@ Colours: |c_gpu - c_oracle| <= 1e-5 + 4 nu per output (nu = oracle sensitivity
 floor, tests/_parity.py), for FP32 parameters and for BF16 parameters alike (the
 oracle is fed the dequantised values; the arithmetic is FP32 in both).
 Gradients: relative L2 error <= 1e-4 per parameter plane, for c0 and for the
-means; at and near the poles element by element (grad_report).
+means, and element by element (grad_report): |dg| <= 1e-4 |g| + 4 nu + f +
+1e-12 max|g of the plane|, f the FP32 rounding floor of the gradients that are
+sums of terms of opposite sign (_chain_floor).
 """
 import math
 
@@ -71,6 +73,20 @@ def _check_backward(lib, w, bf16, norm="approx", act="raw", family="nasgabor"):
     assert max(errs) <= GRAD_TOL, errs
     np.testing.assert_array_equal(g_c0.cpu().numpy(), w.g_rgb.T)
     assert rel_l2(g_mu.cpu().numpy(), r_mu) <= GRAD_TOL
+    # element by element: |dg| <= 1e-4 |g| + 4 nu + the projection floor + 1e-12 max|g of the plane|
+    P, n, L = g_p.shape[0], w.n, w.n_lobes
+
+    def bwd(p_, c_, m_, cm_):
+        gp_, _, gm_ = ong.backward(p_, c_, m_, cm_, w.g_rgb, L, w.frame_mode, norm, act, family)
+        return np.concatenate([gp_.ravel(), gm_.ravel()])
+
+    ref, nu = sensitivity_floor(bwd, (p_np, c0_np, w.means, w.cam), (0, 1, 2, 3))
+    groups = np.concatenate([np.repeat(np.arange(P), n * L), np.full(3 * n, P)])
+    scale = np.array([np.abs(ref[groups == g]).max() for g in range(P + 1)])
+    floor = _chain_floor(p_np, w.means, w.cam, w.g_rgb, L, w.frame_mode, norm, act, family)
+    got = np.concatenate([g_p.ravel(), g_mu.cpu().numpy().ravel()])
+    rep = grad_report(got, ref, nu, atol=1e-12 * scale[groups] + floor)
+    assert rep["violations"] == 0, rep
     return errs
 
 
@@ -100,10 +116,10 @@ EPS32 = 2.0 ** -24
 
 def _chain_floor(params, means, cam, g_rgb, L, frame="quat", norm="approx", act_mode="raw", family="nasgabor",
                  roundings=8, frame_planes=True):
-    """Per-element rounding floor of the gradients that end in a projection: the
-    frame planes (dLoss/dx, dLoss/dz through the frame Jacobian) and the means
-    (dLoss/dd through I - d d^T). Each is a sum whose terms can be many orders larger
-    than the result (near a pole dLoss/dd is almost radial: at 1e-5 rad from the
+    """Per-element rounding floor of the gradients that are sums of terms of opposite sign:
+    the frame planes (dLoss/dx, dLoss/dz through the frame Jacobian), the means
+    (dLoss/dd through I - d d^T) and the carrier's k and phi planes. Each is a sum whose
+    terms can be many orders larger than the result (near a pole dLoss/dd is almost radial: at 1e-5 rad from the
     anti-pole ~1e7 against a tangential part ~1), and FP32 forms every term to a few
     roundings of its own magnitude, so the error a correct FP32 evaluation makes is
     about `roundings` * 2^-24 * (sum of the terms' magnitudes), which the oracle's
@@ -116,7 +132,7 @@ def _chain_floor(params, means, cam, g_rgb, L, frame="quat", norm="approx", act_
     act = ong.activate(ong.split_planes(p64, n, L, frame, variant), frame, act_mode, variant)
     x, z = ong._frames(act, frame)
     d, dist = ong.view_directions(means, cam)
-    _, par = ong.lobe(d[:, None, :], x, z, act["lam"], act["a"], act["k"], norm, need_grad=True,
+    G, par = ong.lobe(d[:, None, :], x, z, act["lam"], act["a"], act["k"], norm, need_grad=True,
                       phi=act.get("phi"))
     g_G = np.abs(np.sum(np.asarray(g_rgb, np.float64)[:, None, :] * act["w"], axis=-1))   # (N, L)
     mx, mz = np.linalg.norm(par["x"], axis=-1), np.linalg.norm(par["z"], axis=-1)
@@ -124,6 +140,16 @@ def _chain_floor(params, means, cam, g_rgb, L, frame="quat", norm="approx", act_
     tol = roundings * EPS32
     F = (4 if frame == "quat" else 3) if frame_planes else 0
     floor = np.zeros(p64.shape)
+    if frame == "quat" and frame_planes:
+        # the kernel's dLoss/dq = (2/|q|^2)[gv d.(dx~/dq)/2 + gu d.(dz~/dq)/2 - q (gv v + gu u)]
+        # (x~, z~ the quadratic forms of the axes): every term is at most (|gu| + |gv|) |q| in
+        # size, and a component can be far smaller than them (the sum is tangent to q)
+        gu = g_G * np.sum(par["z"] * d[:, None, :], axis=-1)
+        gv = g_G * np.sum(par["x"] * d[:, None, :], axis=-1)
+        qn = np.sqrt(np.sum(np.asarray(act["q"], np.float64) ** 2, axis=-1))
+        term = (tol * 4.0 * (np.abs(gu) + np.abs(gv)) / qn).reshape(-1)
+        for f in range(4):
+            floor[f] = term
     for f in range(F):
         h = 1e-6 * np.maximum(1.0, np.abs(p64[f]))
         fr = []
@@ -135,7 +161,25 @@ def _chain_floor(params, means, cam, g_rgb, L, frame="quat", norm="approx", act_
         hh = (2.0 * h).reshape(n, L)
         jx = np.linalg.norm(fr[0][0] - fr[1][0], axis=-1) / hh
         jz = np.linalg.norm(fr[0][1] - fr[1][1], axis=-1) / hh
-        floor[f] = (tol * g_G * (mx * jx + mz * jz)).reshape(-1)
+        floor[f] = np.maximum(floor[f], (tol * g_G * (mx * jx + mz * jz)).reshape(-1))
+    # the carrier's k and phi partials, dG/dk = G d ln C^-1/dk - C^-1 p E sin(k v + phi) v/2 and
+    # dG/dphi = G d ln C^-1/dphi - C^-1 p E sin(k v + phi)/2: where k v is small the two terms
+    # nearly cancel (the normalisation takes out what the carrier's shift puts in)
+    fields = ong.variant_fields(variant)
+    F0 = 4 if frame == "quat" else 3
+    if "k" in fields:
+        phi = act.get("phi")
+        arg = act["k"] * np.sum(d[:, None, :] * x, axis=-1) + (0.0 if phi is None else phi)
+        hh = (1.0 + np.cos(arg)) / 2.0
+        cpe = np.where(hh > 0.0, G / np.where(hh > 0.0, hh, 1.0), 0.0)
+        sn = np.sin(arg)
+        vv = np.sum(d[:, None, :] * x, axis=-1)
+        slopes = ong.activation_slopes(act, act_mode)
+        t2 = -0.5 * cpe * sn * vv
+        floor[F0 + fields.index("k")] = (tol * g_G * np.abs(slopes["k"]) * (np.abs(par["k"] - t2) + np.abs(t2))).reshape(-1)
+        if "phi" in fields:
+            t2 = -0.5 * cpe * sn
+            floor[F0 + fields.index("phi")] = (tol * g_G * (np.abs(par["phi"] - t2) + np.abs(t2))).reshape(-1)
     # component c of (I - d d^T) g_d: the c-th terms of g_d and (g_d . d) d_c
     terms_c = np.sum(np.abs(g_G[..., None] * par["d"]), axis=1)                          # (N, 3)
     fm = tol * (terms_c + np.sum(g_G * md, axis=1)[:, None] * np.abs(d)) / dist[:, None]
