@@ -16,6 +16,8 @@ import math
 
 import numpy as np
 
+from oracle import nasgabor as ong
+
 
 def ulp_perturb(x, rng, ulps=1):
     """Every element moved by `ulps` FP32 ulps up or down (random direction)."""
@@ -101,3 +103,78 @@ def rel_l2(a, b):
     if den == 0.0:
         return float(np.linalg.norm(a))
     return float(np.linalg.norm(a - b) / den)
+
+
+EPS32 = 2.0 ** -24
+
+
+def chain_floor(params, means, cam, g_rgb, L, frame="quat", norm="approx", act_mode="raw", family="nasgabor",
+                 roundings=8, frame_planes=True):
+    """Per-element rounding floor of the gradients that are sums of terms of opposite sign:
+    the frame planes (dLoss/dx, dLoss/dz through the frame Jacobian), the means
+    (dLoss/dd through I - d d^T) and the carrier's k and phi planes. Each is a sum whose
+    terms can be many orders larger than the result (near a pole dLoss/dd is almost radial: at 1e-5 rad from the
+    anti-pole ~1e7 against a tangential part ~1), and FP32 forms every term to a few
+    roundings of its own magnitude, so the error a correct FP32 evaluation makes is
+    about `roundings` * 2^-24 * (sum of the terms' magnitudes), which the oracle's
+    input sensitivity (a smooth function of the inputs) does not see. Returned in the
+    layout of grad_report's inputs: the P parameter planes (N*L each; 0 outside the
+    frame planes, and everywhere without `frame_planes`) then the means (3 N)."""
+    n = means.shape[0]
+    variant = family
+    p64 = np.asarray(params, np.float64)
+    act = ong.activate(ong.split_planes(p64, n, L, frame, variant), frame, act_mode, variant)
+    x, z = ong._frames(act, frame)
+    d, dist = ong.view_directions(means, cam)
+    G, par = ong.lobe(d[:, None, :], x, z, act["lam"], act["a"], act["k"], norm, need_grad=True,
+                      phi=act.get("phi"))
+    g_G = np.abs(np.sum(np.asarray(g_rgb, np.float64)[:, None, :] * act["w"], axis=-1))   # (N, L)
+    mx, mz = np.linalg.norm(par["x"], axis=-1), np.linalg.norm(par["z"], axis=-1)
+    md = np.linalg.norm(par["d"], axis=-1)
+    tol = roundings * EPS32
+    F = (4 if frame == "quat" else 3) if frame_planes else 0
+    floor = np.zeros(p64.shape)
+    if frame == "quat" and frame_planes:
+        # the kernel's dLoss/dq = (2/|q|^2)[gv d.(dx~/dq)/2 + gu d.(dz~/dq)/2 - q (gv v + gu u)]
+        # (x~, z~ the quadratic forms of the axes): every term is at most (|gu| + |gv|) |q| in
+        # size, and a component can be far smaller than them (the sum is tangent to q)
+        gu = g_G * np.sum(par["z"] * d[:, None, :], axis=-1)
+        gv = g_G * np.sum(par["x"] * d[:, None, :], axis=-1)
+        qn = np.sqrt(np.sum(np.asarray(act["q"], np.float64) ** 2, axis=-1))
+        term = (tol * 4.0 * (np.abs(gu) + np.abs(gv)) / qn).reshape(-1)
+        for f in range(4):
+            floor[f] = term
+    for f in range(F):
+        h = 1e-6 * np.maximum(1.0, np.abs(p64[f]))
+        fr = []
+        for sgn in (1.0, -1.0):
+            pp = p64.copy()
+            pp[f] += sgn * h
+            fr.append(ong._frames(ong.activate(ong.split_planes(pp, n, L, frame, variant), frame, act_mode,
+                                               variant), frame))
+        hh = (2.0 * h).reshape(n, L)
+        jx = np.linalg.norm(fr[0][0] - fr[1][0], axis=-1) / hh
+        jz = np.linalg.norm(fr[0][1] - fr[1][1], axis=-1) / hh
+        floor[f] = np.maximum(floor[f], (tol * g_G * (mx * jx + mz * jz)).reshape(-1))
+    # the carrier's k and phi partials, dG/dk = G d ln C^-1/dk - C^-1 p E sin(k v + phi) v/2 and
+    # dG/dphi = G d ln C^-1/dphi - C^-1 p E sin(k v + phi)/2: where k v is small the two terms
+    # nearly cancel (the normalisation takes out what the carrier's shift puts in)
+    fields = ong.variant_fields(variant)
+    F0 = 4 if frame == "quat" else 3
+    if "k" in fields:
+        phi = act.get("phi")
+        arg = act["k"] * np.sum(d[:, None, :] * x, axis=-1) + (0.0 if phi is None else phi)
+        hh = (1.0 + np.cos(arg)) / 2.0
+        cpe = np.where(hh > 0.0, G / np.where(hh > 0.0, hh, 1.0), 0.0)
+        sn = np.sin(arg)
+        vv = np.sum(d[:, None, :] * x, axis=-1)
+        slopes = ong.activation_slopes(act, act_mode)
+        t2 = -0.5 * cpe * sn * vv
+        floor[F0 + fields.index("k")] = (tol * g_G * np.abs(slopes["k"]) * (np.abs(par["k"] - t2) + np.abs(t2))).reshape(-1)
+        if "phi" in fields:
+            t2 = -0.5 * cpe * sn
+            floor[F0 + fields.index("phi")] = (tol * g_G * (np.abs(par["phi"] - t2) + np.abs(t2))).reshape(-1)
+    # component c of (I - d d^T) g_d: the c-th terms of g_d and (g_d . d) d_c
+    terms_c = np.sum(np.abs(g_G[..., None] * par["d"]), axis=1)                          # (N, 3)
+    fm = tol * (terms_c + np.sum(g_G * md, axis=1)[:, None] * np.abs(d)) / dist[:, None]
+    return np.concatenate([floor.ravel(), fm.ravel()])

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import nasgabor as ong
 from paper_2606_09794_gb300 import inputs
-from tests._parity import colour_report, rel_l2, sensitivity_floor
+from tests._parity import chain_floor, colour_report, grad_report, rel_l2, sensitivity_floor
 
 pytestmark = pytest.mark.gpu
 
@@ -108,6 +108,23 @@ def test_batched_exact_normalisation(lib):
     _compare_with_single(lib, scenes, norm="exact")
 
 
+def _grads_elementwise(gp, gm, pq, cq, means, cam, g_rgb, L):
+    """Every gradient element against the oracle (as the single-scene parity tests):
+    |dg| <= 1e-4 |g| + 4 nu + the FP32 floor of the sums of terms of opposite sign."""
+    P, n = gp.shape[0], means.shape[0]
+
+    def bwd(p_, c_, m_, cm_):
+        r_p, _, r_mu = ong.backward(p_, c_, m_, cm_, g_rgb, L)
+        return np.concatenate([r_p.ravel(), r_mu.ravel()])
+
+    ref, nu = sensitivity_floor(bwd, (pq, cq, means, cam), (0, 1, 2, 3))
+    groups = np.concatenate([np.repeat(np.arange(P), n * L), np.full(3 * n, P)])
+    scale = np.array([np.abs(ref[groups == g]).max() for g in range(P + 1)])
+    floor = chain_floor(pq, means, cam, g_rgb, L)
+    got = np.concatenate([np.asarray(gp).ravel(), np.asarray(gm).ravel()])
+    return grad_report(got, ref, nu, atol=1e-12 * scale[groups] + floor)
+
+
 def test_batched_oracle_parity(lib):
     import torch
     scenes = _scenes([(2000, 8), (900, 16), (1500, 4)], 500, True)
@@ -130,6 +147,8 @@ def test_batched_oracle_parity(lib):
         gp = sc["g_params"].cpu().numpy()
         assert max(rel_l2(gp[p], r_p[p]) for p in range(10)) <= 1e-4
         assert rel_l2(sc["g_means"].cpu().numpy(), r_mu) <= 1e-4
+        rep = _grads_elementwise(gp, sc["g_means"].cpu().numpy(), pq, cq, w.means, cam, w.g_rgb, L)
+        assert rep["violations"] == 0, rep
 
 
 def test_batched_full_workload_sampled(lib):
@@ -137,7 +156,7 @@ def test_batched_full_workload_sampled(lib):
     the launch configuration the benchmark times (autotuned, replayed from a captured
     CUDA graph); the oracle checks a seeded sample of 48 primitives of every scene:
     colours within the usual bound, gradients within relative L2 1e-4 per plane over
-    the sample."""
+    the sample and element by element."""
     import torch
     sizes = inputs.batched_scene_sizes(32, 1004)
     scenes = [inputs.device_point_cloud(n, L, 1004 * 100 + j, "cuda", torch.bfloat16)
@@ -173,9 +192,12 @@ def test_batched_full_workload_sampled(lib):
         assert rep["violations"] == 0, (j, rep)
         r_p, r_c0, r_mu = ong.backward(pq, cq, ms, cam, gs, L)
         gp = sc["g_params"][:, tl].cpu().numpy()
+        gm = sc["g_means"][ti].cpu().numpy()
         assert max(rel_l2(gp[p], r_p[p]) for p in range(gp.shape[0])) <= 1e-4, j
         np.testing.assert_array_equal(sc["g_c0"][:, ti].cpu().numpy(), r_c0.astype(np.float32))
-        assert rel_l2(sc["g_means"][ti].cpu().numpy(), r_mu) <= 1e-4, j
+        assert rel_l2(gm, r_mu) <= 1e-4, j
+        rep = _grads_elementwise(gp, gm, pq, cq, ms, cam, gs, L)
+        assert rep["violations"] == 0, (j, rep)
 
 
 def test_batched_cuda_graph_replay_and_autotune(lib):

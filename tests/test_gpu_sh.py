@@ -4,9 +4,35 @@ import pytest
 
 from oracle import sh as osh
 from paper_2606_09794_gb300 import inputs
-from tests._parity import colour_report, rel_l2, sensitivity_floor
+from tests._parity import colour_report, grad_report, rel_l2, sensitivity_floor
 
 pytestmark = pytest.mark.gpu
+
+
+def _grad_elementwise(gc, gm, coeffs, means, cam, g, degree):
+    """Every gradient element against the oracle: |dg| <= 1e-4 |g| + 4 nu + f, f for the
+    means the FP32 rounding floor of dLoss/dd = sum_j (dLoss/dY_j) grad Y_j projected by
+    I - d d^T: the kernel differentiates the basis polynomials in Cartesian form, whose
+    gradient adds to the tangent one a radial part of about l Y_j for a degree-l term, so
+    f = 16 x 2^-24 x (the terms' magnitudes + their radial parts along d_c) / |mu - cam|."""
+    def bwd(c, m, cm):
+        r_c, r_m = osh.backward(c, m, cm, g, degree)
+        return np.concatenate([r_c.ravel(), r_m.ravel()])
+
+    ref, nu = sensitivity_floor(bwd, (coeffs, means, cam), (0, 1, 2))
+    r = np.asarray(means, np.float64) - np.asarray(cam, np.float64)
+    dist = np.linalg.norm(r, axis=-1)
+    d = r / dist[:, None]
+    Y, gY = osh.basis(d, degree, need_grad=True)
+    wj = np.abs(np.einsum("jcn,nc->nj", np.asarray(coeffs, np.float64), np.asarray(g, np.float64)))
+    terms = np.einsum("nj,njk->nk", wj, np.abs(gY))
+    ls = np.floor(np.sqrt(np.arange(Y.shape[-1])))                 # degree of basis function j
+    radial = np.sum(wj * ls * np.abs(Y), axis=-1, keepdims=True)
+    fm = 16 * 2.0 ** -24 * (terms + (np.linalg.norm(terms, axis=-1, keepdims=True) + radial) * np.abs(d)) / dist[:, None]
+    nc = np.asarray(coeffs).size
+    atol = np.concatenate([np.full(nc, 1e-12 * np.abs(ref[:nc]).max()), fm.ravel() + 1e-12 * np.abs(ref[nc:]).max()])
+    got = np.concatenate([np.asarray(gc, np.float64).ravel(), np.asarray(gm, np.float64).ravel()])
+    return grad_report(got, ref, nu, atol=atol)
 
 
 @pytest.mark.parametrize("degree,n", [(0, 100), (1, 257), (2, 1000), (3, 4099), (3, 1)])
@@ -35,6 +61,8 @@ def test_sh_parity(lib, degree, n):
         assert rel_l2(gm.cpu().numpy(), r_m) <= 1e-4
     else:
         assert np.abs(gm.cpu().numpy()).max() < 1e-6
+    rep = _grad_elementwise(gc.cpu().numpy(), gm.cpu().numpy(), coeffs, means, cam, g, degree)
+    assert rep["violations"] == 0, rep
 
 
 def test_sh_full_size_sampled(lib):
@@ -56,6 +84,9 @@ def test_sh_full_size_sampled(lib):
     r_c, r_m = osh.backward(cs, w.means[sample], w.cam, w.g_rgb[sample])
     assert rel_l2(gc.cpu().numpy()[:, :, sample], r_c) <= 1e-6
     assert rel_l2(gm.cpu().numpy()[sample], r_m) <= 1e-4
+    rep = _grad_elementwise(gc.cpu().numpy()[:, :, sample], gm.cpu().numpy()[sample], cs, w.means[sample], w.cam,
+                            w.g_rgb[sample], 3)
+    assert rep["violations"] == 0, rep
 
 
 def test_sh_autograd(lib):
