@@ -578,13 +578,26 @@ __device__ __forceinline__ V lobe_at(const V* d, const V* x, const V* z, V lam, 
   const M anti = vand(pole, vnot(up));
   const V inv_s2 = vsel(pole, 0.f, vrcp(s2));
   // 1 - u and 1 + u, each from s2 on the side where it is small
-  const V one_m_u = 1.f - u, one_p_u = 1.f + u;
-  const V rd = vrcp(vsel(up, one_p_u, one_m_u));
-  const V omu = vsel(up, s2 * rd, one_m_u);
-  const V opu = vsel(up, one_p_u, s2 * rd);
-  const V inv_opu = vsel(up, rd, one_m_u * inv_s2);  // 1/(1+u) = 1/(2 kappa)
-  const V t = -0.5f * omu;
-  const V kap = vsel(up, 1.f + t, 0.5f * opu);
+  V t, kap, inv_opu;
+  if constexpr (F::HAS_A) {
+    // 1 + |u| and 1 - |u| = s2/(1 + |u|); t = kappa - 1 = -(1 - u)/2 is only read where
+    // kappa >= 3/4 (the series of ln kappa), i.e. where u > 0 and 1 - u = 1 - |u|
+    const V big = 1.f + vabs(u);
+    const V rb = vrcp(big);
+    const V small = s2 * rb;
+    const V opu = vsel(up, big, small);
+    inv_opu = vsel(up, rb, big * inv_s2);  // 1/(1+u) = 1/(2 kappa)
+    t = -0.5f * small;
+    kap = 0.5f * opu;
+  } else {
+    const V one_m_u = 1.f - u, one_p_u = 1.f + u;
+    const V rd = vrcp(vsel(up, one_p_u, one_m_u));
+    const V omu = vsel(up, s2 * rd, one_m_u);
+    const V opu = vsel(up, one_p_u, s2 * rd);
+    inv_opu = vsel(up, rd, one_m_u * inv_s2);
+    t = -0.5f * omu;
+    kap = vsel(up, 1.f + t, 0.5f * opu);
+  }
   // without anisotropy (SG): tau = 0, E = 1, E kappa - 1 = kappa - 1 = t exactly
   const V ln_k = F::HAS_A ? vsel(anti, 0.f, vlnkappa(t, vmax(kap, kFltMin))) : vconst<V>(0.f);  // ln kappa
   const V tau = F::HAS_A ? a * v * v * inv_s2 : vconst<V>(0.f);
