@@ -144,6 +144,10 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
         for (int p = 0; p < 10; ++p) raw[p] = p2(p == 0 ? 1.f : 0.f);
       }
       fit_lobes<true, EXACT>(raw, s.identity != 0, s.normalised != 0, stu);
+      if (!mine) {  // a lane past the last lobe pair adds nothing to the colour
+#pragma unroll
+        for (int c = 0; c < 3; ++c) stu.w[c] = p2(0.f);
+      }
       if (ok) load_pair(s.teacher, s.n, lt, i, 2 * tp, false, raw);
       else {
 #pragma unroll
@@ -151,12 +155,11 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
       }
       fit_lobes<false, EXACT>(raw, s.identity != 0, s.normalised != 0, tea);
     }
-    float c0s[3], c0t[3];
+    float dc0[3];  // student minus teacher diffuse colour
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float cv = ok ? s.c0[c * s.n + i] : 0.f;
-      c0s[c] = s.quantize ? fit_bf16_rne(cv) : cv;
-      c0t[c] = ok ? s.tc0[c * s.n + i] : 0.f;
+      dc0[c] = (s.quantize ? fit_bf16_rne(cv) : cv) - (ok ? s.tc0[c * s.n + i] : 0.f);
     }
     const P2 zero = p2(0.f);
     P2 acc_lam = zero, acc_a = zero, acc_k = zero;
@@ -195,19 +198,21 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const P2 wg = stu.w[c] * Gs;
-          col[c] = mine ? wg.v.x + wg.v.y : 0.f;
+          col[c] = wg.v.x + wg.v.y;
         }
         for (int o = S >> 1; o >= 1; o >>= 1) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) col[c] += __shfl_xor_sync(0xffffffffu, col[c], o);
         }
+        // the residual r = student - teacher colour; the accumulators sum r-weighted terms and
+        // are scaled once after the loop by d(mean over directions and channels)/dc = 2/(3 D)
         float gc[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float r = (c0s[c] + col[c]) - (c0t[c] + tc[c]);
+          const float r = (col[c] - tc[c]) + dc0[c];
           if (ok && g == 0) sq_sum = fmaf(r, r, sq_sum);
-          gc[c] = inv3d * r;  // d(per-primitive mean over directions and channels)/dc
-          acc_c0[c] += gc[c];
+          gc[c] = r;
+          acc_c0[c] += r;
         }
         const P2 gG = vfma(p2(gc[0]), stu.w[0], vfma(p2(gc[1]), stu.w[1], p2(gc[2]) * stu.w[2]));
 #pragma unroll
@@ -224,6 +229,19 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
       }
     }
     // ---- chain to the raw parameters and take the Adam step ----
+    {
+      const P2 sc = p2(inv3d);
+      acc_lam = acc_lam * sc;
+      acc_a = acc_a * sc;
+      acc_k = acc_k * sc;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc_w[c] = acc_w[c] * sc;
+        acc_gx[c] = acc_gx[c] * sc;
+        acc_gz[c] = acc_gz[c] * sc;
+        acc_c0[c] *= inv3d;
+      }
+    }
     if (mine) {
       const int64_t NL = s.n * ls;
       const int64_t off = i * ls + l0;
