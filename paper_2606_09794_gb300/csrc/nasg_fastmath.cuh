@@ -89,15 +89,18 @@ __device__ __forceinline__ void vtanh(V x, V& t, V& sech2) {
   sech2 = 4.f * ex * (inv * inv);           // 1 - tanh^2 = 4 e/(1 + e)^2
 }
 
-// Weight activation for BF16-stored raw values by table: the entries are vtanh of
+// Weight activation for BF16-stored raw values by table: the entries hold vtanh of
 // every BF16 magnitude in [2^-13, 64) (2432 values), formed on the device by vtanh
 // itself, so there a lookup returns the bits of the evaluation. Outside, closed forms:
 // from 64 on t = +-1 and 1 - tanh^2 = 0 (what vtanh gives there); below 2^-13 t = x
-// (what the series gives) and 1 - tanh^2 = 1 - x^2 (within a few ulps of vtanh's
-// 4 e/(1 + e)^2, and exact to rounding). An entry (A, B, C, D) gives
-// t = B x + copysign(A, x) and 1 - tanh^2 = D x^2 + C: (tanh|x_j|, 0, sech^2 x_j, 0) in
-// the range, (1, 0, 0, 0) past it, (0, 1, 1, -1) below it. Finite inputs only (an
-// infinite raw value gives NaN, where the evaluation gives +-1).
+// (what the series gives) and 1 - tanh^2 = 1 (1 - x^2 rounded to FP32: x^2 < 2^-26 is
+// under half the spacing of the floats below 1; vtanh's 4 e/(1 + e)^2 is within a
+// few ulps of it). Layout: entry 0 the closed form below 2^-13, entries 1..2432 the
+// magnitudes from 2^-13 up, entry 2433 the closed form from 64 on, so that an index is
+// the magnitude bits clamped once on each side. An entry (A, B, C, 0) gives
+// t = B x + copysign(A, x) and 1 - tanh^2 = C: (tanh|x_j|, 0, sech^2 x_j, 0) in the
+// range, (1, 0, 0, 0) past it, (0, 1, 1, 0) below it. Finite inputs only (an infinite
+// raw value gives NaN, where the evaluation gives +-1).
 constexpr uint32_t kTanhLo = 0x3900u;                // BF16 magnitude bits of 2^-13
 constexpr uint32_t kTanhHi = 0x4280u;                // BF16 magnitude bits of 64
 constexpr uint32_t kTanhN = kTanhHi - kTanhLo;       // 2432 entries
@@ -108,14 +111,14 @@ constexpr uint32_t kTanhBytes = kTanhEntries * 16u;  // 38944 bytes of shared me
 __device__ __forceinline__ void fill_tanh_table(float4* tab) {
   for (uint32_t j = threadIdx.x; j < kTanhEntries; j += blockDim.x) {
     float4 e;
-    if (j < kTanhN) {
+    if (j == 0) {
+      e = make_float4(0.f, 1.f, 1.f, 0.f);
+    } else if (j <= kTanhN) {
       float t, s2;
-      vtanh<float>(__uint_as_float((kTanhLo + j) << 16), t, s2);
+      vtanh<float>(__uint_as_float((kTanhLo + j - 1u) << 16), t, s2);
       e = make_float4(t, 0.f, s2, 0.f);
-    } else if (j == kTanhN) {
-      e = make_float4(1.f, 0.f, 0.f, 0.f);
     } else {
-      e = make_float4(0.f, 1.f, 1.f, -1.f);
+      e = make_float4(1.f, 0.f, 0.f, 0.f);
     }
     tab[j] = e;
   }
@@ -124,10 +127,10 @@ __device__ __forceinline__ void fill_tanh_table(float4* tab) {
 // tanh x and 1 - tanh^2 x for x a BF16 value (in an FP32 register) from the table.
 __device__ __forceinline__ void tanh_lookup(const float4* tab, float x, float& t, float& sech2) {
   const uint32_t m = (__float_as_uint(x) >> 16) & 0x7fffu;
-  const uint32_t j = m < kTanhLo ? kTanhN + 1u : min(m - kTanhLo, kTanhN);
+  const uint32_t j = min(max(m, kTanhLo - 1u) - (kTanhLo - 1u), kTanhN + 1u);
   const float4 e = tab[j];
   t = fmaf(e.y, x, copysignf(e.x, x));
-  sech2 = fmaf(e.w * x, x, e.z);
+  sech2 = e.z;
 }
 __device__ __forceinline__ void tanh_lookup(const float4* tab, P2 x, P2& t, P2& sech2) {
   tanh_lookup(tab, x.v.x, t.v.x, sech2.v.x);
