@@ -337,7 +337,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-paths", action="store_true")
-    ap.add_argument("--case", choices=["paths", "scene_step", "batched", "fit", "frame"], default=None,
+    ap.add_argument("--case", choices=["paths", "scene_step", "batched", "batched_one", "fit", "frame"], default=None,
                     help="run only this secondary measurement (at --case-n primitives) and print its JSON")
     ap.add_argument("--case-n", type=int, default=None)
     ap.add_argument("--case-steps", type=int, default=None)
@@ -504,6 +504,9 @@ def run_case(args):
         res = measure_frame(nb, inputs, dev, stream, **kw)
     elif args.case == "batched":
         res = measure_batched(nb, inputs, dev, stream, peak, **({"n_scenes": args.case_n} if args.case_n else {}))
+    elif args.case == "batched_one":
+        res = measure_batched_one(nb, inputs, dev, stream, peak, **({"n_lobes": args.case_n} if args.case_n else {}),
+                                  **({"reps": args.case_steps} if args.case_steps else {}))
     else:
         if args.case_steps:
             kw["steps"] = args.case_steps
@@ -733,6 +736,51 @@ def measure_batched(nb, inputs, dev, stream, peak, n_scenes=32, seed=1004, reps=
             "total_primitives": int(sum(n for n, _ in sizes)), "total_lobes": b.total_lobes, "us": us,
             "value": b.total_lobes / (us * 1e-6), "unit": UNIT, "tuning": tune, "alg_bytes": alg, "gbs": gbs,
             "frac": gbs / peak}
+
+
+def measure_batched_one(nb, inputs, dev, stream, peak, n_lobes=8, reps=100, seed=77):
+    """The batched launch and the single-scene fused kernel on the same work: one BF16 scene of
+    8e6 / L primitives x L lobes, the batched launch with the staged dynamic schedule (2 blocks
+    per SM, 4 sub-tiles) and with the static one. reps = 0 runs each path once (profiling)."""
+    import torch
+    L = n_lobes
+    n = 8_000_000 // L
+    sc = inputs.device_point_cloud(n, L, seed, dev, torch.bfloat16)
+    sc["n_lobes"] = L
+    b = nb.Batch([dict(sc)], sub_tiles=4)
+    cam = tuple(float(x) for x in sc["cam"])
+    out = (torch.empty((n, 3), device=dev), torch.empty(sc["params"].shape, device=dev),
+           torch.empty((3, n), device=dev), torch.empty((n, 3), device=dev))
+    tunings = {"batched_dynamic": nb.NasgBatchTuning(1, 2, 4, 1), "batched_static": nb.NasgBatchTuning(0, 2, 4, 1)}
+
+    def single():
+        nb.nasgabor_fused_fwd_bwd(sc["params"], sc["c0"], sc["means"], cam, sc["g_rgb"], L, out=out, stream=stream)
+
+    def batched(t):
+        b.tuning = t
+        b.run(stream=stream)
+
+    runs = [("single", single)] + [(k, lambda t=t: batched(t)) for k, t in tunings.items()]
+    res = {"workload": f"one scene, N={n}, L={L}, BF16, fused fwd+bwd: single-scene kernel and the batched launch",
+           "n": n, "n_lobes": L}
+    alg = n * bytes_fused_bf16(L)
+    for name, f in runs:
+        for _ in range(5 if reps else 1):
+            f()
+        if not reps:
+            continue
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            f()
+        e1.record(stream)
+        e1.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / reps
+        res[name] = {"us": us, "frac": alg / (us * 1e-6) / 1e9 / peak}
+    torch.cuda.synchronize(dev)
+    res["same_rgb"] = bool(torch.equal(out[0], b.scenes[0]["rgb"]))
+    return res
 
 
 def fit_lr(nb, inputs, step, steps):
