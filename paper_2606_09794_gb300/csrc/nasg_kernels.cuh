@@ -519,7 +519,10 @@ __device__ __forceinline__ void issue_tile(const EvalArgs& a, const TileGeom& g,
   }
 }
 
-template <int FRAME, typename T, int MODE, int FLAGS, bool ANYN, int LC>
+// KI: items per thread and stage (a tile of KI x THREADS/S primitives; a thread evaluates
+// its KI items of a stage one after the other, which spreads the per-stage work -- the
+// waits, the producer's turn, the tile arithmetic -- over KI items).
+template <int FRAME, typename T, int MODE, int FLAGS, bool ANYN, int LC, int KI = 1>
 __global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(const EvalArgs a) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr bool FWD = (MODE & kFwd) != 0;
@@ -530,7 +533,7 @@ __global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(con
   extern __shared__ __align__(128) unsigned char smem[];
   const int slog = LC ? log2_of(slice_of_lobes(LC)) : a.slice_log2;
   const uint32_t L = LC ? uint32_t(LC) : uint32_t(a.n_lobes);
-  const TileGeom g = tile_geom<T, P, ANYN>(slog, int(L), NT);
+  const TileGeom g = tile_geom<T, P, ANYN>(slog, int(L), NT * KI);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * g.stage_bytes);  // tile landed
   uint64_t* empty = full + kStages;                                             // tile read by all warps
   constexpr bool TAB = tanh_table<FRAME, T>();
@@ -598,34 +601,40 @@ __global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(con
     pending &= ~(1u << s);  // this stage's fill (whoever issued it) has landed
     const uint32_t p0 = tile * g.tp;
     const uint32_t count = min(g.tp, n - p0);
-    RawItem<T, P> r;
-    r.ok = local < count;
-    const uint32_t i = p0 + local;
-    if (r.ok) {
-      const float* mu = reinterpret_cast<const float*>(st + g.off_mu);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) r.mu[c] = mu[3 * local + c];
-      if (BWD) {
-        const float* gc = reinterpret_cast<const float*>(st + g.off_gc);
+    for (int k = 0; k < KI; ++k) {
+      const uint32_t loc = local + uint32_t(k) * (NT >> slog);  // this item's primitive in the tile
+      RawItem<T, P> r;
+      r.ok = loc < count;
+      const uint32_t i = p0 + loc;
+      if (r.ok) {
+        const float* mu = reinterpret_cast<const float*>(st + g.off_mu);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) r.gc[c] = gc[3 * local + c];
+        for (int c = 0; c < 3; ++c) r.mu[c] = mu[3 * loc + c];
+        if (BWD) {
+          const float* gc = reinterpret_cast<const float*>(st + g.off_gc);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) r.gc[c] = gc[3 * loc + c];
+        }
+        if (FWD) {
+          // plain shared-memory reads (load1 uses the global read-only path)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            r.c0[c] = to_float(*reinterpret_cast<const T*>(st + g.off_c0 + c * g.c0_cap + c0_head<T, ANYN>(c, n) +
+                                                           loc * sizeof(T)));
+        }
+        if (uint32_t(l0) < L) {
+#pragma unroll
+          for (int p = 0; p < P; ++p)
+            r.w[p] = *reinterpret_cast<const W*>(st + p * g.plane_bytes + (loc * L + l0) * sizeof(T));
+        }
       }
-      if (FWD) {
-        // plain shared-memory reads (load1 uses the global read-only path)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          r.c0[c] = to_float(*reinterpret_cast<const T*>(st + g.off_c0 + c * g.c0_cap + c0_head<T, ANYN>(c, n) +
-                                                         local * sizeof(T)));
+      if (k == KI - 1) {
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
       }
-      if (uint32_t(l0) < L) {
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-          r.w[p] = *reinterpret_cast<const W*>(st + p * g.plane_bytes + (local * L + l0) * sizeof(T));
-      }
+      eval_item<FRAME, T, uint32_t, MODE, true, FLAGS, LC, TAB>(a, r, i, l0, tab);
     }
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
-    eval_item<FRAME, T, uint32_t, MODE, true, FLAGS, LC, TAB>(a, r, i, l0, tab);
   }
 }
 
@@ -681,13 +690,13 @@ bool tma_eligible(const EvalArgs& a, bool even) {
   return true;
 }
 
-template <int MODE, int FRAME, typename T, int FLAGS, bool ANYN, int LC>
+template <int MODE, int FRAME, typename T, int FLAGS, bool ANYN, int LC, int KI = 1>
 nasg_status launch_tma_geom(const EvalArgs& a, cudaStream_t s) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr uint32_t NT = staged_threads<MODE>();
-  const TileGeom g = tile_geom<T, P, ANYN>(a.slice_log2, a.n_lobes, NT);
+  const TileGeom g = tile_geom<T, P, ANYN>(a.slice_log2, a.n_lobes, NT * KI);
   const size_t smem = size_t(kStages) * g.stage_bytes + kBarrierBytes + (tanh_table<FRAME, T>() ? kTanhBytes : 0u);
-  auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS, ANYN, LC>;
+  auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS, ANYN, LC, KI>;
   if (const nasg_status e = ensure_smem_limit(reinterpret_cast<const void*>(k), smem); e != NASG_OK) return e;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem) != cudaSuccess || per_sm < 1)
@@ -704,8 +713,11 @@ nasg_status launch_tma_geom(const EvalArgs& a, cudaStream_t s) {
 // and the FP32 forward).
 template <int MODE, int FRAME, typename T, int FLAGS, int LC>
 nasg_status launch_tma_lc(const EvalArgs& a, cudaStream_t s) {
-  return a.n % 8 == 0 ? launch_tma_geom<MODE, FRAME, T, FLAGS, false, LC>(a, s)
-                      : launch_tma_geom<MODE, FRAME, T, FLAGS, true, LC>(a, s);
+  // BF16 forward+backward at L = 8 and 16: two items per thread and stage (tiles of 1024
+  // lobes; three stages and the tanh table still fit two blocks per SM)
+  constexpr int KI = (sizeof(T) == 2 && MODE == kFwdBwd && LC >= 8) ? 2 : 1;
+  return a.n % 8 == 0 ? launch_tma_geom<MODE, FRAME, T, FLAGS, false, LC, KI>(a, s)
+                      : launch_tma_geom<MODE, FRAME, T, FLAGS, true, LC, KI>(a, s);
 }
 
 template <int MODE, int FRAME, typename T, int FLAGS>

@@ -41,12 +41,14 @@ static void check_span(const SpanPlan& s, uint64_t off, uint32_t bytes, uint64_t
   ++g_cases;
 }
 
+// Tiles of the staged kernels for a block of `threads` x items per thread (256: the passes with
+// a backward, 384: the forward alone, 512: two items per thread of 256-thread blocks).
 template <typename T, int P, bool ANYN>
-static void check_eval(uint32_t n, uint32_t L) {
+static void check_eval(uint32_t n, uint32_t L, uint32_t threads = 256u) {
   const uint32_t es = sizeof(T);
   int slog = 0;
   while ((1u << slog) < (L + 1) / 2) ++slog;
-  const TileGeom g = tile_geom<T, P, ANYN>(slog, int(L));
+  const TileGeom g = tile_geom<T, P, ANYN>(slog, int(L), threads);
   CHECK(g.off_mu % 16 == 0 && g.off_gc % 16 == 0 && g.off_c0 % 16 == 0 && g.c0_cap % 16 == 0 &&
             g.stage_bytes % 128 == 0 && g.off_c0 + 3 * g.c0_cap <= g.stage_bytes,
         "layout L=%u", L);
@@ -129,11 +131,18 @@ int main() {
         check_eval<F16, 9, true>(n, L);
         check_eval<F16, 11, true>(n, L);
         if (n % 8 == 0) check_eval<F16, 10, false>(n, L);
+        if (L >= 8) {
+          check_eval<F16, 10, true>(n, L, 512u);
+          check_eval<F16, 9, true>(n, L, 512u);
+          if (n % 8 == 0) check_eval<F16, 10, false>(n, L, 512u);
+        }
       }
       if ((uint64_t(n) * L * 4) % 16 == 0) {
         check_eval<float, 10, true>(n, L);
         check_eval<float, 8, true>(n, L);
         if (n % 8 == 0) check_eval<float, 10, false>(n, L);
+        check_eval<float, 10, true>(n, L, 384u);
+        if (n % 8 == 0) check_eval<float, 10, false>(n, L, 384u);
       }
       // batched scenes are staged when L is even and N L sizeof(T) % 16 == 0
       if ((uint64_t(n) * L * 2) % 16 == 0) check_batch<F16, 10>(n, L);
