@@ -6,16 +6,17 @@
 // caller workspace; the run call is one kernel launch (preceded, for dynamic
 // scheduling, by a 4-byte counter reset), so a stream capture of it records a
 // CUDA graph that can be replayed. Work items are tiles of k sub-tiles of
-// 256/S primitives of one scene (S = lanes per primitive for that scene's L).
+// I x 256/S primitives of one scene (S = lanes per primitive for that scene's L,
+// I = unit_items: a thread evaluates I items of each sub-tile one after the other).
 // Blocks take tiles round-robin (static) or from an atomic counter (dynamic),
 // look the scene up in the shared-memory copy of the table, and evaluate the
 // tile with the lobe-pair lanes of the single-scene kernels, fetching each
 // lane's next sub-tile item before computing the current one. No thread waits
 // on another block. A staged variant moves each sub-tile's parameter spans,
 // means, upstream gradients and diffuse colours into shared memory with bulk
-// copies (span plans for any N), four (BF16) or three (FP32) sub-tiles ahead
-// (one elected producer thread, full/empty mbarriers, every wait bounded), for
-// the scenes whose planes allow it, and loads the rest directly; its copy of the
+// copies (span plans for any N), three sub-tiles ahead (one elected producer
+// thread, full/empty mbarriers, every wait bounded), for the scenes whose planes
+// allow it (L >= 4), and loads the rest directly; its copy of the
 // scene table sits in dynamic shared memory, sized for the batch. The autotuner times the candidate schedules on the
 // caller's own prepared batch and returns the fastest.
 #include <algorithm>
@@ -30,7 +31,7 @@ struct SceneDev {
                        // memory by the item arithmetic (no per-thread copy in registers)
   int64_t tile_begin;  // first global tile of this scene
   int64_t unit_begin;  // first global sub-tile (tile_begin x sub_tiles)
-  int32_t staged;  // bit 0: parameter spans may be moved by bulk copies (even L, N L sizeof(T) % 16 == 0,
+  int32_t staged;  // bit 0: parameter spans may be moved by bulk copies (even L >= 4, N L sizeof(T) % 16 == 0,
                    // 16-byte aligned planes); bit 1: the means, upstream gradients and diffuse colours
                    // too (16-byte aligned buffers, moved by span plans)
   int32_t pad;
@@ -144,12 +145,13 @@ __global__ void __launch_bounds__(256, 2) batched_kernel(const BatchArgs b) {
     const int tp = 256 >> sc.slice_log2;
     const int local = threadIdx.x >> sc.slice_log2;
     const int l0 = 2 * (threadIdx.x & ((1 << sc.slice_log2) - 1));
-    const int64_t base = (tile - sd[lo].tile_begin) * int64_t(tp) * b.sub_tiles;
+    const int sub = b.sub_tiles * unit_items<T>();  // sub-items of tp primitives in the tile
+    const int64_t base = (tile - sd[lo].tile_begin) * int64_t(tp) * sub;
     RawItem<T, P> cur, nxt;
     fetch_scene_item<T, P>(sc, base + local, l0, true, cur);
-    for (int j = 0; j < b.sub_tiles; ++j) {
+    for (int j = 0; j < sub; ++j) {
       const int64_t prim = base + int64_t(j) * tp + local;
-      fetch_scene_item<T, P>(sc, prim + tp, l0, j + 1 < b.sub_tiles, nxt);
+      fetch_scene_item<T, P>(sc, prim + tp, l0, j + 1 < sub, nxt);
       eval_scene_item<FRAME, T, FLAGS, PAIRS>(sc, cur, prim, l0);
       cur = nxt;
     }
@@ -176,10 +178,10 @@ struct PlanDev {
 // Staged variant
 // ---------------------------------------------------------------------------
 
-// Stages in flight per block (f32 parameters take twice the space).
+// Stages in flight per block.
 template <typename T>
-constexpr int batch_stages() { return sizeof(T) == 2 ? 4 : 3; }
-constexpr int kMaxBatchStages = 4;
+constexpr int batch_stages() { return 3; }
+constexpr int kMaxBatchStages = 3;
 constexpr uint32_t kUnitEnd = 0xffffffffu;
 
 // Shared-memory metadata of one stage, written by the producer with the unit.
@@ -191,10 +193,10 @@ struct StageMeta {
   int64_t p0;        // first primitive of the unit in its scene
 };
 
-// Stage layout: batch_geom<T, P>() (P parameter spans of up to 512 lobes, then
-// the means, upstream-gradient and diffuse-colour regions of up to 256
-// primitives; a sub-tile holds at most 512 lobes: 256/S primitives x L lobes
-// with S >= L/2).
+// Stage layout: batch_geom<T, P>() (P parameter spans of up to I x 512 lobes, then
+// the means, upstream-gradient and diffuse-colour regions of up to I x 128
+// primitives): a staged sub-tile holds I x 256/S primitives x L lobes with S >= L/2
+// and L >= 4 (S >= 2); the sub-tiles of scenes with fewer lobes are loaded directly.
 template <typename T, int P>
 __host__ __device__ inline uint32_t batch_stage_bytes() {
   return batch_geom<T, P>().stage_bytes;
@@ -224,7 +226,7 @@ __device__ __forceinline__ bool issue_unit(const BatchArgs& b, const SceneDev* s
   const int32_t staged = sd[sc_i].staged;
   const int64_t n = sc.n;
   const uint32_t L = uint32_t(sc.n_lobes);
-  const int64_t tp = 256 >> sc.slice_log2;
+  const int64_t tp = int64_t(256 >> sc.slice_log2) * unit_items<T>();
   const int64_t p0 = (u - sd[sc_i].unit_begin) * tp;
   const int64_t count = n - p0 < tp ? n - p0 : tp;
   meta->unit = unit;
@@ -343,56 +345,62 @@ __global__ void __launch_bounds__(kStagedThreads, 2) batched_staged_kernel(const
     pending &= ~(1u << s);  // this stage's fill (whoever issued it) has landed
     const StageMeta m = meta[s];
     if (m.unit == kUnitEnd) break;  // block-uniform: every warp reads the same stage
-    RawItem<T, P> r;
-    r.ok = 0;
-    int64_t prim = 0;
-    int l0 = 0;
     const EvalArgs& sc = sd[m.scene >= 0 ? m.scene : 0].args;
-    if (m.scene >= 0) {
-      const int local = int(threadIdx.x) >> sc.slice_log2;
-      l0 = 2 * (int(threadIdx.x) & ((1 << sc.slice_log2) - 1));
-      prim = m.p0 + local;
-      if (m.staged & 1) {
-        r.ok = local < m.count;
-        if (r.ok) {
-          r.i = 0;
-          const unsigned char* st = smem + s * sbytes;
-          if (m.staged & 2) {
-            // a unit's first primitive is a multiple of 256/S >= 16: the means start
-            // on a 16-byte boundary, diffuse-colour plane c at c0_head(c, N)
-            const float* mu = reinterpret_cast<const float*>(st + g.off_mu);
-            const float* gc = reinterpret_cast<const float*>(st + g.off_gc);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) r.mu[c] = mu[3 * local + c];
+    for (int k = 0; k < unit_items<T>(); ++k) {
+      RawItem<T, P> r;
+      r.ok = 0;
+      int64_t prim = 0;
+      int l0 = 0;
+      if (m.scene >= 0) {
+        const int local = int(threadIdx.x) >> sc.slice_log2;
+        const int loc = local + k * (256 >> sc.slice_log2);  // this item's primitive in the unit
+        l0 = 2 * (int(threadIdx.x) & ((1 << sc.slice_log2) - 1));
+        prim = m.p0 + loc;
+        if (m.staged & 1) {
+          r.ok = loc < m.count;
+          if (r.ok) {
+            r.i = 0;
+            const unsigned char* st = smem + s * sbytes;
+            if (m.staged & 2) {
+              // a unit's first primitive is a multiple of 256/S >= 16: the means start
+              // on a 16-byte boundary, diffuse-colour plane c at c0_head(c, N)
+              const float* mu = reinterpret_cast<const float*>(st + g.off_mu);
+              const float* gc = reinterpret_cast<const float*>(st + g.off_gc);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) r.gc[c] = gc[3 * local + c];
+              for (int c = 0; c < 3; ++c) r.mu[c] = mu[3 * loc + c];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-              r.c0[c] = to_float(*reinterpret_cast<const T*>(st + g.off_c0 + c * g.c0_cap + c0_head<T>(c, sc.n) +
-                                                             local * sizeof(T)));
-          } else {
+              for (int c = 0; c < 3; ++c) r.gc[c] = gc[3 * loc + c];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) r.mu[c] = __ldg(sc.means + 3 * prim + c);
+              for (int c = 0; c < 3; ++c)
+                r.c0[c] = to_float(*reinterpret_cast<const T*>(st + g.off_c0 + c * g.c0_cap + c0_head<T>(c, sc.n) +
+                                                               loc * sizeof(T)));
+            } else {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) r.gc[c] = __ldg(sc.g_rgb + 3 * prim + c);
-            const T* c0 = static_cast<const T*>(sc.c0);
+              for (int c = 0; c < 3; ++c) r.mu[c] = __ldg(sc.means + 3 * prim + c);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) r.c0[c] = load1<T>(c0 + c * sc.n + prim);
+              for (int c = 0; c < 3; ++c) r.gc[c] = __ldg(sc.g_rgb + 3 * prim + c);
+              const T* c0 = static_cast<const T*>(sc.c0);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) r.c0[c] = load1<T>(c0 + c * sc.n + prim);
+            }
+            if (l0 < sc.n_lobes) {
+#pragma unroll
+              for (int p = 0; p < P; ++p)
+                r.w[p] = *reinterpret_cast<const W*>(st + size_t(p) * g.plane_bytes +
+                                                     size_t(loc * sc.n_lobes + l0) * sizeof(T));
+            }
           }
-          if (l0 < sc.n_lobes) {
-#pragma unroll
-            for (int p = 0; p < P; ++p)
-              r.w[p] = *reinterpret_cast<const W*>(st + size_t(p) * g.plane_bytes +
-                                                   size_t(local * sc.n_lobes + l0) * sizeof(T));
-          }
+        } else {
+          fetch_scene_item<T, P>(sc, prim, l0, loc < m.count, r);
         }
-      } else {
-        fetch_scene_item<T, P>(sc, prim, l0, true, r);
       }
+      if (k == unit_items<T>() - 1) {
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
+      }
+      if (m.scene >= 0) eval_scene_item<FRAME, T, FLAGS, PAIRS>(sc, r, prim, l0);
     }
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
-    if (m.scene >= 0) eval_scene_item<FRAME, T, FLAGS, PAIRS>(sc, r, prim, l0);
   }
   // on a failed wait, let the copies this block started finish before leaving (bounded)
   if (lane == 0 && failed) {
@@ -477,13 +485,13 @@ extern "C" nasg_status nasgabor_batched_prepare(const nasg_scene* scenes, int32_
       const bool idx32 = s.n * s.n_lobes * P < lim && 3 * s.n < lim;
       pair_path = pair_path && even && idx32;
     }
-    d.staged = (s.n_lobes % 2 == 0) && s.params && aligned(s.params, 16) && (s.n * s.n_lobes * es) % 16 == 0
+    d.staged = (s.n_lobes % 2 == 0) && s.n_lobes >= 4 && s.params && aligned(s.params, 16) && (s.n * s.n_lobes * es) % 16 == 0
                    ? 1 | (aligned(s.means, 16) && aligned(s.g_rgb, 16) && aligned(s.c0, 16) ? 2 : 0)
                    : 0;
     d.tile_begin = tiles;
     d.unit_begin = tiles * sub_tiles;
     d.pad = 0;
-    const int64_t tile_prims = int64_t(256 >> a.slice_log2) * sub_tiles;
+    const int64_t tile_prims = int64_t(256 >> a.slice_log2) * unit_items_of(modes->param_dtype) * sub_tiles;
     tiles += (s.n + tile_prims - 1) / tile_prims;
     prims += s.n;
     lobes += s.n * s.n_lobes;

@@ -168,10 +168,16 @@ NASG_HD SpanPlan tile_span(const TileGeom& g, uint32_t n, uint32_t n_lobes, uint
   return span_plan((uint64_t(c) * n + p0) * es, count * es, uint64_t(3) * n * es);
 }
 
-// Stage layout of the staged batched kernel: room for any scene's unit (at most
-// 256 primitives and 512 lobes), i.e. the layout of a 256-primitive tile of
-// two lobes.
+// Items per thread in a sub-tile of the batched kernels: two for BF16 parameters
+// (sub-tiles of 2 x 256/S primitives), one for FP32 (whose stages are twice as large).
+template <typename T>
+NASG_HD constexpr int unit_items() { return sizeof(T) == 2 ? 2 : 1; }
+NASG_HD constexpr int unit_items_of(int param_dtype) { return param_dtype == 1 ? 2 : 1; }  // NASG_DTYPE_BF16
+
+// Stage layout of the staged batched kernel: room for the sub-tile of any scene it
+// stages (L >= 4, so S >= 2: at most I x 128 primitives and I x 512 lobes), i.e. the
+// layout of an I x 128-primitive tile of four lobes.
 template <typename T, int P>
-NASG_HD constexpr TileGeom batch_geom() { return tile_geom<T, P, true>(0, 2); }
+NASG_HD constexpr TileGeom batch_geom() { return tile_geom<T, P, true>(1, 4, 256u * uint32_t(unit_items<T>())); }
 
 }  // namespace nasg

@@ -82,14 +82,14 @@ static void check_eval(uint32_t n, uint32_t L, uint32_t threads = 256u) {
   }
 }
 
-// Units of the staged batched kernel: sub-tiles of 256/S primitives of one scene,
+// Units of the staged batched kernel: sub-tiles of I x 256/S primitives of one scene,
 // staged into the fixed batch layout.
 template <typename T, int P>
 static void check_batch(uint32_t n, uint32_t L) {
   const uint32_t es = sizeof(T);
   int slog = 0;
   while ((1u << slog) < (L + 1) / 2) ++slog;
-  const uint32_t tp = 256u >> slog;
+  const uint32_t tp = (256u >> slog) * uint32_t(unit_items<T>());
   const TileGeom g = batch_geom<T, P>();
   CHECK(g.off_mu % 16 == 0 && g.off_gc % 16 == 0 && g.off_c0 % 16 == 0 && g.c0_cap % 16 == 0 &&
             g.stage_bytes % 128 == 0 && g.off_c0 + 3 * g.c0_cap <= g.stage_bytes,
@@ -144,9 +144,9 @@ int main() {
         check_eval<float, 10, true>(n, L, 384u);
         if (n % 8 == 0) check_eval<float, 10, false>(n, L, 384u);
       }
-      // batched scenes are staged when L is even and N L sizeof(T) % 16 == 0
-      if ((uint64_t(n) * L * 2) % 16 == 0) check_batch<F16, 10>(n, L);
-      if ((uint64_t(n) * L * 4) % 16 == 0) check_batch<float, 9>(n, L);
+      // batched scenes are staged when L >= 4 is even and N L sizeof(T) % 16 == 0
+      if (L >= 4 && (uint64_t(n) * L * 2) % 16 == 0) check_batch<F16, 10>(n, L);
+      if (L >= 4 && (uint64_t(n) * L * 4) % 16 == 0) check_batch<float, 9>(n, L);
     }
   }
   std::printf("ok %ld\n", g_cases);
