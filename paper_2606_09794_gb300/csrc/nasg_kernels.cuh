@@ -467,7 +467,8 @@ constexpr uint32_t kStagedWarps = kStagedThreads / 32;
 template <int MODE>
 constexpr uint32_t staged_threads() { return MODE == kFwd ? 384u : kStagedThreads; }
 // The full and empty barriers of the stages, rounded to 16 bytes.
-constexpr uint32_t kBarrierBytes = (2u * kStages * 8u + 15u) & ~15u;
+constexpr uint32_t barrier_bytes(int stages) { return (2u * uint32_t(stages) * 8u + 15u) & ~15u; }
+constexpr uint32_t kBarrierBytes = barrier_bytes(kStages);
 
 // Moves the plain-load part of a span plan (the last bytes of a buffer).
 __device__ __forceinline__ void span_tail(unsigned char* dst, const void* base, const SpanPlan& s) {
@@ -522,7 +523,7 @@ __device__ __forceinline__ void issue_tile(const EvalArgs& a, const TileGeom& g,
 // KI: items per thread and stage (a tile of KI x THREADS/S primitives; a thread evaluates
 // its KI items of a stage one after the other, which spreads the per-stage work -- the
 // waits, the producer's turn, the tile arithmetic -- over KI items).
-template <int FRAME, typename T, int MODE, int FLAGS, bool ANYN, int LC, int KI = 1>
+template <int FRAME, typename T, int MODE, int FLAGS, bool ANYN, int LC, int KI = 1, int NS = kStages>
 __global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(const EvalArgs a) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr bool FWD = (MODE & kFwd) != 0;
@@ -534,17 +535,17 @@ __global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(con
   const int slog = LC ? log2_of(slice_of_lobes(LC)) : a.slice_log2;
   const uint32_t L = LC ? uint32_t(LC) : uint32_t(a.n_lobes);
   const TileGeom g = tile_geom<T, P, ANYN>(slog, int(L), NT * KI);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * g.stage_bytes);  // tile landed
-  uint64_t* empty = full + kStages;                                             // tile read by all warps
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NS * g.stage_bytes);  // tile landed
+  uint64_t* empty = full + NS;                                             // tile read by all warps
   constexpr bool TAB = tanh_table<FRAME, T>();
   // after the barriers, on a 16-byte boundary (the stages are 128-byte multiples)
-  float4* tab = reinterpret_cast<float4*>(smem + kStages * g.stage_bytes + kBarrierBytes);
+  float4* tab = reinterpret_cast<float4*>(smem + NS * g.stage_bytes + barrier_bytes(NS));
   if constexpr (TAB) fill_tanh_table(tab);
   const uint32_t n = uint32_t(a.n);
   const uint32_t n_tiles = (n + g.tp - 1) / g.tp;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], NW);
     }
@@ -560,7 +561,7 @@ __global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(con
   uint32_t pending = 0, pend_par = 0;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < NS; ++s) {
       const uint32_t tile = blockIdx.x + s * gridDim.x;
       if (tile < n_tiles) {
         issue_tile<T, P, FWD, BWD, ANYN>(a, g, L, tile, smem + s * g.stage_bytes, &full[s]);
@@ -577,23 +578,23 @@ __global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(con
     // of slack, so the wait for its last reader is normally already over)
     if (it >= 1 && lane == 0 && warp == (it - 1) % NW) {
       const uint32_t pit = it - 1;
-      const uint32_t nit = pit + kStages;
+      const uint32_t nit = pit + NS;
       const uint32_t next = blockIdx.x + nit * gridDim.x;
-      const int ps = pit % kStages;
-      if (next < n_tiles && mbar_wait(&empty[ps], (pit / kStages) & 1u, a.dev_err)) {
+      const int ps = pit % NS;
+      if (next < n_tiles && mbar_wait(&empty[ps], (pit / NS) & 1u, a.dev_err)) {
         fence_proxy_async();
         issue_tile<T, P, FWD, BWD, ANYN>(a, g, L, next, smem + ps * g.stage_bytes, &full[ps]);
         pending |= 1u << ps;
-        pend_par = (pend_par & ~(1u << ps)) | (((nit / kStages) & 1u) << ps);
+        pend_par = (pend_par & ~(1u << ps)) | (((nit / NS) & 1u) << ps);
       }
     }
-    const int s = it % kStages;
+    const int s = it % NS;
     const unsigned char* st = smem + s * g.stage_bytes;
-    const bool arrived = __all_sync(0xffffffffu, mbar_wait(&full[s], (it / kStages) & 1u, a.dev_err));
+    const bool arrived = __all_sync(0xffffffffu, mbar_wait(&full[s], (it / NS) & 1u, a.dev_err));
     if (!arrived) {  // warp-uniform; the other warps give up on their own waits
       // let the copies this lane started land before the block leaves (bounded)
       if (lane == 0) {
-        for (int q = 0; q < kStages; ++q)
+        for (int q = 0; q < NS; ++q)
           if (pending & (1u << q)) mbar_wait(&full[q], (pend_par >> q) & 1u, nullptr, 1u << 16);
       }
       return;
@@ -690,13 +691,13 @@ bool tma_eligible(const EvalArgs& a, bool even) {
   return true;
 }
 
-template <int MODE, int FRAME, typename T, int FLAGS, bool ANYN, int LC, int KI = 1>
+template <int MODE, int FRAME, typename T, int FLAGS, bool ANYN, int LC, int KI = 1, int NS = kStages>
 nasg_status launch_tma_geom(const EvalArgs& a, cudaStream_t s) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr uint32_t NT = staged_threads<MODE>();
   const TileGeom g = tile_geom<T, P, ANYN>(a.slice_log2, a.n_lobes, NT * KI);
-  const size_t smem = size_t(kStages) * g.stage_bytes + kBarrierBytes + (tanh_table<FRAME, T>() ? kTanhBytes : 0u);
-  auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS, ANYN, LC, KI>;
+  const size_t smem = size_t(NS) * g.stage_bytes + barrier_bytes(NS) + (tanh_table<FRAME, T>() ? kTanhBytes : 0u);
+  auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS, ANYN, LC, KI, NS>;
   if (const nasg_status e = ensure_smem_limit(reinterpret_cast<const void*>(k), smem); e != NASG_OK) return e;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem) != cudaSuccess || per_sm < 1)
@@ -713,11 +714,14 @@ nasg_status launch_tma_geom(const EvalArgs& a, cudaStream_t s) {
 // and the FP32 forward).
 template <int MODE, int FRAME, typename T, int FLAGS, int LC>
 nasg_status launch_tma_lc(const EvalArgs& a, cudaStream_t s) {
-  // BF16 forward+backward at L = 8 and 16: two items per thread and stage (tiles of 1024
-  // lobes; three stages and the tanh table still fit two blocks per SM)
-  constexpr int KI = (sizeof(T) == 2 && MODE == kFwdBwd && LC >= 8) ? 2 : 1;
-  return a.n % 8 == 0 ? launch_tma_geom<MODE, FRAME, T, FLAGS, false, LC, KI>(a, s)
-                      : launch_tma_geom<MODE, FRAME, T, FLAGS, true, LC, KI>(a, s);
+  // BF16 forward+backward: several items per thread and stage in two stages (L = 8, 16:
+  // three items, tiles of 1536 lobes; L = 4: two items, tiles of 1024 lobes), which with
+  // the tanh table still fit two blocks per SM
+  constexpr bool many = sizeof(T) == 2 && MODE == kFwdBwd;
+  constexpr int KI = many ? (LC >= 8 ? 3 : 2) : 1;
+  constexpr int NS = many ? 2 : kStages;
+  return a.n % 8 == 0 ? launch_tma_geom<MODE, FRAME, T, FLAGS, false, LC, KI, NS>(a, s)
+                      : launch_tma_geom<MODE, FRAME, T, FLAGS, true, LC, KI, NS>(a, s);
 }
 
 template <int MODE, int FRAME, typename T, int FLAGS>

@@ -42,7 +42,7 @@ static void check_span(const SpanPlan& s, uint64_t off, uint32_t bytes, uint64_t
 }
 
 // Tiles of the staged kernels for a block of `threads` x items per thread (256: the passes with
-// a backward, 384: the forward alone, 512: two items per thread of 256-thread blocks).
+// a backward, 384: the forward alone, 512 / 768: two / three items per thread of 256-thread blocks).
 template <typename T, int P, bool ANYN>
 static void check_eval(uint32_t n, uint32_t L, uint32_t threads = 256u) {
   const uint32_t es = sizeof(T);
@@ -131,11 +131,10 @@ int main() {
         check_eval<F16, 9, true>(n, L);
         check_eval<F16, 11, true>(n, L);
         if (n % 8 == 0) check_eval<F16, 10, false>(n, L);
-        if (L >= 8) {
-          check_eval<F16, 10, true>(n, L, 512u);
-          check_eval<F16, 9, true>(n, L, 512u);
-          if (n % 8 == 0) check_eval<F16, 10, false>(n, L, 512u);
-        }
+        const uint32_t many = L >= 8 ? 768u : 512u;
+        check_eval<F16, 10, true>(n, L, many);
+        check_eval<F16, 9, true>(n, L, many);
+        if (n % 8 == 0) check_eval<F16, 10, false>(n, L, many);
       }
       if ((uint64_t(n) * L * 4) % 16 == 0) {
         check_eval<float, 10, true>(n, L);
