@@ -283,8 +283,11 @@ __device__ __forceinline__ float pick3(const float v[3], int c) { return c == 0 
 constexpr int slice_of_lobes(int L) { return L <= 2 ? 1 : 2 * slice_of_lobes((L + 1) / 2); }
 constexpr int log2_of(int x) { return x <= 1 ? 0 : 1 + log2_of(x >> 1); }
 
-// LC: the lobe count when fixed at compile time (0: read from the arguments).
-template <int FRAME, typename T, typename IDX, int MODE, bool EVEN, int FLAGS, int LC = 0, bool TAB = false>
+// LC: the lobe count when fixed at compile time (0: read from the arguments). C0_OWN: the
+// item holds only the diffuse colour of the lane's own output channel, in c0[0] (slices
+// of S >= 4 lanes, where a lane writes at most channel l0/2).
+template <int FRAME, typename T, typename IDX, int MODE, bool EVEN, int FLAGS, int LC = 0, bool TAB = false,
+          bool C0_OWN = false>
 __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, FrameTraits<FRAME>::P>& cur, IDX i,
                                           int l0, const float4* tab = nullptr) {
   constexpr int P = FrameTraits<FRAME>::P;
@@ -373,7 +376,7 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
     const float dot = __shfl_sync(0xffffffffu, e0, lane | 3);
     const int c = l0 >> 1;  // this lane's channel (lane index within the slice)
     if (ok && c < 3) {
-      a.rgb[3 * i + c] = e0 + pick3(cur.c0, c);
+      a.rgb[3 * i + c] = e0 + (C0_OWN ? cur.c0[0] : pick3(cur.c0, c));
       store1(a.g_c0 + c * n + i, pick3(cur.gc, c), acc);
       // dLoss/dmu = (I - d d^T) dLoss/dd / |mu - cam|
       if (a.g_means) store1(a.g_means + 3 * i + c, mean_grad_rn(e1, dot, pick3(d, c), inv_dist), acc);
@@ -391,7 +394,7 @@ __device__ __forceinline__ void eval_item(const EvalArgs& a, const RawItem<T, Fr
   if (ok) {
     const float dot = BWD ? dot3_rn(gd, d) : 0.f;
     for (int c = l0 >> 1; c < 3; c += S()) {
-      if (FWD) a.rgb[3 * i + c] = pick3(rgb, c) + pick3(cur.c0, c);
+      if (FWD) a.rgb[3 * i + c] = pick3(rgb, c) + (C0_OWN ? cur.c0[0] : pick3(cur.c0, c));
       if (BWD) {
         store1(a.g_c0 + c * n + i, pick3(cur.gc, c), acc);
         // dLoss/dmu = (I - d d^T) dLoss/dd / |mu - cam|
@@ -530,6 +533,8 @@ __global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(con
   constexpr bool BWD = (MODE & kBwd) != 0;
   constexpr uint32_t NT = staged_threads<MODE>();
   constexpr uint32_t NW = NT / 32;
+  // several items per thread at L >= 8 (S >= 4): each lane reads only its own channel's c0
+  constexpr bool C0_OWN = KI > 1 && LC >= 8;
   using W = typename RawWord<T>::type;
   extern __shared__ __align__(128) unsigned char smem[];
   const int slog = LC ? log2_of(slice_of_lobes(LC)) : a.slice_log2;
@@ -619,10 +624,16 @@ __global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(con
         }
         if (FWD) {
           // plain shared-memory reads (load1 uses the global read-only path)
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            r.c0[c] = to_float(*reinterpret_cast<const T*>(st + g.off_c0 + c * g.c0_cap + c0_head<T, ANYN>(c, n) +
+          if constexpr (C0_OWN) {
+            const uint32_t c = min(uint32_t(l0) >> 1, 2u);  // the lane's output channel
+            r.c0[0] = to_float(*reinterpret_cast<const T*>(st + g.off_c0 + c * g.c0_cap + c0_head<T, ANYN>(c, n) +
                                                            loc * sizeof(T)));
+          } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              r.c0[c] = to_float(*reinterpret_cast<const T*>(st + g.off_c0 + c * g.c0_cap + c0_head<T, ANYN>(c, n) +
+                                                             loc * sizeof(T)));
+          }
         }
         if (uint32_t(l0) < L) {
 #pragma unroll
@@ -634,7 +645,7 @@ __global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(con
         __syncwarp();
         if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
       }
-      eval_item<FRAME, T, uint32_t, MODE, true, FLAGS, LC, TAB>(a, r, i, l0, tab);
+      eval_item<FRAME, T, uint32_t, MODE, true, FLAGS, LC, TAB, C0_OWN>(a, r, i, l0, tab);
     }
   }
 }
