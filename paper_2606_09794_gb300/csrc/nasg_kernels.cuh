@@ -462,13 +462,16 @@ constexpr int kStages = 3;
 // A compile-time warp count keeps the producer's turn (iteration mod warps) cheap:
 // the same modulo by blockDim.x / 32 at run time cost 3.5 % of the fused pass.
 // The forward alone (fewer registers) runs 384 threads, 24 warps per SM at two
-// blocks: 3 % faster than 256 for the FP32 forward, while the passes with a
-// backward need the registers of 256-thread blocks (at 384 they spill).
+// blocks: 3 % faster than 256 for the FP32 forward with one item per thread, while
+// the passes with a backward need the registers of 256-thread blocks (at 384 they
+// spill).
 // A tile of THREADS/S primitives is a multiple of 8 for S <= THREADS/8.
 constexpr uint32_t kStagedThreads = 256;
 constexpr uint32_t kStagedWarps = kStagedThreads / 32;
-template <int MODE>
-constexpr uint32_t staged_threads() { return MODE == kFwd ? 384u : kStagedThreads; }
+// (A forward that takes several items per thread and stage runs 256-thread blocks, whose
+// stages of two items fit two blocks per SM.)
+template <int MODE, int KI = 1>
+constexpr uint32_t staged_threads() { return MODE == kFwd && KI == 1 ? 384u : kStagedThreads; }
 // The full and empty barriers of the stages, rounded to 16 bytes.
 constexpr uint32_t barrier_bytes(int stages) { return (2u * uint32_t(stages) * 8u + 15u) & ~15u; }
 constexpr uint32_t kBarrierBytes = barrier_bytes(kStages);
@@ -527,11 +530,11 @@ __device__ __forceinline__ void issue_tile(const EvalArgs& a, const TileGeom& g,
 // its KI items of a stage one after the other, which spreads the per-stage work -- the
 // waits, the producer's turn, the tile arithmetic -- over KI items).
 template <int FRAME, typename T, int MODE, int FLAGS, bool ANYN, int LC, int KI = 1, int NS = kStages>
-__global__ void __launch_bounds__(staged_threads<MODE>(), 2) eval_tma_kernel(const EvalArgs a) {
+__global__ void __launch_bounds__(staged_threads<MODE, KI>(), 2) eval_tma_kernel(const EvalArgs a) {
   constexpr int P = FrameTraits<FRAME>::P;
   constexpr bool FWD = (MODE & kFwd) != 0;
   constexpr bool BWD = (MODE & kBwd) != 0;
-  constexpr uint32_t NT = staged_threads<MODE>();
+  constexpr uint32_t NT = staged_threads<MODE, KI>();
   constexpr uint32_t NW = NT / 32;
   // several items per thread at L >= 8 (S >= 4): each lane reads only its own channel's c0
   constexpr bool C0_OWN = KI > 1 && LC >= 8;
@@ -705,7 +708,7 @@ bool tma_eligible(const EvalArgs& a, bool even) {
 template <int MODE, int FRAME, typename T, int FLAGS, bool ANYN, int LC, int KI = 1, int NS = kStages>
 nasg_status launch_tma_geom(const EvalArgs& a, cudaStream_t s) {
   constexpr int P = FrameTraits<FRAME>::P;
-  constexpr uint32_t NT = staged_threads<MODE>();
+  constexpr uint32_t NT = staged_threads<MODE, KI>();
   const TileGeom g = tile_geom<T, P, ANYN>(a.slice_log2, a.n_lobes, NT * KI);
   const size_t smem = size_t(NS) * g.stage_bytes + barrier_bytes(NS) + (tanh_table<FRAME, T>() ? kTanhBytes : 0u);
   auto k = eval_tma_kernel<FRAME, T, MODE, FLAGS, ANYN, LC, KI, NS>;
@@ -727,10 +730,12 @@ template <int MODE, int FRAME, typename T, int FLAGS, int LC>
 nasg_status launch_tma_lc(const EvalArgs& a, cudaStream_t s) {
   // BF16 forward+backward: several items per thread and stage in two stages (L = 8, 16:
   // three items, tiles of 1536 lobes; L = 4: two items, tiles of 1024 lobes), which with
-  // the tanh table still fit two blocks per SM
+  // the tanh table still fit two blocks per SM; the FP32 forward alone: two items per
+  // thread in two stages of 256-thread blocks (at 384 threads they would not fit two blocks)
   constexpr bool many = sizeof(T) == 2 && MODE == kFwdBwd;
-  constexpr int KI = many ? (LC >= 8 ? 3 : 2) : 1;
-  constexpr int NS = many ? 2 : kStages;
+  constexpr bool ffwd = sizeof(T) == 4 && MODE == kFwd;
+  constexpr int KI = many ? (LC >= 8 ? 3 : 2) : (ffwd ? 2 : 1);
+  constexpr int NS = (many || ffwd) ? 2 : kStages;
   return a.n % 8 == 0 ? launch_tma_geom<MODE, FRAME, T, FLAGS, false, LC, KI, NS>(a, s)
                       : launch_tma_geom<MODE, FRAME, T, FLAGS, true, LC, KI, NS>(a, s);
 }

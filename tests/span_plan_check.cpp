@@ -142,6 +142,8 @@ int main() {
         if (n % 8 == 0) check_eval<float, 10, false>(n, L);
         check_eval<float, 10, true>(n, L, 384u);
         if (n % 8 == 0) check_eval<float, 10, false>(n, L, 384u);
+        check_eval<float, 10, true>(n, L, 512u);
+        if (n % 8 == 0) check_eval<float, 10, false>(n, L, 512u);
       }
       // batched scenes are staged when L >= 4 is even and N L sizeof(T) % 16 == 0
       if (L >= 4 && (uint64_t(n) * L * 2) % 16 == 0) check_batch<F16, 10>(n, L);
