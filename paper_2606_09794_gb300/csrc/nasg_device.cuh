@@ -560,8 +560,9 @@ __device__ __forceinline__ void lobe_norm(V lam, V a, V k, V phi, bool normalise
 }
 
 // One lobe of family FAM at direction d, given its normalisation factors nc (a, k,
-// phi ignored where the family has none; see Family).
-template <bool GRAD, int FAM, class V>
+// phi ignored where the family has none; see Family). PER_G: G_u, G_a and G_lam are
+// returned divided by G (the caller multiplies them by G once, with its upstream factor).
+template <bool GRAD, int FAM, class V, bool PER_G = false>
 __device__ __forceinline__ V lobe_at(const V* d, const V* x, const V* z, V lam, V a, V k, V phi,
                                      const LobeNorm<V>& nc, bool exact, bool logscale, LobePartials<V>* pd) {
   using F = Family<FAM>;
@@ -633,13 +634,15 @@ __device__ __forceinline__ V lobe_at(const V* d, const V* x, const V* z, V lam, 
     const V dlne_dv = ln_k * dtau_dv;
     const V cpe_sin = cpe * sin_kv;                     // C^-1 p E sin(k v + phi)
     if (F::HAS_A) {
-      pd->G_u = G * vfma(two_lam_ek, dlne_du + inv_opu, dlne_du);
+      const V f_u = vfma(two_lam_ek, dlne_du + inv_opu, dlne_du);
+      pd->G_u = PER_G ? f_u : G * f_u;
       const V gv_env = G * (two_lam_ek + 1.f) * dlne_dv;
       pd->G_v = F::HAS_K ? vfma(G * (two_lam_ek + 1.f), dlne_dv, -(cpe_sin * (0.5f * k))) : gv_env;
       // d(tau)/da = v^2/(1-u^2); logscale: a d(tau)/da = tau
-      pd->G_a = G * vfma((two_lam_ek + 1.f) * ln_k, logscale ? tau : v * v * inv_s2, nc.da);
+      const V f_a = vfma((two_lam_ek + 1.f) * ln_k, logscale ? tau : v * v * inv_s2, nc.da);
+      pd->G_a = PER_G ? f_a : G * f_a;
     } else {
-      pd->G_u = G * lam;                                // d/du 2 lam (kappa - 1) = lam
+      pd->G_u = PER_G ? lam : G * lam;                  // d/du 2 lam (kappa - 1) = lam
       pd->G_v = vconst<V>(0.f);
       pd->G_a = vconst<V>(0.f);
     }
@@ -650,7 +653,8 @@ __device__ __forceinline__ V lobe_at(const V* d, const V* x, const V* z, V lam, 
     }
     pd->G_phi = F::HAS_PHASE ? (exact ? vfma(G, nc.dphi, -(0.5f * cpe_sin)) : -(0.5f * cpe_sin))
                              : vconst<V>(0.f);
-    pd->G_lam = G * vfma(logscale ? two_lam : vconst<V>(2.f), em1, nc.dlam);
+    const V f_lam = vfma(logscale ? two_lam : vconst<V>(2.f), em1, nc.dlam);
+    pd->G_lam = PER_G ? f_lam : G * f_lam;
   }
   return G;
 }

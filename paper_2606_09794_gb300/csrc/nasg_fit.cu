@@ -175,14 +175,15 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
         const P2 Gt = lobe_at<false, kFamNasGabor>(d, tea.x, tea.z, tea.lam, tea.a, tea.k, zero, tea.nc, EXACT,
                                                    s.identity == 0, &pd);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const P2 wg = tea.w[c] * Gt;
-          tcol[c] = wg.v.x + wg.v.y;
-        }
+        for (int c = 0; c < 3; ++c) tcol[c] = fmaf(tea.w[c].v.y, Gt.v.y, tea.w[c].v.x * Gt.v.x);
         for (int o = 1; o < tpairs; o <<= 1) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) tcol[c] += __shfl_xor_sync(0xffffffffu, tcol[c], o);
         }
+        // the teacher colour less the student-minus-teacher diffuse colour (this lane's
+        // primitive is the slice's): the residual below is then one subtraction
+#pragma unroll
+        for (int c = 0; c < 3; ++c) tcol[c] -= dc0[c];
       }
       for (int kk = 0; kk < G && base + kk < s.n_dirs; ++kk) {  // uniform
         const int j = base + kk;
@@ -192,14 +193,11 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
         const float dx = __ldg(s.dirs + 3 * j), dy = __ldg(s.dirs + 3 * j + 1), dz = __ldg(s.dirs + 3 * j + 2);
         const P2 d[3] = {p2(dx), p2(dy), p2(dz)};
         LobePartials<P2> pd;
-        const P2 Gs = lobe_at<true, kFamNasGabor>(d, stu.x, stu.z, stu.lam, stu.a, stu.k, zero, stu.nc, EXACT,
-                                                  s.identity == 0, &pd);
+        const P2 Gs = lobe_at<true, kFamNasGabor, P2, true>(d, stu.x, stu.z, stu.lam, stu.a, stu.k, zero, stu.nc,
+                                                            EXACT, s.identity == 0, &pd);
         float col[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const P2 wg = stu.w[c] * Gs;
-          col[c] = wg.v.x + wg.v.y;
-        }
+        for (int c = 0; c < 3; ++c) col[c] = fmaf(stu.w[c].v.y, Gs.v.y, stu.w[c].v.x * Gs.v.x);
         for (int o = S >> 1; o >= 1; o >>= 1) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) col[c] += __shfl_xor_sync(0xffffffffu, col[c], o);
@@ -209,18 +207,21 @@ __global__ void __launch_bounds__(kFitBlock, 2) fit_kernel(const FitArgs s) {
         float gc[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const float r = (col[c] - tc[c]) + dc0[c];
-          if (ok && g == 0) sq_sum = fmaf(r, r, sq_sum);
-          gc[c] = r;
-          acc_c0[c] += r;
+          gc[c] = col[c] - tc[c];
+          acc_c0[c] += gc[c];
+        }
+        if (ok && g == 0) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) sq_sum = fmaf(gc[c], gc[c], sq_sum);
         }
         const P2 gG = vfma(p2(gc[0]), stu.w[0], vfma(p2(gc[1]), stu.w[1], p2(gc[2]) * stu.w[2]));
+        const P2 gGG = gG * Gs;  // G_u, G_a, G_lam come divided by G
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc_w[c] = vfma(p2(gc[c]), Gs, acc_w[c]);
-        acc_lam = vfma(gG, pd.G_lam, acc_lam);
-        acc_a = vfma(gG, pd.G_a, acc_a);
+        acc_lam = vfma(gGG, pd.G_lam, acc_lam);
+        acc_a = vfma(gGG, pd.G_a, acc_a);
         acc_k = vfma(gG, pd.G_k, acc_k);
-        const P2 gv = gG * pd.G_v, gu = gG * pd.G_u;
+        const P2 gv = gG * pd.G_v, gu = gGG * pd.G_u;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           acc_gx[c] = vfma(gv, d[c], acc_gx[c]);
