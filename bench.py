@@ -506,7 +506,7 @@ def run_case(args):
         res = measure_batched(nb, inputs, dev, stream, peak, **({"n_scenes": args.case_n} if args.case_n else {}))
     elif args.case == "batched_one":
         res = measure_batched_one(nb, inputs, dev, stream, peak, **({"n_lobes": args.case_n} if args.case_n else {}),
-                                  **({"reps": args.case_steps} if args.case_steps else {}))
+                                  **({"reps": args.case_steps} if args.case_steps is not None else {}))
     else:
         if args.case_steps:
             kw["steps"] = args.case_steps
