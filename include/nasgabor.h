@@ -332,10 +332,10 @@ typedef struct nasg_batch_plan {
 /* Launch schedule: dynamic (1: tiles from an atomic counter, 0: round-robin),
  * blocks per SM (0: as many as fit), sub_tiles (the k prepare was called with),
  * staged (1: each sub-tile's parameter spans, means, upstream gradients and
- * diffuse colours moved into shared memory by bulk copies, four sub-tiles
- * ahead (three for FP32), for the scenes with even L, N L sizeof(T) a multiple
- * of 16 bytes and 16-byte aligned buffers; the others are loaded directly;
- * 0: every load direct, one sub-tile ahead). */
+ * diffuse colours moved into shared memory by bulk copies, three sub-tiles
+ * ahead, for the scenes with even L >= 4, N L sizeof(T) a multiple of 16 bytes
+ * and 16-byte aligned buffers; the others are loaded directly; 0: every load
+ * direct, one sub-tile ahead). */
 typedef struct nasg_batch_tuning {
   int32_t dynamic, blocks_per_sm, sub_tiles, staged;
 } nasg_batch_tuning;
@@ -345,7 +345,9 @@ size_t nasgabor_batched_workspace_bytes(int32_t n_scenes);
 
 /*
  * Validates the scenes (HOST array of n_scenes) and writes their device table
- * and tile ranges (tiles of sub_tiles x 256/S primitives, 1 <= sub_tiles <= 64)
+ * and tile ranges (tiles of sub_tiles sub-tiles of I x 256/S primitives, S the
+ * lanes per primitive of the scene's L, I = 2 for BF16 and 1 for FP32 parameters,
+ * 1 <= sub_tiles <= 64)
  * into `workspace` (16-byte aligned, >= nasgabor_batched_workspace_bytes).
  * Synchronises `stream` (not for use inside a stream capture). The buffers the
  * scenes point to are read/written by later runs, not by this call.
